@@ -1,0 +1,201 @@
+/*
+ * rbfgs.h -- C ABI of the GB300 (sm_103a) library for randomized quasi-Newton
+ * matrix inversion (Gower & Richtarik, "Randomized Quasi-Newton Updates are
+ * Linearly Convergent Matrix Inversion Algorithms", arXiv:1602.01768).
+ *
+ * The problem (Sec. 5 and Sec. 9): given a dense symmetric positive definite
+ * A (n x n), iterate towards X = A^-1 with
+ *   - RBFGS (Algorithm 3 with W = A^-1, the block BFGS update Eq. (qunac),
+ *     Sec. 8.8):  X+ = S L S^T + (I - S L S^T A) X (I - A S L S^T),
+ *     L = (S^T A S)^-1, S drawn i.i.d. each step (Gaussian or a coordinate
+ *     block);
+ *   - AdaRBFGS (Algorithm 4, factored update Eq. (Cholimprov), Sec. 9.3):
+ *     X = L L^T kept as its factor, S = L S~ with S~ drawn i.i.d.;
+ *   - Newton-Schulz, Eq. (Newton-Schulz), and MR, Eq. (MRiter), the
+ *     comparison methods of Sec. 10.
+ *
+ * Conventions shared by every entry point
+ *   - Matrices are column-major with an explicit leading dimension (ld >= n),
+ *     element type FP32 or FP64 as stated per call.
+ *   - Pointers named *_dev are device pointers of the current CUDA device;
+ *     pointers named *_host are host pointers (pinned or pageable).
+ *   - A handle owns every device buffer it allocates (its copy of A, the
+ *     iterate X or its factor L, workspaces); the caller owns everything it
+ *     passes in and may free it as soon as the call returns.
+ *   - All work is queued on the CUDA stream given at creation (a cudaStream_t
+ *     passed as void*; NULL = legacy default stream).  Step calls are
+ *     asynchronous; calls documented as "synchronises" wait for the stream.
+ *   - Every call returns an rb_status and never aborts the process.  Device
+ *     side failures (a Cholesky breakdown, a non-finite value) are recorded
+ *     in a device status word; the step that hits one and every later step
+ *     leave the iterate untouched, and the next synchronising call returns
+ *     the failure.
+ *   - A handle is used from one host thread at a time; distinct handles are
+ *     independent.
+ */
+#ifndef RBFGS_H
+#define RBFGS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rb_ctx *rbfgs_t;
+
+typedef enum {
+    RB_OK = 0,
+    RB_NOTCONV = 1,        /* solve stopped at max_iter above the tolerance (not an error) */
+    RB_EINVAL = -1,        /* bad argument (null pointer, n < 1, q out of range, ld < n) */
+    RB_ENOMEM = -2,        /* device allocation failed */
+    RB_ECUDA = -3,         /* a CUDA runtime call failed */
+    RB_ENOTSPD = -4,       /* Cholesky of S^T A S or S~^T S~ met a pivot <= 0 / non-finite:
+                              A is not SPD or S is rank deficient (Thm 5.1 needs full rank) */
+    RB_ENONFINITE = -5,    /* a non-finite residual */
+    RB_ETIMEOUT = -6,      /* a bounded device-side wait gave up */
+    RB_EUNSUPPORTED = -7   /* combination not built (method/precision/sketch) */
+} rb_status;
+
+typedef enum {
+    RB_FP64 = 0,    /* FP64 storage and arithmetic (the parity mode) */
+    RB_FP32 = 1,    /* FP32 storage, FP32 SIMT products, FP64 q x q core */
+    RB_TF32 = 2,    /* FP32 storage, single-pass TF32 tensor-core products */
+    RB_TF32X3 = 3,  /* FP32 storage, 3-term split TF32 tensor-core products (~FP32 accuracy) */
+    RB_MIXED = 4    /* FP32 storage, 3xTF32 where accuracy needs it, 1xTF32 for the
+                       rank-q correction whose size vanishes at the fixed point */
+} rb_prec;
+
+typedef enum {
+    RB_SKETCH_GAUSS = 0,          /* S (RBFGS) or S~ (AdaRBFGS) i.i.d. N(0,1), n x q */
+    RB_SKETCH_COORD_TRACE = 1,    /* RBFGS: contiguous block of q coordinates, drawn with
+                                     probability proportional to its diagonal trace
+                                     (Sec. 7.2, Eq. (convprob) with W = A^-1) */
+    RB_SKETCH_COORD_UNIFORM = 2   /* AdaRBFGS_cols: q distinct coordinates, uniform (Sec. 10) */
+} rb_sketch;
+
+typedef enum { RB_METHOD_RBFGS = 0, RB_METHOD_ADARBFGS = 1, RB_METHOD_NS = 2, RB_METHOD_MR = 3 } rb_method;
+
+typedef enum { RB_WHAT_X = 0, RB_WHAT_L = 1 } rb_what;
+
+typedef struct {
+    int32_t method;     /* rb_method */
+    int32_t sketch;     /* rb_sketch */
+    int32_t q;          /* sketch width, 1 <= q <= min(n, 128) */
+    int32_t prec;       /* rb_prec */
+    uint64_t seed;      /* Philox key of the sketch stream */
+    uint64_t stream_id; /* Philox counter word 3: independent streams for one seed */
+    int32_t power_iters;/* Newton-Schulz: power iterations for ||A||_2 (0 = 100) */
+    int32_t reserved[7];
+} rb_opts;
+
+/* Fill *opts with defaults: RBFGS, Gaussian sketch, q = 8, FP64, seed 0, stream 0. */
+void rbfgs_default_opts(rb_opts *opts);
+
+/*
+ * Create a solver for the n x n SPD matrix A_dev (ld lda, a_is_fp64 selects
+ * FP64 or FP32 elements).  A is copied into the handle's storage type (FP64
+ * for RB_FP64, FP32 otherwise).  The iterate starts at X0 = I (RBFGS) or
+ * L0 = I (AdaRBFGS), the starts of Sec. 10; Newton-Schulz and MR use
+ * newton_schulz_init / mr_init.  The step counter k starts at 0.
+ * Errors: RB_EINVAL, RB_ENOMEM, RB_ECUDA, RB_EUNSUPPORTED.
+ */
+rb_status rbfgs_init(rbfgs_t *h, int n, const void *A_dev, int64_t lda, int a_is_fp64,
+                     const rb_opts *opts, void *stream);
+
+/*
+ * nsteps RBFGS steps (Algorithm 3, W = A^-1): draw S_k, G = A S, the q x q
+ * core (Cholesky of S^T A S in FP64), Y = X G, T = G^T Y and the symmetric
+ * rank-2q update X += S W^T + W S^T, W = S (Lam + Lam T Lam)/2 - Y Lam, which
+ * equals Eq. (qunac).  Asynchronous.  The handle must be an RBFGS handle.
+ */
+rb_status rbfgs_step(rbfgs_t h, int nsteps);
+
+/*
+ * nsteps AdaRBFGS steps (Algorithm 4, Eq. (Cholimprov)): draw S~_k,
+ * S = L S~, G = A S, C C^T = S^T A S and D D^T = S~^T S~ (lower Cholesky),
+ * W = G^T L, V = D^-1 S~^T - C^-1 W, L += S C^-T V.  Asynchronous.
+ */
+rb_status adarbfgs_step(rbfgs_t h, int nsteps);
+
+/*
+ * Residual ||I - X A||_F / sqrt(n) of the current iterate (X = L L^T for
+ * AdaRBFGS), the stopping quantity of Sec. 10 without its normalisation by
+ * ||I - A X0||_F.  ncols = 0 evaluates it exactly (cost O(n^3)); ncols = m > 0
+ * estimates it from m distinct columns J (Floyd sampling on Philox with key
+ * col_seed): sqrt(sum_{j in J} ||e_j - X A e_j||^2 / m).  Sums in FP64.
+ * Synchronises; returns the first recorded device failure, if any.
+ */
+rb_status rbfgs_residual(rbfgs_t h, int ncols, uint64_t col_seed, double *out);
+
+/*
+ * Run steps until the sampled residual (check_cols columns, check_every
+ * steps apart; a final exact or sampled confirmation with confirm_cols,
+ * 0 = exact) is <= tol, or max_iter steps are done.  *iters gets the steps
+ * taken, *resid the last confirmed residual.  Returns RB_OK, RB_NOTCONV or an
+ * error.  Synchronises.
+ */
+rb_status rbfgs_solve(rbfgs_t h, double tol, int max_iter, int check_every, int check_cols,
+                      int confirm_cols, int *iters, double *resid);
+
+/*
+ * Copy the iterate out: what = RB_WHAT_X (X; for AdaRBFGS X = L L^T is formed)
+ * or RB_WHAT_L (AdaRBFGS factor).  out_dev has the handle's storage type
+ * (FP64 for RB_FP64, else FP32) and leading dimension ld.  Asynchronous.
+ */
+rb_status rbfgs_export(rbfgs_t h, int what, void *out_dev, int64_t ld);
+
+/*
+ * Replace the iterate (X for RBFGS/NS/MR, L for AdaRBFGS) by in_dev (storage
+ * type, ld).  With rbfgs_set_step this resumes a run from a checkpoint: the
+ * sketch stream is counter based, so the resumed run draws exactly the
+ * sketches of the uninterrupted one.  Asynchronous.
+ */
+rb_status rbfgs_import(rbfgs_t h, int what, const void *in_dev, int64_t ld);
+rb_status rbfgs_set_step(rbfgs_t h, uint64_t k);
+rb_status rbfgs_get_step(rbfgs_t h, uint64_t *k);
+
+/*
+ * Write the sketch of step k into out_dev (n x q, storage type, ld >= n):
+ * the Gaussian S_k (RBFGS) or S~_k (AdaRBFGS), or the 0/1 coordinate matrix
+ * I[:, C_k] (columns beyond a ragged last block are zero).  The draw is a pure
+ * function of (seed, stream_id, k), so this reproduces exactly what step k
+ * uses.  Asynchronous.
+ */
+rb_status rbfgs_draw_sketch(rbfgs_t h, uint64_t k, void *out_dev, int64_t ld);
+
+/* Device status word (0 = fine); synchronises. */
+rb_status rbfgs_sync(rbfgs_t h);
+
+/*
+ * Newton-Schulz (Sec. 10): X0 = 0.99 A / sigma^2, sigma = ||A||_2 from
+ * power_iters steps of the power iteration started at 1/sqrt(n) (standing in
+ * for MATLAB normest); sigma_override > 0 skips the estimate.  Steps:
+ * X+ = 2 X - X (A X), Eq. (Newton-Schulz).  Use rbfgs_residual / export /
+ * destroy on the handle.
+ */
+rb_status newton_schulz_init(rbfgs_t *h, int n, const void *A_dev, int64_t lda, int a_is_fp64,
+                             int prec, int power_iters, double sigma_override, void *stream);
+rb_status newton_schulz_step(rbfgs_t h, int nsteps);
+
+/*
+ * Minimal residual (Sec. 10, Eq. (MRiter)): X0 = (Tr A / Tr A A^T) I;
+ * R = I - A X, X+ = X + alpha X R, alpha = <R, A X R> / ||A X R||_F^2.
+ */
+rb_status mr_init(rbfgs_t *h, int n, const void *A_dev, int64_t lda, int a_is_fp64, int prec,
+                  void *stream);
+rb_status mr_step(rbfgs_t h, int nsteps);
+
+/* Spectral-norm estimate sigma used by newton_schulz_init (synchronises). */
+rb_status rbfgs_sigma(rbfgs_t h, double *sigma);
+
+rb_status rbfgs_destroy(rbfgs_t h);
+
+const char *rbfgs_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RBFGS_H */

@@ -1,0 +1,204 @@
+"""ctypes binding of include/rbfgs.h (argument marshalling only).
+
+Every function here has the name of the C entry point it wraps and does no
+arithmetic of its own.  Device buffers are passed as raw pointers (for
+example ``tensor.data_ptr()``); streams as ``cudaStream_t`` integers.  A
+failing status raises :class:`RbfgsError`; ``RB_NOTCONV`` is returned.
+"""
+import ctypes as C
+import os
+
+from . import build as _build
+
+RB_OK, RB_NOTCONV = 0, 1
+RB_EINVAL, RB_ENOMEM, RB_ECUDA, RB_ENOTSPD, RB_ENONFINITE, RB_ETIMEOUT, RB_EUNSUPPORTED = -1, -2, -3, -4, -5, -6, -7
+
+RB_FP64, RB_FP32, RB_TF32, RB_TF32X3, RB_MIXED = 0, 1, 2, 3, 4
+RB_SKETCH_GAUSS, RB_SKETCH_COORD_TRACE, RB_SKETCH_COORD_UNIFORM = 0, 1, 2
+RB_METHOD_RBFGS, RB_METHOD_ADARBFGS, RB_METHOD_NS, RB_METHOD_MR = 0, 1, 2, 3
+RB_WHAT_X, RB_WHAT_L = 0, 1
+
+PREC = {"fp64": RB_FP64, "fp32": RB_FP32, "tf32": RB_TF32, "tf32x3": RB_TF32X3, "mixed": RB_MIXED}
+
+
+class RbOpts(C.Structure):
+    _fields_ = [("method", C.c_int32), ("sketch", C.c_int32), ("q", C.c_int32), ("prec", C.c_int32),
+                ("seed", C.c_uint64), ("stream_id", C.c_uint64), ("power_iters", C.c_int32),
+                ("reserved", C.c_int32 * 7)]
+
+
+class RbfgsError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        msg = _lib().rbfgs_status_string(status).decode()
+        super().__init__(f"{where}: {msg} (status {status})")
+
+
+_LIB = None
+
+# name -> (restype, argtypes)
+_SIGS = {
+    "rbfgs_default_opts": (None, [C.c_void_p]),
+    "rbfgs_status_string": (C.c_char_p, [C.c_int]),
+    "rbfgs_init": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_void_p]),
+    "rbfgs_step": (C.c_int, [C.c_void_p, C.c_int]),
+    "adarbfgs_step": (C.c_int, [C.c_void_p, C.c_int]),
+    "rbfgs_residual": (C.c_int, [C.c_void_p, C.c_int, C.c_uint64, C.c_void_p]),
+    "rbfgs_solve": (C.c_int, [C.c_void_p, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p,
+                              C.c_void_p]),
+    "rbfgs_export": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64]),
+    "rbfgs_import": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64]),
+    "rbfgs_set_step": (C.c_int, [C.c_void_p, C.c_uint64]),
+    "rbfgs_get_step": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "rbfgs_sync": (C.c_int, [C.c_void_p]),
+    "rbfgs_draw_sketch": (C.c_int, [C.c_void_p, C.c_uint64, C.c_void_p, C.c_int64]),
+    "newton_schulz_init": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_int,
+                                     C.c_double, C.c_void_p]),
+    "newton_schulz_step": (C.c_int, [C.c_void_p, C.c_int]),
+    "mr_init": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_void_p]),
+    "mr_step": (C.c_int, [C.c_void_p, C.c_int]),
+    "rbfgs_sigma": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "rbfgs_destroy": (C.c_int, [C.c_void_p]),
+}
+
+
+def library_path():
+    return _build.LIB
+
+
+def _lib():
+    """Load the sm_103a library (building it in-tree first if it is missing).
+
+    There is no fallback: if the library cannot be built or loaded, this
+    raises, and nothing of the method runs.
+    """
+    global _LIB
+    if _LIB is None:
+        path = _build.LIB
+        if not os.path.exists(path) or _build._stale():
+            _build.build()
+        L = C.CDLL(path, mode=C.RTLD_GLOBAL)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def exported_symbols():
+    return list(_SIGS.keys())
+
+
+def _check(st, where):
+    if st < 0:
+        raise RbfgsError(st, where)
+    return st
+
+
+def _p(x):
+    return None if x is None else C.c_void_p(int(x))
+
+
+def rbfgs_status_string(status):
+    return _lib().rbfgs_status_string(status).decode()
+
+
+def rbfgs_default_opts():
+    o = RbOpts()
+    _lib().rbfgs_default_opts(C.byref(o))
+    return o
+
+
+def make_opts(method=RB_METHOD_RBFGS, sketch=RB_SKETCH_GAUSS, q=8, prec=RB_FP64, seed=0, stream_id=0,
+              power_iters=0):
+    o = rbfgs_default_opts()
+    o.method, o.sketch, o.q, o.prec = method, sketch, q, prec
+    o.seed, o.stream_id, o.power_iters = seed, stream_id, power_iters
+    return o
+
+
+def rbfgs_init(n, A_dev, lda, a_is_fp64, opts, stream=0):
+    h = C.c_void_p()
+    _check(_lib().rbfgs_init(C.byref(h), n, _p(A_dev), lda, int(a_is_fp64), C.byref(opts), _p(stream)),
+           "rbfgs_init")
+    return h
+
+
+def rbfgs_step(h, nsteps):
+    return _check(_lib().rbfgs_step(h, nsteps), "rbfgs_step")
+
+
+def adarbfgs_step(h, nsteps):
+    return _check(_lib().adarbfgs_step(h, nsteps), "adarbfgs_step")
+
+
+def rbfgs_residual(h, ncols=0, col_seed=0):
+    out = C.c_double()
+    _check(_lib().rbfgs_residual(h, ncols, col_seed, C.byref(out)), "rbfgs_residual")
+    return out.value
+
+
+def rbfgs_solve(h, tol, max_iter, check_every, check_cols, confirm_cols):
+    it = C.c_int()
+    r = C.c_double()
+    st = _check(_lib().rbfgs_solve(h, tol, max_iter, check_every, check_cols, confirm_cols, C.byref(it),
+                                   C.byref(r)), "rbfgs_solve")
+    return st, it.value, r.value
+
+
+def rbfgs_export(h, what, out_dev, ld):
+    return _check(_lib().rbfgs_export(h, what, _p(out_dev), ld), "rbfgs_export")
+
+
+def rbfgs_import(h, what, in_dev, ld):
+    return _check(_lib().rbfgs_import(h, what, _p(in_dev), ld), "rbfgs_import")
+
+
+def rbfgs_set_step(h, k):
+    return _check(_lib().rbfgs_set_step(h, k), "rbfgs_set_step")
+
+
+def rbfgs_get_step(h):
+    k = C.c_uint64()
+    _check(_lib().rbfgs_get_step(h, C.byref(k)), "rbfgs_get_step")
+    return k.value
+
+
+def rbfgs_draw_sketch(h, k, out_dev, ld):
+    return _check(_lib().rbfgs_draw_sketch(h, k, _p(out_dev), ld), "rbfgs_draw_sketch")
+
+
+def rbfgs_sync(h):
+    return _check(_lib().rbfgs_sync(h), "rbfgs_sync")
+
+
+def newton_schulz_init(n, A_dev, lda, a_is_fp64, prec, power_iters=0, sigma_override=0.0, stream=0):
+    h = C.c_void_p()
+    _check(_lib().newton_schulz_init(C.byref(h), n, _p(A_dev), lda, int(a_is_fp64), prec, power_iters,
+                                     sigma_override, _p(stream)), "newton_schulz_init")
+    return h
+
+
+def newton_schulz_step(h, nsteps):
+    return _check(_lib().newton_schulz_step(h, nsteps), "newton_schulz_step")
+
+
+def mr_init(n, A_dev, lda, a_is_fp64, prec, stream=0):
+    h = C.c_void_p()
+    _check(_lib().mr_init(C.byref(h), n, _p(A_dev), lda, int(a_is_fp64), prec, _p(stream)), "mr_init")
+    return h
+
+
+def mr_step(h, nsteps):
+    return _check(_lib().mr_step(h, nsteps), "mr_step")
+
+
+def rbfgs_sigma(h):
+    s = C.c_double()
+    _check(_lib().rbfgs_sigma(h, C.byref(s)), "rbfgs_sigma")
+    return s.value
+
+
+def rbfgs_destroy(h):
+    return _check(_lib().rbfgs_destroy(h), "rbfgs_destroy")

@@ -1,0 +1,851 @@
+// api.cu -- the C ABI of include/rbfgs.h: handles, step drivers, residual
+// monitor and solve loop.  Every arithmetic step runs in the kernels of this
+// library; the host only sequences launches and reads back scalars.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "kernels.cuh"
+#include "tc.cuh"
+
+struct rb_ctx {
+    int method = 0, sketch = 0, prec = 0;
+    int n = 0, q = 0;
+    bool f64 = false;
+    uint64_t seed = 0, stream_id = 0, k = 0;
+    cudaStream_t st = nullptr;
+    size_t esz = 4;
+
+    void *A = nullptr;  // own copy of A, ld n
+    void *X = nullptr;  // iterate: X (RBFGS/NS/MR) or L (AdaRBFGS), ld n
+    void *X2 = nullptr, *X3 = nullptr;  // n x n scratch (NS/MR/exact residual)
+
+    // n x q panels (ld n) and q x n panels (ld q)
+    void *St = nullptr, *S = nullptr, *G = nullptr, *Y = nullptr, *Sh = nullptr;
+    void *W = nullptr, *V = nullptr;
+    void *P3 = nullptr;  // RBFGS: [S | W | S], n x 3q
+    void *Cinv = nullptr, *Dinv = nullptr, *Lam = nullptr, *B1 = nullptr;  // q x q
+    double *part = nullptr, *M = nullptr, *N = nullptr, *Tm = nullptr;
+    double *dots = nullptr, *dpart = nullptr;
+    double *pv = nullptr, *pw = nullptr, *sigma = nullptr;
+    int *d_status = nullptr;
+    int *blk = nullptr, *idx = nullptr;
+    uint64_t *P = nullptr;
+    int nb = 0;
+    double host_sigma = 0.0;
+
+    // residual workspace (grown on demand)
+    int *J = nullptr;
+    int rcap = 0;
+    void *R1 = nullptr, *R2 = nullptr, *R3 = nullptr;
+    double *rpart = nullptr, *rsum = nullptr;
+
+    tc_plan *tc = nullptr;  // tensor-core plan (FP32 storage, TF32 modes)
+};
+
+static void rb_free(void *&p)
+{
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+template <typename T>
+static void rb_freet(T *&p)
+{
+    if (p) cudaFree(p);
+    p = nullptr;
+}
+
+template <typename P>
+static rb_status rb_alloc(P **p, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    if (cudaMalloc((void **)p, bytes) != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return RB_ENOMEM;
+    }
+    return RB_OK;
+}
+
+extern "C" void rbfgs_default_opts(rb_opts *o)
+{
+    if (!o) return;
+    memset(o, 0, sizeof(*o));
+    o->method = RB_METHOD_RBFGS;
+    o->sketch = RB_SKETCH_GAUSS;
+    o->q = 8;
+    o->prec = RB_FP64;
+}
+
+extern "C" const char *rbfgs_status_string(int s)
+{
+    switch (s) {
+    case RB_OK: return "ok";
+    case RB_NOTCONV: return "not converged within max_iter";
+    case RB_EINVAL: return "invalid argument";
+    case RB_ENOMEM: return "device allocation failed";
+    case RB_ECUDA: return "CUDA runtime error";
+    case RB_ENOTSPD: return "Cholesky breakdown: A not SPD or sketch rank deficient";
+    case RB_ENONFINITE: return "non-finite value";
+    case RB_ETIMEOUT: return "device wait timed out";
+    case RB_EUNSUPPORTED: return "unsupported combination";
+    default: return "unknown status";
+    }
+}
+
+static void destroy_ctx(rb_ctx *h)
+{
+    if (!h) return;
+    void **bufs[] = {&h->A, &h->X, &h->X2, &h->X3, &h->St, &h->S, &h->G, &h->Y, &h->Sh, &h->W,
+                     &h->V, &h->P3, &h->Cinv, &h->Dinv, &h->Lam, &h->B1, &h->R1, &h->R2, &h->R3};
+    for (void **b : bufs) rb_free(*b);
+    rb_freet(h->part);
+    rb_freet(h->M);
+    rb_freet(h->N);
+    rb_freet(h->Tm);
+    rb_freet(h->dots);
+    rb_freet(h->dpart);
+    rb_freet(h->pv);
+    rb_freet(h->pw);
+    rb_freet(h->sigma);
+    rb_freet(h->d_status);
+    rb_freet(h->blk);
+    rb_freet(h->idx);
+    rb_freet(h->P);
+    rb_freet(h->J);
+    rb_freet(h->rpart);
+    rb_freet(h->rsum);
+    tc_plan_destroy(h->tc);
+    delete h;
+}
+
+static rb_status status_from_device(rb_ctx *h)
+{
+    int s = 0;
+    RB_CUDA(cudaMemcpyAsync(&s, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, h->st));
+    RB_CUDA(cudaStreamSynchronize(h->st));
+    if (s & ST_NOTSPD) return RB_ENOTSPD;
+    if (s & ST_NONFINITE) return RB_ENONFINITE;
+    if (s & ST_TIMEOUT) return RB_ETIMEOUT;
+    return RB_OK;
+}
+
+// Copy the caller's A into the handle's storage type (ld n).
+static rb_status copy_in_A(rb_ctx *h, const void *A, int64_t lda, int a_is_fp64)
+{
+    const int n = h->n;
+    RB_TRY(rb_alloc(&h->A, h->esz * (size_t)n * n));
+    if (h->f64) {
+        if (a_is_fp64)
+            launch_copy2d<double, double>(h->st, n, n, (const double *)A, lda, (double *)h->A, n, 1.0);
+        else
+            launch_copy2d<float, double>(h->st, n, n, (const float *)A, lda, (double *)h->A, n, 1.0);
+    } else {
+        if (a_is_fp64)
+            launch_copy2d<double, float>(h->st, n, n, (const double *)A, lda, (float *)h->A, n, 1.0);
+        else
+            launch_copy2d<float, float>(h->st, n, n, (const float *)A, lda, (float *)h->A, n, 1.0);
+    }
+    RB_CUDA(cudaGetLastError());
+    return RB_OK;
+}
+
+// Trace weights of the contiguous coordinate blocks (exact integers, computed
+// on the host in the order s_b = sum_{i in C_b} A_ii ascending i, T = sum_b s_b
+// ascending b, w_b = max(1, floor(2^52 s_b / T)), prefix sums P).
+static rb_status build_trace_weights(rb_ctx *h)
+{
+    const int n = h->n, q = h->q;
+    double *dd = nullptr;
+    RB_TRY(rb_alloc(&dd, sizeof(double) * n));
+    if (h->f64)
+        launch_diag<double>(h->st, n, (const double *)h->A, n, dd);
+    else
+        launch_diag<float>(h->st, n, (const float *)h->A, n, dd);
+    std::vector<double> d(n);
+    cudaError_t e1 = cudaMemcpyAsync(d.data(), dd, sizeof(double) * n, cudaMemcpyDeviceToHost, h->st);
+    cudaError_t e2 = cudaStreamSynchronize(h->st);
+    cudaFree(dd);
+    if (e1 != cudaSuccess || e2 != cudaSuccess) return RB_ECUDA;
+    const int nb = (n + q - 1) / q;
+    std::vector<double> s(nb);
+    double T = 0.0;
+    for (int b = 0; b < nb; ++b) {
+        double acc = 0.0;
+        for (int i = b * q; i < n && i < (b + 1) * q; ++i) acc += d[i];
+        s[b] = acc;
+    }
+    for (int b = 0; b < nb; ++b) T += s[b];
+    if (!(T > 0.0)) return RB_ENOTSPD;
+    std::vector<uint64_t> P(nb + 1, 0);
+    for (int b = 0; b < nb; ++b) {
+        if (!(s[b] > 0.0)) return RB_ENOTSPD;
+        uint64_t w = (uint64_t)floor(ldexp(s[b] / T, 52));
+        if (w == 0) w = 1;
+        P[b + 1] = P[b] + w;
+    }
+    RB_TRY(rb_alloc(&h->P, sizeof(uint64_t) * (nb + 1)));
+    RB_CUDA(cudaMemcpyAsync(h->P, P.data(), sizeof(uint64_t) * (nb + 1), cudaMemcpyHostToDevice, h->st));
+    RB_CUDA(cudaStreamSynchronize(h->st));
+    h->nb = nb;
+    return RB_OK;
+}
+
+static rb_status alloc_common(rb_ctx *h)
+{
+    RB_TRY(rb_alloc(&h->d_status, sizeof(int)));
+    RB_CUDA(cudaMemsetAsync(h->d_status, 0, sizeof(int), h->st));
+    RB_TRY(rb_alloc(&h->rsum, sizeof(double) * 2));
+    RB_TRY(rb_alloc(&h->dots, sizeof(double) * 2));
+    RB_TRY(rb_alloc(&h->dpart, sizeof(double) * 2 * 512));
+    return RB_OK;
+}
+
+static rb_status alloc_sketch_workspace(rb_ctx *h)
+{
+    const size_t n = h->n, q = h->q, e = h->esz;
+    const size_t nq = n * q * e, qq = q * q * e;
+    const int nch = ceil_div(h->n, GRAM_CHUNK);
+    RB_TRY(rb_alloc(&h->St, nq));
+    RB_TRY(rb_alloc(&h->S, nq));
+    RB_TRY(rb_alloc(&h->G, nq));
+    RB_TRY(rb_alloc(&h->Y, nq));
+    RB_TRY(rb_alloc(&h->Sh, nq));
+    RB_TRY(rb_alloc(&h->W, nq));
+    RB_TRY(rb_alloc(&h->V, nq));
+    RB_TRY(rb_alloc(&h->Cinv, qq));
+    RB_TRY(rb_alloc(&h->Dinv, qq));
+    RB_TRY(rb_alloc(&h->Lam, qq));
+    RB_TRY(rb_alloc(&h->B1, qq));
+    RB_TRY(rb_alloc(&h->part, sizeof(double) * q * q * nch));
+    RB_TRY(rb_alloc(&h->M, sizeof(double) * q * q));
+    RB_TRY(rb_alloc(&h->N, sizeof(double) * q * q));
+    RB_TRY(rb_alloc(&h->Tm, sizeof(double) * q * q));
+    RB_TRY(rb_alloc(&h->blk, sizeof(int) * 2));
+    RB_TRY(rb_alloc(&h->idx, sizeof(int) * q));
+    if (h->method == RB_METHOD_RBFGS) RB_TRY(rb_alloc(&h->P3, 3 * nq));
+    return RB_OK;
+}
+
+static bool prec_ok(int prec) { return prec >= RB_FP64 && prec <= RB_MIXED; }
+
+extern "C" rb_status rbfgs_init(rbfgs_t *out, int n, const void *A_dev, int64_t lda, int a_is_fp64,
+                                const rb_opts *opts, void *stream)
+{
+    if (!out || !A_dev || !opts || n < 1 || lda < n) return RB_EINVAL;
+    *out = nullptr;
+    const int method = opts->method, sketch = opts->sketch, q = opts->q, prec = opts->prec;
+    if (method != RB_METHOD_RBFGS && method != RB_METHOD_ADARBFGS) return RB_EINVAL;
+    if (!prec_ok(prec)) return RB_EINVAL;
+    if (q < 1 || q > n || q > 128) return RB_EINVAL;
+    if (method == RB_METHOD_RBFGS && q > 64) return RB_EUNSUPPORTED;  // RBFGS core holds 3 q x q in smem
+    if (method == RB_METHOD_RBFGS && sketch != RB_SKETCH_GAUSS && sketch != RB_SKETCH_COORD_TRACE)
+        return RB_EUNSUPPORTED;
+    if (method == RB_METHOD_ADARBFGS && sketch != RB_SKETCH_GAUSS && sketch != RB_SKETCH_COORD_UNIFORM)
+        return RB_EUNSUPPORTED;
+    rb_ctx *h = new rb_ctx();
+    h->method = method;
+    h->sketch = sketch;
+    h->prec = prec;
+    h->n = n;
+    h->q = q;
+    h->f64 = (prec == RB_FP64);
+    h->esz = h->f64 ? 8 : 4;
+    h->seed = opts->seed;
+    h->stream_id = opts->stream_id;
+    h->st = (cudaStream_t)stream;
+    rb_status s = RB_OK;
+    do {
+        if ((s = alloc_common(h)) != RB_OK) break;
+        if ((s = copy_in_A(h, A_dev, lda, a_is_fp64)) != RB_OK) break;
+        if ((s = rb_alloc(&h->X, h->esz * (size_t)n * n)) != RB_OK) break;
+        if (h->f64)
+            launch_set_identity<double>(h->st, n, (double *)h->X, n, 1.0);
+        else
+            launch_set_identity<float>(h->st, n, (float *)h->X, n, 1.0f);
+        if ((s = alloc_sketch_workspace(h)) != RB_OK) break;
+        if (method == RB_METHOD_RBFGS && sketch == RB_SKETCH_COORD_TRACE)
+            if ((s = build_trace_weights(h)) != RB_OK) break;
+        if (!h->f64 && prec != RB_FP32) {
+            h->tc = tc_plan_create(n, q, prec);
+            if (!h->tc) {
+                s = RB_ENOMEM;
+                break;
+            }
+        }
+        if (cudaGetLastError() != cudaSuccess) {
+            s = RB_ECUDA;
+            break;
+        }
+    } while (0);
+    if (s != RB_OK) {
+        destroy_ctx(h);
+        return s;
+    }
+    *out = h;
+    return RB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// One RBFGS step (Algorithm 3 with W = A^-1, Eq. (qunac) in its expanded
+// rank-2q form).
+// ---------------------------------------------------------------------------
+template <typename T>
+static void rbfgs_step_gauss(rb_ctx *h)
+{
+    const int n = h->n, q = h->q;
+    cudaStream_t st = h->st;
+    const int *stp = h->d_status;
+    T *A = (T *)h->A, *X = (T *)h->X;
+    T *S = (T *)h->P3, *Wp = S + (size_t)n * q, *S2 = S + 2 * (size_t)n * q;
+    T *G = (T *)h->G, *Y = (T *)h->Y;
+    launch_gauss_sketch<T>(st, n, q, h->seed, h->stream_id, h->k, S, n);
+    launch_copy2d<T, T>(st, n, q, S, n, S2, n, 1.0);
+    gemm_simt<T>(st, false, false, n, q, n, T(1), A, n, S, n, T(0), G, n, stp);   // G = A S
+    launch_gram<T>(st, n, q, q, S, n, G, n, h->part, h->M);                        // M = S^T A S
+    gemm_simt<T>(st, false, false, n, q, n, T(1), X, n, G, n, T(0), Y, n, stp);   // Y = X G
+    launch_gram<T>(st, n, q, q, G, n, Y, n, h->part, h->Tm);                       // T = G^T X G
+    launch_core_rbfgs<T>(st, q, h->M, h->Tm, (T *)h->Lam, (T *)h->B1, h->d_status);
+    gemm_simt<T>(st, false, false, n, q, q, T(1), S, n, (T *)h->B1, q, T(0), Wp, n, stp);  // W = S B1
+    gemm_simt<T>(st, false, false, n, q, q, T(-1), Y, n, (T *)h->Lam, q, T(1), Wp, n, stp); //   - Y Lam
+    gemm_simt<T>(st, false, true, n, n, 2 * q, T(1), S, n, Wp, n, T(1), X, n, stp);         // X += [S W][W S]^T
+}
+
+template <typename T>
+static void rbfgs_step_coord(rb_ctx *h)
+{
+    const int n = h->n, q = h->q;
+    cudaStream_t st = h->st;
+    const int *stp = h->d_status;
+    T *A = (T *)h->A, *X = (T *)h->X, *G = (T *)h->G, *Y = (T *)h->Y, *W = (T *)h->W;
+    launch_coord_trace_draw(st, n, q, h->nb, h->P, h->seed, h->stream_id, h->k, h->blk);
+    launch_coord_gather<T>(st, n, q, A, n, h->blk, G, n, h->M, stp);               // G = A[:, C], M = A[C, C]
+    gemm_simt<T>(st, false, false, n, q, n, T(1), X, n, G, n, T(0), Y, n, stp);   // Y = X G
+    launch_gram<T>(st, n, q, q, G, n, Y, n, h->part, h->Tm);                       // T = G^T X G
+    launch_core_rbfgs<T>(st, q, h->M, h->Tm, (T *)h->Lam, (T *)h->B1, h->d_status);
+    gemm_simt<T>(st, false, false, n, q, q, T(-1), Y, n, (T *)h->Lam, q, T(0), W, n, stp);  // W = -Y Lam
+    launch_coord_add_b1<T>(st, q, h->blk, (const T *)h->B1, W, n, stp);                     //   + S B1
+    launch_coord_update<T>(st, n, q, h->blk, W, n, X, n, stp);                               // rows/cols C
+}
+
+extern "C" rb_status rbfgs_step(rbfgs_t h, int nsteps)
+{
+    if (!h || nsteps < 0 || h->method != RB_METHOD_RBFGS) return RB_EINVAL;
+    for (int s = 0; s < nsteps; ++s) {
+        if (h->sketch == RB_SKETCH_COORD_TRACE) {
+            if (h->f64)
+                rbfgs_step_coord<double>(h);
+            else
+                rbfgs_step_coord<float>(h);
+        } else {
+            if (h->f64)
+                rbfgs_step_gauss<double>(h);
+            else
+                rbfgs_step_gauss<float>(h);
+        }
+        ++h->k;
+    }
+    RB_CUDA(cudaGetLastError());
+    return RB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// One AdaRBFGS step (Algorithm 4, Eq. (Cholimprov) with lower Cholesky
+// factors: L+ = L + (S C^-T)(D^-1 S~^T - C^-1 (A S)^T L)).
+// ---------------------------------------------------------------------------
+template <typename T>
+static void ada_draw(rb_ctx *h, T *St)
+{
+    if (h->sketch == RB_SKETCH_COORD_UNIFORM) {
+        launch_floyd_draw(h->st, h->n, h->q, h->seed, h->stream_id, h->k, h->idx);
+        launch_coord_matrix<T>(h->st, h->n, h->q, h->idx, St, h->n);
+    } else {
+        launch_gauss_sketch<T>(h->st, h->n, h->q, h->seed, h->stream_id, h->k, St, h->n);
+    }
+}
+
+template <typename T>
+static void ada_step_simt(rb_ctx *h)
+{
+    const int n = h->n, q = h->q;
+    cudaStream_t st = h->st;
+    const int *stp = h->d_status;
+    T *A = (T *)h->A, *L = (T *)h->X, *St = (T *)h->St, *S = (T *)h->S, *G = (T *)h->G;
+    T *W = (T *)h->W, *V = (T *)h->V, *Sh = (T *)h->Sh, *Ci = (T *)h->Cinv, *Di = (T *)h->Dinv;
+    ada_draw<T>(h, St);
+    gemm_simt<T>(st, false, false, n, q, n, T(1), L, n, St, n, T(0), S, n, stp);   // S = L S~
+    gemm_simt<T>(st, false, false, n, q, n, T(1), A, n, S, n, T(0), G, n, stp);    // G = A S
+    launch_gram<T>(st, n, q, q, S, n, G, n, h->part, h->M);                         // S^T A S
+    launch_gram<T>(st, n, q, q, St, n, St, n, h->part, h->N);                       // S~^T S~
+    launch_core_ada<T>(st, q, h->M, h->N, Ci, Di, h->d_status);                     // C^-1, D^-1
+    gemm_simt<T>(st, true, false, q, n, n, T(1), G, n, L, n, T(0), W, q, stp);     // W = G^T L
+    gemm_simt<T>(st, false, true, q, n, q, T(1), Di, q, St, n, T(0), V, q, stp);   // V = D^-1 S~^T
+    gemm_simt<T>(st, false, false, q, n, q, T(-1), Ci, q, W, q, T(1), V, q, stp);  //   - C^-1 W
+    gemm_simt<T>(st, false, true, n, q, q, T(1), S, n, Ci, q, T(0), Sh, n, stp);   // S^ = S C^-T
+    gemm_simt<T>(st, false, false, n, n, q, T(1), Sh, n, V, q, T(1), L, n, stp);   // L += S^ V
+}
+
+static void ada_step_tc(rb_ctx *h)
+{
+    const int n = h->n, q = h->q;
+    cudaStream_t st = h->st;
+    const int *stp = h->d_status;
+    float *A = (float *)h->A, *L = (float *)h->X, *St = (float *)h->St, *S = (float *)h->S, *G = (float *)h->G;
+    float *W = (float *)h->W, *V = (float *)h->V, *Sh = (float *)h->Sh, *Ci = (float *)h->Cinv,
+          *Di = (float *)h->Dinv;
+    const int acc = (h->prec == RB_TF32) ? 1 : 3;  // split terms of the accuracy-critical products
+    const int upd = (h->prec == RB_TF32X3) ? 3 : 1;
+    ada_draw<float>(h, St);
+    tc_gemm_nk(h->tc, st, acc, TC_A_MN, n, q, n, L, n, St, n, S, n, stp);   // S = L S~   (A = L, M-contiguous)
+    tc_gemm_nk(h->tc, st, acc, TC_A_K, n, q, n, A, n, S, n, G, n, stp);     // G = A S    (A symmetric)
+    launch_gram<float>(st, n, q, q, S, n, G, n, h->part, h->M);
+    launch_gram<float>(st, n, q, q, St, n, St, n, h->part, h->N);
+    launch_core_ada<float>(st, q, h->M, h->N, Ci, Di, h->d_status);
+    tc_gemm_nk(h->tc, st, acc, TC_A_K, n, q, n, L, n, G, n, W, n, stp);     // W^T = L^T G (n x q)
+    // V = D^-1 S~^T - C^-1 W, stored q x n (ld q); W^T is n x q (ld n)
+    gemm_simt<float>(st, false, true, q, n, q, 1.f, Di, q, St, n, 0.f, V, q, stp);
+    gemm_simt<float>(st, false, true, q, n, q, -1.f, Ci, q, W, n, 1.f, V, q, stp);
+    // S^ = S C^-T stored row-major (n x q with q contiguous) for the K-major update operand
+    gemm_simt<float>(st, false, true, q, n, q, 1.f, Ci, q, S, n, 0.f, Sh, q, stp);  // S^^T = C^-1 S^T (q x n)
+    tc_update(h->tc, st, upd, n, q, Sh, V, L, n, stp);                         // L += S^ V
+}
+
+extern "C" rb_status adarbfgs_step(rbfgs_t h, int nsteps)
+{
+    if (!h || nsteps < 0 || h->method != RB_METHOD_ADARBFGS) return RB_EINVAL;
+    for (int s = 0; s < nsteps; ++s) {
+        if (h->f64)
+            ada_step_simt<double>(h);
+        else if (h->prec == RB_FP32 || !h->tc)
+            ada_step_simt<float>(h);
+        else
+            ada_step_tc(h);
+        ++h->k;
+    }
+    RB_CUDA(cudaGetLastError());
+    return RB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Residual monitor.
+// ---------------------------------------------------------------------------
+static void host_floyd(uint64_t seed, int n, int m, std::vector<int> &out)
+{
+    out.assign(m, 0);
+    for (int i = 0; i < m; ++i) {
+        const uint32_t t = (uint32_t)(n - m + i);
+        const u32x4 w = philox10((uint32_t)i, TAG_COLS, 0u, 0u, (uint32_t)seed, (uint32_t)(seed >> 32));
+        const int d = (int)(((uint64_t)w.x * (uint64_t)(t + 1u)) >> 32);
+        bool seen = false;
+        for (int a = 0; a < i; ++a) seen |= (out[a] == d);
+        out[i] = seen ? (int)t : d;
+    }
+    std::sort(out.begin(), out.end());
+}
+
+static rb_status ensure_resid_ws(rb_ctx *h, int m)
+{
+    if (m <= h->rcap) return RB_OK;
+    rb_free(h->R1);
+    rb_free(h->R2);
+    rb_free(h->R3);
+    rb_freet(h->J);
+    rb_freet(h->rpart);
+    h->rcap = 0;
+    const size_t bytes = h->esz * (size_t)h->n * m;
+    RB_TRY(rb_alloc(&h->R1, bytes));
+    RB_TRY(rb_alloc(&h->R2, bytes));
+    RB_TRY(rb_alloc(&h->R3, bytes));
+    RB_TRY(rb_alloc(&h->J, sizeof(int) * m));
+    RB_TRY(rb_alloc(&h->rpart, sizeof(double) * 32 * (size_t)m));
+    h->rcap = m;
+    return RB_OK;
+}
+
+template <typename T>
+static void resid_products(rb_ctx *h, int m, const T *Y, T *Z1, T *Z)
+{
+    const int n = h->n;
+    cudaStream_t st = h->st;
+    const T *X = (const T *)h->X;
+    const bool tc = (!h->f64 && h->tc && h->prec != RB_FP32);
+    if (h->method == RB_METHOD_ADARBFGS) {
+        if constexpr (sizeof(T) == 4) {
+            if (tc) {
+                // residual products always at ~FP32 accuracy (3-term split)
+                tc_gemm_nk(h->tc, st, 3, TC_A_K, n, m, n, (const float *)X, n, (const float *)Y, n, (float *)Z1, n,
+                           nullptr);
+                tc_gemm_nk(h->tc, st, 3, TC_A_MN, n, m, n, (const float *)X, n, (const float *)Z1, n, (float *)Z, n,
+                           nullptr);
+                return;
+            }
+        }
+        gemm_simt<T>(st, true, false, n, m, n, T(1), X, n, Y, n, T(0), Z1, n, nullptr);  // L^T A e_J
+        gemm_simt<T>(st, false, false, n, m, n, T(1), X, n, Z1, n, T(0), Z, n, nullptr); // L L^T A e_J
+    } else {
+        gemm_simt<T>(st, false, false, n, m, n, T(1), X, n, Y, n, T(0), Z, n, nullptr);  // X A e_J
+    }
+}
+
+template <typename T>
+static void resid_launch(rb_ctx *h, bool exact, int m, const int *J)
+{
+    const int n = h->n;
+    const T *Y = (const T *)h->A;  // exact: Y = A (all columns)
+    if (!exact) {
+        launch_gather_cols<T>(h->st, n, m, (const T *)h->A, n, J, (T *)h->R1, n);
+        Y = (const T *)h->R1;
+    }
+    T *Z1 = (T *)h->R3, *Z = (T *)h->R2;
+    resid_products<T>(h, m, Y, Z1, Z);
+    launch_resid_sumsq<T>(h->st, n, m, Z, n, J, h->rpart, h->rsum);
+}
+
+extern "C" rb_status rbfgs_residual(rbfgs_t h, int ncols, uint64_t col_seed, double *out)
+{
+    if (!h || !out || ncols < 0) return RB_EINVAL;
+    const int n = h->n;
+    const bool exact = (ncols == 0 || ncols >= n);
+    const int m = exact ? n : ncols;
+    RB_TRY(ensure_resid_ws(h, m));
+    cudaStream_t st = h->st;
+    const int *J = nullptr;
+    std::vector<int> hj;
+    if (!exact) {
+        host_floyd(col_seed, n, m, hj);
+        RB_CUDA(cudaMemcpyAsync(h->J, hj.data(), sizeof(int) * m, cudaMemcpyHostToDevice, st));
+        J = h->J;
+    }
+    if (h->f64)
+        resid_launch<double>(h, exact, m, J);
+    else
+        resid_launch<float>(h, exact, m, J);
+    RB_CUDA(cudaGetLastError());
+    double sum = 0.0;
+    RB_CUDA(cudaMemcpyAsync(&sum, h->rsum, sizeof(double), cudaMemcpyDeviceToHost, st));
+    RB_CUDA(cudaStreamSynchronize(st));
+    RB_TRY(status_from_device(h));
+    const double r = sqrt(sum / m);
+    if (!isfinite(r)) return RB_ENONFINITE;
+    *out = r;
+    return RB_OK;
+}
+
+extern "C" rb_status rbfgs_solve(rbfgs_t h, double tol, int max_iter, int check_every, int check_cols,
+                                 int confirm_cols, int *iters, double *resid)
+{
+    if (!h || max_iter < 0 || check_every < 1 || check_cols < 0) return RB_EINVAL;
+    int done = 0;
+    double r = INFINITY;
+    uint64_t col_seed = 0x5eed0000ull;
+    while (done < max_iter) {
+        const int chunk = std::min(check_every, max_iter - done);
+        rb_status s = RB_OK;
+        if (h->method == RB_METHOD_RBFGS)
+            s = rbfgs_step(h, chunk);
+        else if (h->method == RB_METHOD_ADARBFGS)
+            s = adarbfgs_step(h, chunk);
+        else if (h->method == RB_METHOD_NS)
+            s = newton_schulz_step(h, chunk);
+        else
+            s = mr_step(h, chunk);
+        if (s != RB_OK) return s;
+        done += chunk;
+        RB_TRY(rbfgs_residual(h, check_cols, col_seed++, &r));
+        if (r <= tol) {
+            double rc = r;
+            if (confirm_cols != check_cols) RB_TRY(rbfgs_residual(h, confirm_cols, col_seed++, &rc));
+            r = rc;
+            if (rc <= tol) break;
+        }
+    }
+    if (iters) *iters = done;
+    if (resid) *resid = r;
+    return (r <= tol) ? RB_OK : RB_NOTCONV;
+}
+
+extern "C" rb_status rbfgs_export(rbfgs_t h, int what, void *out, int64_t ld)
+{
+    if (!h || !out || ld < h->n) return RB_EINVAL;
+    const int n = h->n;
+    if (what == RB_WHAT_L) {
+        if (h->method != RB_METHOD_ADARBFGS) return RB_EINVAL;
+    } else if (what != RB_WHAT_X) {
+        return RB_EINVAL;
+    }
+    if (what == RB_WHAT_X && h->method == RB_METHOD_ADARBFGS) {
+        if (h->f64)
+            gemm_simt<double>(h->st, false, true, n, n, n, 1.0, (const double *)h->X, n, (const double *)h->X, n,
+                              0.0, (double *)out, ld, nullptr);
+        else
+            gemm_simt<float>(h->st, false, true, n, n, n, 1.f, (const float *)h->X, n, (const float *)h->X, n, 0.f,
+                             (float *)out, ld, nullptr);
+    } else {
+        if (h->f64)
+            launch_copy2d<double, double>(h->st, n, n, (const double *)h->X, n, (double *)out, ld, 1.0);
+        else
+            launch_copy2d<float, float>(h->st, n, n, (const float *)h->X, n, (float *)out, ld, 1.0);
+    }
+    RB_CUDA(cudaGetLastError());
+    return RB_OK;
+}
+
+extern "C" rb_status rbfgs_import(rbfgs_t h, int what, const void *in, int64_t ld)
+{
+    if (!h || !in || ld < h->n) return RB_EINVAL;
+    const bool want_l = (h->method == RB_METHOD_ADARBFGS);
+    if ((what == RB_WHAT_L) != want_l) return RB_EINVAL;
+    const int n = h->n;
+    if (h->f64)
+        launch_copy2d<double, double>(h->st, n, n, (const double *)in, ld, (double *)h->X, n, 1.0);
+    else
+        launch_copy2d<float, float>(h->st, n, n, (const float *)in, ld, (float *)h->X, n, 1.0);
+    RB_CUDA(cudaMemsetAsync(h->d_status, 0, sizeof(int), h->st));
+    RB_CUDA(cudaGetLastError());
+    return RB_OK;
+}
+
+extern "C" rb_status rbfgs_set_step(rbfgs_t h, uint64_t k)
+{
+    if (!h) return RB_EINVAL;
+    h->k = k;
+    return RB_OK;
+}
+
+extern "C" rb_status rbfgs_get_step(rbfgs_t h, uint64_t *k)
+{
+    if (!h || !k) return RB_EINVAL;
+    *k = h->k;
+    return RB_OK;
+}
+
+template <typename T>
+static void coord_block_matrix(rb_ctx *h, uint64_t k, T *out, int64_t ld);
+
+extern "C" rb_status rbfgs_draw_sketch(rbfgs_t h, uint64_t k, void *out, int64_t ld)
+{
+    if (!h || !out || ld < h->n || h->q < 1) return RB_EINVAL;
+    const int n = h->n, q = h->q;
+    if (h->method == RB_METHOD_RBFGS && h->sketch == RB_SKETCH_COORD_TRACE) {
+        if (h->f64)
+            coord_block_matrix<double>(h, k, (double *)out, ld);
+        else
+            coord_block_matrix<float>(h, k, (float *)out, ld);
+    } else if (h->sketch == RB_SKETCH_COORD_UNIFORM) {
+        launch_floyd_draw(h->st, n, q, h->seed, h->stream_id, k, h->idx);
+        if (h->f64)
+            launch_coord_matrix<double>(h->st, n, q, h->idx, (double *)out, ld);
+        else
+            launch_coord_matrix<float>(h->st, n, q, h->idx, (float *)out, ld);
+    } else {
+        if (h->f64)
+            launch_gauss_sketch<double>(h->st, n, q, h->seed, h->stream_id, k, (double *)out, ld);
+        else
+            launch_gauss_sketch<float>(h->st, n, q, h->seed, h->stream_id, k, (float *)out, ld);
+    }
+    RB_CUDA(cudaGetLastError());
+    return RB_OK;
+}
+
+template <typename T>
+static void coord_block_matrix(rb_ctx *h, uint64_t k, T *out, int64_t ld)
+{
+    const int n = h->n, q = h->q;
+    launch_coord_trace_draw(h->st, n, q, h->nb, h->P, h->seed, h->stream_id, k, h->blk);
+    // 0/1 matrix from the block: column c has a one in row first + c (c < size)
+    launch_block_matrix<T>(h->st, n, q, h->blk, out, ld);
+}
+
+extern "C" rb_status rbfgs_sync(rbfgs_t h)
+{
+    if (!h) return RB_EINVAL;
+    return status_from_device(h);
+}
+
+// ---------------------------------------------------------------------------
+// Comparison methods (Sec. 10).
+// ---------------------------------------------------------------------------
+static rb_status init_dense_method(rbfgs_t *out, int method, int n, const void *A_dev, int64_t lda, int a_is_fp64,
+                                   int prec, void *stream, rb_ctx **hp)
+{
+    if (!out || !A_dev || n < 1 || lda < n || !prec_ok(prec)) return RB_EINVAL;
+    *out = nullptr;
+    rb_ctx *h = new rb_ctx();
+    h->method = method;
+    h->prec = prec;
+    h->n = n;
+    h->q = 0;
+    h->f64 = (prec == RB_FP64);
+    h->esz = h->f64 ? 8 : 4;
+    h->st = (cudaStream_t)stream;
+    rb_status s = RB_OK;
+    do {
+        if ((s = alloc_common(h)) != RB_OK) break;
+        if ((s = copy_in_A(h, A_dev, lda, a_is_fp64)) != RB_OK) break;
+        const size_t nn = h->esz * (size_t)n * n;
+        if ((s = rb_alloc(&h->X, nn)) != RB_OK) break;
+        if ((s = rb_alloc(&h->X2, nn)) != RB_OK) break;
+        if ((s = rb_alloc(&h->X3, nn)) != RB_OK) break;
+        if ((s = rb_alloc(&h->pv, sizeof(double) * n)) != RB_OK) break;
+        if ((s = rb_alloc(&h->pw, sizeof(double) * n)) != RB_OK) break;
+        if ((s = rb_alloc(&h->sigma, sizeof(double))) != RB_OK) break;
+        if (!h->f64 && prec != RB_FP32) {
+            h->tc = tc_plan_create(n, 0, prec);
+            if (!h->tc) {
+                s = RB_ENOMEM;
+                break;
+            }
+        }
+    } while (0);
+    if (s != RB_OK) {
+        destroy_ctx(h);
+        return s;
+    }
+    *hp = h;
+    return RB_OK;
+}
+
+extern "C" rb_status newton_schulz_init(rbfgs_t *out, int n, const void *A_dev, int64_t lda, int a_is_fp64,
+                                        int prec, int power_iters, double sigma_override, void *stream)
+{
+    rb_ctx *h = nullptr;
+    RB_TRY(init_dense_method(out, RB_METHOD_NS, n, A_dev, lda, a_is_fp64, prec, stream, &h));
+    double sigma = sigma_override;
+    if (!(sigma > 0.0)) {
+        const int iters = power_iters > 0 ? power_iters : 100;
+        if (h->f64)
+            launch_power_iteration<double>(h->st, n, (const double *)h->A, n, iters, h->pv, h->pw, h->sigma);
+        else
+            launch_power_iteration<float>(h->st, n, (const float *)h->A, n, iters, h->pv, h->pw, h->sigma);
+        if (cudaMemcpyAsync(&sigma, h->sigma, sizeof(double), cudaMemcpyDeviceToHost, h->st) != cudaSuccess ||
+            cudaStreamSynchronize(h->st) != cudaSuccess) {
+            destroy_ctx(h);
+            return RB_ECUDA;
+        }
+    }
+    h->host_sigma = sigma;
+    const double scale = 0.99 / (sigma * sigma);
+    // X0 = 0.99 A^T / sigma^2 (A symmetric)
+    if (h->f64)
+        launch_copy2d<double, double>(h->st, n, n, (const double *)h->A, n, (double *)h->X, n, scale);
+    else
+        launch_copy2d<float, float>(h->st, n, n, (const float *)h->A, n, (float *)h->X, n, scale);
+    if (cudaGetLastError() != cudaSuccess) {
+        destroy_ctx(h);
+        return RB_ECUDA;
+    }
+    *out = h;
+    return RB_OK;
+}
+
+template <typename T>
+static void ns_step_impl(rb_ctx *h)
+{
+    const int n = h->n;
+    cudaStream_t st = h->st;
+    T *A = (T *)h->A, *X = (T *)h->X, *P = (T *)h->X2, *Xn = (T *)h->X3;
+    if constexpr (sizeof(T) == 4) {
+        if (h->tc) {
+            const int terms = (h->prec == RB_TF32) ? 1 : 3;
+            tc_gemm_nk(h->tc, st, terms, TC_A_K, n, n, n, (const float *)A, n, (const float *)X, n, (float *)P, n,
+                       nullptr);                                                                   // P = A X
+            tc_gemm_nk_axpby(h->tc, st, terms, TC_A_MN, n, n, n, -1.f, (const float *)X, n, (const float *)P, n, 2.f,
+                             (const float *)X, n, (float *)Xn, n);                                 // 2X - X P
+            std::swap(h->X, h->X3);
+            return;
+        }
+    }
+    gemm_simt<T>(st, false, false, n, n, n, T(1), A, n, X, n, T(0), P, n, nullptr);      // P = A X
+    launch_copy2d<T, T>(st, n, n, X, n, Xn, n, 2.0);                                       // Xn = 2 X
+    gemm_simt<T>(st, false, false, n, n, n, T(-1), X, n, P, n, T(1), Xn, n, nullptr);    // Xn -= X P
+    std::swap(h->X, h->X3);
+}
+
+extern "C" rb_status newton_schulz_step(rbfgs_t h, int nsteps)
+{
+    if (!h || nsteps < 0 || h->method != RB_METHOD_NS) return RB_EINVAL;
+    for (int s = 0; s < nsteps; ++s) {
+        if (h->f64)
+            ns_step_impl<double>(h);
+        else
+            ns_step_impl<float>(h);
+        ++h->k;
+    }
+    RB_CUDA(cudaGetLastError());
+    return RB_OK;
+}
+
+extern "C" rb_status rbfgs_sigma(rbfgs_t h, double *sigma)
+{
+    if (!h || !sigma || h->method != RB_METHOD_NS) return RB_EINVAL;
+    *sigma = h->host_sigma;
+    return RB_OK;
+}
+
+extern "C" rb_status mr_init(rbfgs_t *out, int n, const void *A_dev, int64_t lda, int a_is_fp64, int prec,
+                             void *stream)
+{
+    rb_ctx *h = nullptr;
+    RB_TRY(init_dense_method(out, RB_METHOD_MR, n, A_dev, lda, a_is_fp64, prec, stream, &h));
+    // X0 = (Tr A / Tr A A^T) I: Tr A and ||A||_F^2 summed in FP64 on the device
+    if (h->f64) {
+        launch_set_identity<double>(h->st, n, (double *)h->X2, n, 1.0);
+        launch_mr_dots<double>(h->st, n, (const double *)h->X2, n, (const double *)h->A, n, h->dpart, h->dots);
+    } else {
+        launch_set_identity<float>(h->st, n, (float *)h->X2, n, 1.0f);
+        launch_mr_dots<float>(h->st, n, (const float *)h->X2, n, (const float *)h->A, n, h->dpart, h->dots);
+    }
+    double d[2] = {0, 0};
+    if (cudaMemcpyAsync(d, h->dots, sizeof(d), cudaMemcpyDeviceToHost, h->st) != cudaSuccess ||
+        cudaStreamSynchronize(h->st) != cudaSuccess || !(d[1] > 0.0)) {
+        destroy_ctx(h);
+        return RB_ECUDA;
+    }
+    if (h->f64)
+        launch_set_identity<double>(h->st, n, (double *)h->X, n, d[0] / d[1]);
+    else
+        launch_set_identity<float>(h->st, n, (float *)h->X, n, (float)(d[0] / d[1]));
+    *out = h;
+    return RB_OK;
+}
+
+template <typename T>
+static void mr_step_impl(rb_ctx *h)
+{
+    const int n = h->n;
+    cudaStream_t st = h->st;
+    T *A = (T *)h->A, *X = (T *)h->X, *R = (T *)h->X2, *Q = (T *)h->X3;
+    gemm_simt<T>(st, false, false, n, n, n, T(1), A, n, X, n, T(0), R, n, nullptr);   // A X
+    launch_i_minus<T>(st, n, R, n);                                                      // R = I - A X
+    gemm_simt<T>(st, false, false, n, n, n, T(1), X, n, R, n, T(0), Q, n, nullptr);   // X R
+    T *AQ = (T *)h->R1;
+    gemm_simt<T>(st, false, false, n, n, n, T(1), A, n, Q, n, T(0), AQ, n, nullptr);  // A X R
+    launch_mr_dots<T>(st, n, R, n, AQ, n, h->dpart, h->dots);                          // <R, AXR>, ||AXR||^2
+    launch_axpy_dev<T>(st, n, h->dots, Q, n, X, n);                                    // X += alpha X R
+}
+
+extern "C" rb_status mr_step(rbfgs_t h, int nsteps)
+{
+    if (!h || nsteps < 0 || h->method != RB_METHOD_MR) return RB_EINVAL;
+    RB_TRY(ensure_resid_ws(h, h->n));
+    for (int s = 0; s < nsteps; ++s) {
+        if (h->f64)
+            mr_step_impl<double>(h);
+        else
+            mr_step_impl<float>(h);
+        ++h->k;
+    }
+    RB_CUDA(cudaGetLastError());
+    return RB_OK;
+}
+
+extern "C" rb_status rbfgs_destroy(rbfgs_t h)
+{
+    if (!h) return RB_EINVAL;
+    cudaStreamSynchronize(h->st);
+    destroy_ctx(h);
+    return RB_OK;
+}

@@ -1,0 +1,61 @@
+// kernels.cuh -- launchers of the sm_103a kernels (host-callable).
+#pragma once
+#include "common.cuh"
+
+constexpr int GRAM_CHUNK = 128;  // rows per FP32 Gram partial (summed in FP64)
+
+// sketch.cu
+template <typename T>
+void launch_gauss_sketch(cudaStream_t, int n, int q, uint64_t seed, uint64_t stream, uint64_t k, T *S, int64_t lds);
+void launch_coord_trace_draw(cudaStream_t, int n, int q, int nb, const uint64_t *P, uint64_t seed, uint64_t stream,
+                             uint64_t k, int *blk);
+void launch_floyd_draw(cudaStream_t, int n, int q, uint64_t seed, uint64_t stream, uint64_t k, int *idx);
+template <typename T>
+void launch_coord_matrix(cudaStream_t, int n, int q, const int *idx, T *S, int64_t lds);
+template <typename T>
+void launch_block_matrix(cudaStream_t, int n, int q, const int *blk, T *S, int64_t lds);
+
+// gemm_simt.cu: C = alpha op(A) op(B) + beta C (column-major)
+template <typename T>
+void gemm_simt(cudaStream_t, bool ta, bool tb, int M, int N, int K, T alpha, const T *A, int64_t lda, const T *B,
+               int64_t ldb, T beta, T *C, int64_t ldc, const int *status);
+
+// small.cu
+template <typename T>
+void launch_gram(cudaStream_t, int n, int p, int r, const T *X, int64_t ldx, const T *Y, int64_t ldy, double *part,
+                 double *out);
+template <typename T>
+void launch_core_ada(cudaStream_t, int q, const double *M, const double *N, T *Cinv, T *Dinv, int *status);
+template <typename T>
+void launch_core_rbfgs(cudaStream_t, int q, const double *M, const double *Tm, T *Lam, T *B1, int *status);
+template <typename T>
+void launch_set_identity(cudaStream_t, int n, T *X, int64_t ld, T diag);
+template <typename Ti, typename To>
+void launch_copy2d(cudaStream_t, int rows, int cols, const Ti *X, int64_t ldx, To *Y, int64_t ldy, double alpha);
+template <typename T>
+void launch_diag(cudaStream_t, int n, const T *A, int64_t lda, double *d);
+
+// aux.cu
+template <typename T>
+void launch_resid_sumsq(cudaStream_t, int n, int m, const T *Z, int64_t ldz, const int *J, double *part,
+                        double *out);
+template <typename T>
+void launch_gather_cols(cudaStream_t, int n, int m, const T *A, int64_t lda, const int *J, T *Y, int64_t ldy);
+template <typename T>
+void launch_coord_gather(cudaStream_t, int n, int q, const T *A, int64_t lda, const int *blk, T *G, int64_t ldg,
+                         double *Mpad, const int *status);
+template <typename T>
+void launch_coord_add_b1(cudaStream_t, int q, const int *blk, const T *B1, T *W, int64_t ldw, const int *status);
+template <typename T>
+void launch_coord_update(cudaStream_t, int n, int q, const int *blk, const T *W, int64_t ldw, T *X, int64_t ldx,
+                         const int *status);
+template <typename T>
+void launch_mr_dots(cudaStream_t, int n, const T *P, int64_t ldp, const T *Q, int64_t ldq, double *part,
+                    double *out);
+template <typename T>
+void launch_i_minus(cudaStream_t, int n, T *P, int64_t ld);
+template <typename T>
+void launch_axpy_dev(cudaStream_t, int n, const double *dots, const T *D, int64_t ldd, T *X, int64_t ldx);
+template <typename T>
+void launch_power_iteration(cudaStream_t, int n, const T *A, int64_t lda, int iters, double *v, double *w,
+                            double *sigma);

@@ -1,0 +1,533 @@
+// tc.cu -- tcgen05 / TMA GEMM for sm_103a (see tc.cuh for the contract).
+//
+// One CTA computes a 128 x BN tile of C over a range of K (split-K partials
+// are summed afterwards in a fixed order, so results are deterministic).
+// Warp roles, 256 threads:
+//   warp 0      TMA producer: streams 128 x 32 tiles of op(A) and BN x 32
+//               tiles of B (FP32, 128-byte swizzle) into a STAGES-deep ring;
+//   warp 1      allocates the TMEM accumulator (BN columns x 128 lanes) and
+//               issues tcgen05.mma kind::tf32 from one elected thread;
+//   warps 4-7   (terms = 3) split each landed tile in place into hi (top 11
+//               significand bits) and lo = x - hi, then (all terms) drain the
+//               accumulator with tcgen05.ld and apply alpha/beta.
+// Every mbarrier wait is bounded (about two seconds of SM clock); a wait
+// that gives up records ST_TIMEOUT in the caller's status word and the CTA
+// winds down instead of hanging.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "kernels.cuh"
+#include "tc.cuh"
+
+namespace {
+
+constexpr int BM = 128;
+constexpr int BK = 32;  // 32 FP32 = one 128-byte swizzle row
+constexpr int A_TILE_BYTES = BM * BK * 4;
+constexpr long long WAIT_LIMIT_CYCLES = 1ll << 32;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: false (and ST_TIMEOUT recorded, abort flag raised) when the
+// phase does not complete within WAIT_LIMIT_CYCLES.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err, volatile int *abort_flag)
+{
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*abort_flag) return false;
+        if (clock64() - t0 > WAIT_LIMIT_CYCLES) {
+            if (err) atomicOr(err, ST_TIMEOUT);
+            *abort_flag = 1;
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            dst),
+        "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
+        : "memory");
+}
+
+// Shared-memory matrix descriptor (tcgen05): start, leading / stride byte
+// offsets (>> 4), version 1, 128-byte swizzle.
+__device__ __forceinline__ uint64_t umma_desc(uint32_t addr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;  // descriptor version for tcgen05
+    d |= (uint64_t)2 << 61;  // SWIZZLE_128B
+    return d;
+}
+
+// Instruction descriptor, kind::tf32: D F32, A/B TF32, A K- or MN-major,
+// B K-major, N = BN, M = 128.
+__host__ __device__ constexpr uint32_t idesc_tf32(int n, int a_mn)
+{
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)a_mn << 15) | ((uint32_t)(n >> 3) << 17) |
+           ((uint32_t)(BM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// 32 lanes x 16 columns of 32-bit accumulator -> 16 registers per thread.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+template <int BN, int TERMS>
+struct Cfg {
+    static constexpr int A_BYTES = A_TILE_BYTES;
+    static constexpr int B_BYTES = BN * BK * 4;
+    static constexpr int STAGE_BYTES = (A_BYTES + B_BYTES) * (TERMS == 3 ? 2 : 1);
+    static constexpr int STAGES_RAW = (200 * 1024) / STAGE_BYTES;
+    static constexpr int STAGES = STAGES_RAW > 8 ? 8 : STAGES_RAW;
+    static constexpr int TMEM_COLS = BN < 32 ? 32 : BN;
+    static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 /*align*/ + 512 /*barriers*/;
+    static_assert(STAGES >= 2, "pipeline needs two stages");
+};
+
+template <int BN, int TERMS>
+__global__ void __launch_bounds__(256, 1)
+k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int a_mn, int M, int N,
+          int nkb, int kb_per_split, float alpha, float beta, const float *Cin, int64_t ldcin, float *C, int64_t ldc,
+          float *part, const int *status, int *err)
+{
+    using CF = Cfg<BN, TERMS>;
+    constexpr int STAGES = CF::STAGES;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    if (status_bad(status)) return;  // uniform: every thread reads the same word
+
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *bar_area = smem + STAGES * CF::STAGE_BYTES;
+    uint64_t *full = (uint64_t *)bar_area;
+    uint64_t *conv = full + STAGES;
+    uint64_t *empty = conv + STAGES;
+    uint64_t *accf = empty + STAGES;
+    uint32_t *tmem_slot = (uint32_t *)(accf + 1);
+    volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * BM;
+    const int n0 = blockIdx.y * BN;
+    const int kb0 = blockIdx.z * kb_per_split;
+    const int nk = min(nkb - kb0, kb_per_split);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(smem_u32(&full[s]), 1);
+            mbar_init(smem_u32(&conv[s]), 128);
+            mbar_init(smem_u32(&empty[s]), 1);
+        }
+        mbar_init(smem_u32(accf), 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"((uint32_t)CF::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    auto stage_a = [&](int s) { return smem + s * CF::STAGE_BYTES; };
+    auto stage_b = [&](int s) { return smem + s * CF::STAGE_BYTES + CF::A_BYTES; };
+    auto stage_alo = [&](int s) { return smem + s * CF::STAGE_BYTES + CF::A_BYTES + CF::B_BYTES; };
+    auto stage_blo = [&](int s) { return smem + s * CF::STAGE_BYTES + 2 * CF::A_BYTES + CF::B_BYTES; };
+
+    if (warp == 0) {
+        // ---------------- TMA producer ----------------
+        if (lane == 0) {
+            for (int i = 0; i < nk; ++i) {
+                const int s = i % STAGES;
+                if (i >= STAGES && !mbar_wait(smem_u32(&empty[s]), ((i / STAGES) - 1) & 1, err, abort_flag)) break;
+                const uint32_t fb = smem_u32(&full[s]);
+                mbar_expect_tx(fb, CF::A_BYTES + CF::B_BYTES);
+                const int k = (kb0 + i) * BK;
+                if (a_mn) {
+#pragma unroll
+                    for (int c = 0; c < BM / 32; ++c)
+                        tma_load_2d(smem_u32(stage_a(s) + c * 4096), &tmA, m0 + 32 * c, k, fb);
+                } else {
+                    tma_load_2d(smem_u32(stage_a(s)), &tmA, k, m0, fb);
+                }
+                tma_load_2d(smem_u32(stage_b(s)), &tmB, k, n0, fb);
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            const uint32_t idesc = idesc_tf32(BN, a_mn);
+            bool ok = true;
+            for (int i = 0; i < nk && ok; ++i) {
+                const int s = i % STAGES;
+                const uint32_t wb = (TERMS == 3) ? smem_u32(&conv[s]) : smem_u32(&full[s]);
+                if (!mbar_wait(wb, (i / STAGES) & 1, err, abort_flag)) {
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t a_hi = smem_u32(stage_a(s)), b_hi = smem_u32(stage_b(s));
+                const uint32_t a_lo = smem_u32(stage_alo(s)), b_lo = smem_u32(stage_blo(s));
+#pragma unroll
+                for (int kk = 0; kk < BK / 8; ++kk) {
+                    // A: K-major advances 32 B within the swizzle row; MN-major
+                    // advances one 8-row (1024 B) group; M-chunks 4 KB apart.
+                    const uint32_t aoff = a_mn ? kk * 1024 : kk * 32;
+                    const uint32_t alb = a_mn ? 4096 : 16, asb = 1024;
+                    const uint64_t da_hi = umma_desc(a_hi + aoff, alb, asb);
+                    const uint64_t db_hi = umma_desc(b_hi + kk * 32, 16, 1024);
+                    const uint32_t first = (i == 0 && kk == 0) ? 0u : 1u;
+                    if (TERMS == 3) {
+                        const uint64_t da_lo = umma_desc(a_lo + aoff, alb, asb);
+                        const uint64_t db_lo = umma_desc(b_lo + kk * 32, 16, 1024);
+                        mma_tf32(tmem, da_lo, db_hi, idesc, first);
+                        mma_tf32(tmem, da_hi, db_lo, idesc, 1u);
+                        mma_tf32(tmem, da_hi, db_hi, idesc, 1u);
+                    } else {
+                        mma_tf32(tmem, da_hi, db_hi, idesc, first);
+                    }
+                }
+                mma_commit(smem_u32(&empty[s]));
+            }
+            if (ok) mma_commit(smem_u32(accf));
+        }
+    } else if (warp >= 4) {
+        const int t = threadIdx.x - 128;  // 0..127
+        // ---------------- hi/lo split (terms = 3) ----------------
+        if (TERMS == 3) {
+            for (int i = 0; i < nk; ++i) {
+                const int s = i % STAGES;
+                if (!mbar_wait(smem_u32(&full[s]), (i / STAGES) & 1, err, abort_flag)) break;
+                float4 *a = (float4 *)stage_a(s);
+                float4 *alo = (float4 *)stage_alo(s);
+                for (int e = t; e < CF::A_BYTES / 16; e += 128) {
+                    float4 v = a[e], h, l;
+                    h.x = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
+                    h.y = __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u);
+                    h.z = __uint_as_float(__float_as_uint(v.z) & 0xFFFFE000u);
+                    h.w = __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u);
+                    l.x = v.x - h.x;
+                    l.y = v.y - h.y;
+                    l.z = v.z - h.z;
+                    l.w = v.w - h.w;
+                    a[e] = h;
+                    alo[e] = l;
+                }
+                float4 *b = (float4 *)stage_b(s);
+                float4 *blo = (float4 *)stage_blo(s);
+                for (int e = t; e < CF::B_BYTES / 16; e += 128) {
+                    float4 v = b[e], h, l;
+                    h.x = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
+                    h.y = __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u);
+                    h.z = __uint_as_float(__float_as_uint(v.z) & 0xFFFFE000u);
+                    h.w = __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u);
+                    l.x = v.x - h.x;
+                    l.y = v.y - h.y;
+                    l.z = v.z - h.z;
+                    l.w = v.w - h.w;
+                    b[e] = h;
+                    blo[e] = l;
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive(smem_u32(&conv[s]));
+            }
+        }
+        // ---------------- epilogue ----------------
+        const bool got = mbar_wait(smem_u32(accf), 0, err, abort_flag);
+        tc_fence_after();
+        if (got) {
+            const int wq = warp & 3;  // TMEM lanes 32 wq .. 32 wq + 31
+            const int m = m0 + 32 * wq + lane;
+            const bool split = (part != nullptr);
+            for (int c0 = 0; c0 < BN; c0 += 16) {
+                uint32_t r[16];
+                tmem_ld16(tmem + ((uint32_t)(32 * wq) << 16) + (uint32_t)c0, r);
+                if (m < M) {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int nn = n0 + c0 + j;
+                        if (nn >= N) break;
+                        const float v = __uint_as_float(r[j]);
+                        if (split) {
+                            part[(size_t)blockIdx.z * M * N + m + (size_t)nn * M] = v;
+                        } else {
+                            float o = alpha * v;
+                            if (beta != 0.f) o = fmaf(beta, Cin[m + (int64_t)nn * ldcin], o);
+                            C[m + (int64_t)nn * ldc] = o;
+                        }
+                    }
+                }
+            }
+        }
+        tc_fence_before();
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"((uint32_t)CF::TMEM_COLS)
+                     : "memory");
+    }
+}
+
+// C = alpha sum_z part[z] + beta Cin, fixed order over z.
+__global__ void k_splitk_reduce(int M, int N, int splits, const float *part, float alpha, float beta,
+                                const float *Cin, int64_t ldcin, float *C, int64_t ldc)
+{
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    const int nn = blockIdx.y;
+    if (m >= M) return;
+    float s = 0.f;
+    for (int z = 0; z < splits; ++z) s += part[(size_t)z * M * N + m + (size_t)nn * M];
+    float o = alpha * s;
+    if (beta != 0.f) o = fmaf(beta, Cin[m + (int64_t)nn * ldcin], o);
+    C[m + (int64_t)nn * ldc] = o;
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+
+bool get_encoder()
+{
+    std::call_once(g_encode_once, [] {
+        cudaDriverEntryPointQueryResult q;
+        void *fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    });
+    return g_encode != nullptr;
+}
+
+// 2-D FP32 tensor map: inner extent `inner` (contiguous), outer extent
+// `outer` with row pitch ld elements; box {32, box_rows}; 128-byte swizzle;
+// out-of-range elements read as zero.
+bool make_map(CUtensorMap *map, const float *ptr, int inner, int outer, int64_t ld, int box_rows)
+{
+    cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+    cuuint32_t box[2] = {32, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void *)ptr, dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+int g_num_sms = 0;
+
+}  // namespace
+
+struct tc_plan {
+    int prec = 0;
+    float *part = nullptr;
+    size_t part_cap = 0;
+    int *err = nullptr;
+};
+
+tc_plan *tc_plan_create(int n, int q, int prec)
+{
+    (void)n;
+    (void)q;
+    if (!get_encoder()) return nullptr;
+    tc_plan *p = new tc_plan();
+    p->prec = prec;
+    if (cudaMalloc(&p->err, sizeof(int)) != cudaSuccess) {
+        delete p;
+        return nullptr;
+    }
+    cudaMemset(p->err, 0, sizeof(int));
+    if (!g_num_sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+        if (g_num_sms <= 0) g_num_sms = 148;
+    }
+    return p;
+}
+
+void tc_plan_destroy(tc_plan *p)
+{
+    if (!p) return;
+    if (p->part) cudaFree(p->part);
+    if (p->err) cudaFree(p->err);
+    delete p;
+}
+
+int tc_plan_error(tc_plan *p, cudaStream_t st)
+{
+    int e = 0;
+    if (!p) return 0;
+    cudaMemcpyAsync(&e, p->err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    cudaStreamSynchronize(st);
+    return e;
+}
+
+template <int BN, int TERMS>
+static int launch_bn(tc_plan *p, cudaStream_t st, const CUtensorMap &ma, const CUtensorMap &mb, int a_mn, int M,
+                     int N, int K, float alpha, float beta, const float *Cin, int64_t ldcin, float *C, int64_t ldc,
+                     const int *status, int *err)
+{
+    using CF = Cfg<BN, TERMS>;
+    static bool attr = false;
+    if (!attr) {
+        if (cudaFuncSetAttribute(k_tc_gemm<BN, TERMS>, cudaFuncAttributeMaxDynamicSharedMemorySize, CF::SMEM) !=
+            cudaSuccess)
+            return -1;
+        attr = true;
+    }
+    const int mt = (M + BM - 1) / BM, nt = (N + BN - 1) / BN;
+    const int nkb = (K + BK - 1) / BK;
+    const int tiles = mt * nt;
+    int splits = 1;
+    if (tiles < g_num_sms) splits = std::max(1, std::min(g_num_sms / tiles, nkb / 4));
+    const int kbps = (nkb + splits - 1) / splits;
+    splits = (nkb + kbps - 1) / kbps;
+    float *part = nullptr;
+    if (splits > 1) {
+        const size_t need = (size_t)splits * M * N;
+        if (need > p->part_cap) {
+            if (p->part) cudaFree(p->part);
+            p->part = nullptr;
+            p->part_cap = 0;
+            if (cudaMalloc(&p->part, need * sizeof(float)) != cudaSuccess) return -2;
+            p->part_cap = need;
+        }
+        part = p->part;
+    }
+    dim3 grid(mt, nt, splits);
+    k_tc_gemm<BN, TERMS><<<grid, 256, CF::SMEM, st>>>(ma, mb, a_mn, M, N, nkb, kbps, alpha, beta, Cin, ldcin, C, ldc,
+                                                      part, status, err);
+    if (splits > 1) {
+        dim3 g2((M + 255) / 256, N);
+        k_splitk_reduce<<<g2, 256, 0, st>>>(M, N, splits, part, alpha, beta, Cin, ldcin, C, ldc);
+    }
+    return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+template <int TERMS>
+static int launch_terms(tc_plan *p, cudaStream_t st, int a_layout, int M, int N, int K, float alpha, const float *A,
+                        int64_t lda, const float *B, int64_t ldb, float beta, const float *Cin, int64_t ldcin,
+                        float *C, int64_t ldc, const int *status, int *err)
+{
+    const int a_mn = (a_layout == TC_A_MN);
+    const int bn = N <= 32 ? 32 : N <= 64 ? 64 : 128;
+    CUtensorMap ma, mb;
+    bool ok = a_mn ? make_map(&ma, A, M, K, lda, 32) : make_map(&ma, A, K, M, lda, BM);
+    ok = ok && make_map(&mb, B, K, N, ldb, bn);
+    if (!ok) return -4;
+    switch (bn) {
+    case 32: return launch_bn<32, TERMS>(p, st, ma, mb, a_mn, M, N, K, alpha, beta, Cin, ldcin, C, ldc, status, err);
+    case 64: return launch_bn<64, TERMS>(p, st, ma, mb, a_mn, M, N, K, alpha, beta, Cin, ldcin, C, ldc, status, err);
+    default:
+        return launch_bn<128, TERMS>(p, st, ma, mb, a_mn, M, N, K, alpha, beta, Cin, ldcin, C, ldc, status, err);
+    }
+}
+
+static bool tma_ok(const void *ptr, int64_t ld) { return ((uintptr_t)ptr % 16 == 0) && (ld % 4 == 0); }
+
+static int tc_run(tc_plan *p, cudaStream_t st, int terms, int a_layout, int M, int N, int K, float alpha,
+                  const float *A, int64_t lda, const float *B, int64_t ldb, float beta, const float *Cin,
+                  int64_t ldcin, float *C, int64_t ldc, const int *status)
+{
+    if (M <= 0 || N <= 0) return 0;
+    const bool ok = p && K > 0 && tma_ok(A, lda) && tma_ok(B, ldb);
+    if (!ok) {
+        // SIMT fallback: alpha op(A) B + beta Cin (Cin copied to C first when distinct)
+        if (beta != 0.f && Cin != C) launch_copy2d<float, float>(st, M, N, Cin, ldcin, C, ldc, 1.0);
+        gemm_simt<float>(st, a_layout == TC_A_K, false, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, status);
+        return 1;
+    }
+    int *err = status ? const_cast<int *>(status) : p->err;
+    if (terms == 3)
+        return launch_terms<3>(p, st, a_layout, M, N, K, alpha, A, lda, B, ldb, beta, Cin, ldcin, C, ldc, status, err);
+    return launch_terms<1>(p, st, a_layout, M, N, K, alpha, A, lda, B, ldb, beta, Cin, ldcin, C, ldc, status, err);
+}
+
+int tc_gemm_nk(tc_plan *p, cudaStream_t st, int terms, int a_layout, int M, int N, int K, const float *A, int64_t lda,
+               const float *B, int64_t ldb, float *C, int64_t ldc, const int *status)
+{
+    return tc_run(p, st, terms, a_layout, M, N, K, 1.f, A, lda, B, ldb, 0.f, nullptr, 0, C, ldc, status);
+}
+
+int tc_gemm_nk_axpby(tc_plan *p, cudaStream_t st, int terms, int a_layout, int M, int N, int K, float alpha,
+                     const float *A, int64_t lda, const float *B, int64_t ldb, float beta, const float *Cin,
+                     int64_t ldcin, float *C, int64_t ldc)
+{
+    return tc_run(p, st, terms, a_layout, M, N, K, alpha, A, lda, B, ldb, beta, Cin, ldcin, C, ldc, nullptr);
+}
+
+int tc_update(tc_plan *p, cudaStream_t st, int terms, int n, int q, const float *ShT, const float *V, float *L,
+              int64_t ldl, const int *status)
+{
+    // L (n x n) += op(A) B with op(A)(i, c) = ShT[c + i q] (K-major, K = q), B(c, j) = V[c + j q]
+    return tc_run(p, st, terms, TC_A_K, n, n, q, 1.f, ShT, q, V, q, 1.f, L, ldl, L, ldl, status);
+}

@@ -1,0 +1,36 @@
+// tc.cuh -- tensor-core (tcgen05 + TMA) GEMMs on FP32-stored operands.
+//
+//   C = alpha op(A) B + beta Cin        (column-major C, M x N)
+//   op(A) M x K: TC_A_K  -> element (m, k) at A[k + m lda]  (K contiguous)
+//                TC_A_MN -> element (m, k) at A[m + k lda]  (M contiguous)
+//   B K x N:     element (k, n) at B[k + n ldb]             (K contiguous)
+//
+// terms = 1: single-pass TF32 products (FP32 accumulate).
+// terms = 3: each operand split x = hi + lo with hi = x truncated to the
+//            11 leading significand bits (exact in TF32) and lo = x - hi;
+//            C accumulates hi*hi + hi*lo + lo*hi, which carries ~22 bits.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+enum { TC_A_K = 0, TC_A_MN = 1 };
+
+struct tc_plan;
+
+tc_plan *tc_plan_create(int n, int q, int prec);
+void tc_plan_destroy(tc_plan *p);
+
+// Returns 0 when launched on the tensor cores, 1 when it fell back to the
+// SIMT kernel (shape or alignment outside what TMA accepts), <0 on error.
+int tc_gemm_nk(tc_plan *p, cudaStream_t st, int terms, int a_layout, int M, int N, int K, const float *A,
+               int64_t lda, const float *B, int64_t ldb, float *C, int64_t ldc, const int *status);
+int tc_gemm_nk_axpby(tc_plan *p, cudaStream_t st, int terms, int a_layout, int M, int N, int K, float alpha,
+                     const float *A, int64_t lda, const float *B, int64_t ldb, float beta, const float *Cin,
+                     int64_t ldcin, float *C, int64_t ldc);
+// L += S^ V with S^ given row-major (element (i, c) at ShT[c + i q]) and V
+// q x n column-major (ld q).
+int tc_update(tc_plan *p, cudaStream_t st, int terms, int n, int q, const float *ShT, const float *V, float *L,
+              int64_t ldl, const int *status);
+
+// Device error word of the plan's kernels (bounded waits that gave up).
+int tc_plan_error(tc_plan *p, cudaStream_t st);

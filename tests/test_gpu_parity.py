@@ -1,0 +1,311 @@
+"""Parity of the sm_103a library (through its C ABI) with the FP64 CPU oracle.
+
+Bars (written out per test):
+  * integer decisions (coordinate blocks, Floyd samples): bit-exact;
+  * FP64 mode: relative Frobenius error of the iterate <= 1e-10 at every
+    checked step;
+  * FP32 storage with FP32 or 3xTF32 products: <= 1e-4 along the trajectory
+    and |r_gpu - r_oracle| <= 0.1 tol on the final residual;
+  * mixed (single-pass TF32 for the rank-q correction): residual agreement.
+"""
+import numpy as np
+import pytest
+
+import paper_1602_01768_gb300._binding as B
+from oracle import oracle as orc
+from paper_1602_01768_gb300 import workloads as wl
+
+from gpu_util import empty_dev, export, from_dev, rel, stream_ptr, to_dev, torch_dtype
+
+pytestmark = pytest.mark.gpu
+
+
+def _handle(A, method, sketch, q, prec, seed=11, stream=0):
+    n = A.shape[0]
+    tdt = torch_dtype(prec)
+    Ad = to_dev(A, tdt)
+    opts = B.make_opts(method=method, sketch=sketch, q=q, prec=prec, seed=seed, stream_id=stream)
+    h = B.rbfgs_init(n, Ad.data_ptr(), n, prec == B.RB_FP64, opts, stream_ptr())
+    return h
+
+
+# --------------------------------------------------------------------------
+# Sketch draws
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("prec,tol", [(B.RB_FP64, 1e-13), (B.RB_FP32, 2e-5)])
+def test_gauss_sketch_matches_oracle(prec, tol):
+    n, q = 1001, 24
+    A = np.eye(n)
+    h = _handle(A, B.RB_METHOD_ADARBFGS, B.RB_SKETCH_GAUSS, q, prec, seed=0xABCDEF12345, stream=3)
+    try:
+        for k in (0, 1, 77, 2**31 + 5):
+            out = empty_dev(n, q, torch_dtype(prec))
+            B.rbfgs_draw_sketch(h, k, out.data_ptr(), n)
+            S = from_dev(out)
+            Sref = orc.gauss_sketch(0xABCDEF12345, 3, k, n, q)
+            assert np.max(np.abs(S - Sref)) <= tol * max(1.0, np.max(np.abs(Sref)))
+    finally:
+        B.rbfgs_destroy(h)
+
+
+def test_coordinate_draws_bit_exact():
+    n, q = 150, 16  # 10 blocks, the last one of size 6
+    A, _, _ = wl.spd_spectrum(n, 1e3, 21)
+    h = _handle(A, B.RB_METHOD_RBFGS, B.RB_SKETCH_COORD_TRACE, q, B.RB_FP64, seed=5, stream=1)
+    try:
+        for k in range(200):
+            out = empty_dev(n, q, torch_dtype(B.RB_FP64))
+            B.rbfgs_draw_sketch(h, k, out.data_ptr(), n)
+            S = from_dev(out)
+            b, first, size = orc.coord_trace_block(A, q, 5, 1, k)
+            ref = np.zeros((n, q))
+            ref[first + np.arange(size), np.arange(size)] = 1.0
+            assert np.array_equal(S, ref), k
+    finally:
+        B.rbfgs_destroy(h)
+    h = _handle(np.eye(97), B.RB_METHOD_ADARBFGS, B.RB_SKETCH_COORD_UNIFORM, 9, B.RB_FP64, seed=8, stream=2)
+    try:
+        for k in range(100):
+            out = empty_dev(97, 9, torch_dtype(B.RB_FP64))
+            B.rbfgs_draw_sketch(h, k, out.data_ptr(), 97)
+            S = from_dev(out)
+            idx = orc.floyd_sample(8, 2, k, orc.TAG_COORD, 97, 9)
+            ref = np.zeros((97, 9))
+            ref[idx, np.arange(9)] = 1.0
+            assert np.array_equal(S, ref), k
+    finally:
+        B.rbfgs_destroy(h)
+
+
+# --------------------------------------------------------------------------
+# FP64 parity (<= 1e-10 relative Frobenius at every checked step)
+# --------------------------------------------------------------------------
+def test_rbfgs_fp64_c1_parity():
+    w = wl.WORKLOADS["c1_rbfgs_fp64_n256"]
+    A, _, _ = wl.c1_matrix()
+    n, q = w["n"], w["q"]
+    h = _handle(A, B.RB_METHOD_RBFGS, B.RB_SKETCH_GAUSS, q, B.RB_FP64, seed=w["seed"])
+    X = np.eye(n)
+    done = 0
+    try:
+        for chk in (1, 5, 50, 150, 300):
+            B.rbfgs_step(h, chk - done)
+            _, X = orc.rbfgs_run(A, X, q, orc.SKETCH_GAUSS, w["seed"], 0, done, chk - done)
+            done = chk
+            Xg = export(h, n, B.RB_FP64, B.RB_WHAT_X)
+            assert rel(Xg, X) <= 1e-10, (chk, rel(Xg, X))
+        r_gpu = B.rbfgs_residual(h, 0)
+        r_orc = orc.residual(A, X)
+        assert abs(r_gpu - r_orc) <= 1e-10 * max(r_orc, 1e-3)
+    finally:
+        B.rbfgs_destroy(h)
+
+
+@pytest.mark.parametrize("n,q", [(203, 7), (64, 64), (1, 1)])
+def test_rbfgs_fp64_ragged_parity(n, q):
+    if n == 1:
+        A = np.array([[2.5]])
+    else:
+        A, _, _ = wl.spd_spectrum(n, 50.0, 22)
+    steps = 30 if n > 1 else 2
+    h = _handle(A, B.RB_METHOD_RBFGS, B.RB_SKETCH_GAUSS, q, B.RB_FP64, seed=3)
+    try:
+        B.rbfgs_step(h, steps)
+        _, X = orc.rbfgs_run(A, np.eye(n), q, orc.SKETCH_GAUSS, 3, 0, 0, steps)
+        assert rel(export(h, n, B.RB_FP64, B.RB_WHAT_X), X) <= 1e-10
+    finally:
+        B.rbfgs_destroy(h)
+
+
+def test_rbfgs_coordinate_fp64_parity():
+    n, q = 150, 16
+    A, _, _ = wl.spd_spectrum(n, 30.0, 23)
+    h = _handle(A, B.RB_METHOD_RBFGS, B.RB_SKETCH_COORD_TRACE, q, B.RB_FP64, seed=6)
+    try:
+        B.rbfgs_step(h, 120)
+        _, X = orc.rbfgs_run(A, np.eye(n), q, orc.SKETCH_COORD_TRACE, 6, 0, 0, 120)
+        assert rel(export(h, n, B.RB_FP64, B.RB_WHAT_X), X) <= 1e-10
+    finally:
+        B.rbfgs_destroy(h)
+
+
+@pytest.mark.parametrize("sketch,kind", [(B.RB_SKETCH_GAUSS, orc.SKETCH_GAUSS),
+                                         (B.RB_SKETCH_COORD_UNIFORM, orc.SKETCH_COORD_UNIFORM)])
+def test_adarbfgs_fp64_parity(sketch, kind):
+    n, q = 300, 12
+    A, _, _ = wl.spd_spectrum(n, 100.0, 24)
+    h = _handle(A, B.RB_METHOD_ADARBFGS, sketch, q, B.RB_FP64, seed=7)
+    L = np.eye(n)
+    done = 0
+    try:
+        for chk in (1, 10, 60):
+            B.adarbfgs_step(h, chk - done)
+            _, L = orc.adarbfgs_run(A, L, q, kind, 7, 0, done, chk - done)
+            done = chk
+            Lg = export(h, n, B.RB_FP64, B.RB_WHAT_L)
+            assert rel(Lg, L) <= 1e-10, (chk, rel(Lg, L))
+        Xg = export(h, n, B.RB_FP64, B.RB_WHAT_X)
+        assert rel(Xg, L @ L.T) <= 1e-10
+        assert abs(B.rbfgs_residual(h, 0) - orc.residual_factored(A, L)) <= 1e-10
+        assert abs(B.rbfgs_residual(h, 40, 99) - orc.residual_sampled(A, 40, 99, L=L)) <= 1e-10
+    finally:
+        B.rbfgs_destroy(h)
+
+
+# --------------------------------------------------------------------------
+# FP32 storage: SIMT FP32 and tensor-core 3xTF32 products
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("prec", [B.RB_FP32, B.RB_TF32X3])
+@pytest.mark.parametrize("n,q", [(1000, 64), (512, 32)])
+def test_adarbfgs_fp32_parity(prec, n, q):
+    # the oracle inverts the same FP32-rounded matrix the device holds
+    A = wl.c2_matrix(n=n).astype(np.float32).astype(np.float64)
+    steps = 40
+    h = _handle(A, B.RB_METHOD_ADARBFGS, B.RB_SKETCH_GAUSS, q, prec, seed=9)
+    try:
+        L = np.eye(n)
+        done = 0
+        for chk in (1, 10, steps):
+            B.adarbfgs_step(h, chk - done)
+            _, L = orc.adarbfgs_run(A, L, q, orc.SKETCH_GAUSS, 9, 0, done, chk - done)
+            done = chk
+            Lg = export(h, n, prec, B.RB_WHAT_L)
+            assert rel(Lg, L) <= 1e-4, (chk, rel(Lg, L))
+        r_orc = orc.residual_factored(A, L)
+        r_gpu = B.rbfgs_residual(h, 0)
+        assert abs(r_gpu - r_orc) <= 1e-3 * r_orc
+    finally:
+        B.rbfgs_destroy(h)
+
+
+def test_adarbfgs_tf32x3_one_step_from_general_L():
+    # exercises the M-contiguous operand path (S = L S~ with L != I) and split-K
+    n, q = 768, 64
+    A = wl.c2_matrix(n=n).astype(np.float32).astype(np.float64)
+    rng = np.random.default_rng(4)
+    L0 = np.eye(n) + 0.05 * rng.standard_normal((n, n))
+    h = _handle(A, B.RB_METHOD_ADARBFGS, B.RB_SKETCH_GAUSS, q, B.RB_TF32X3, seed=12)
+    try:
+        Ld = to_dev(L0, torch_dtype(B.RB_TF32X3))
+        B.rbfgs_import(h, B.RB_WHAT_L, Ld.data_ptr(), n)
+        B.rbfgs_set_step(h, 5)
+        B.adarbfgs_step(h, 1)
+        _, L1 = orc.adarbfgs_run(A, L0.astype(np.float32).astype(np.float64), q, orc.SKETCH_GAUSS, 12, 0, 5, 1)
+        assert rel(export(h, n, B.RB_TF32X3, B.RB_WHAT_L), L1) <= 2e-5
+    finally:
+        B.rbfgs_destroy(h)
+
+
+def test_adarbfgs_mixed_reaches_tolerance_like_oracle():
+    n, q, tol = 512, 32, 1e-4
+    A = wl.c2_matrix(n=n).astype(np.float32).astype(np.float64)
+    h = _handle(A, B.RB_METHOD_ADARBFGS, B.RB_SKETCH_GAUSS, q, B.RB_MIXED, seed=13)
+    try:
+        st, iters, r = B.rbfgs_solve(h, tol, 3000, 16, 128, 0)
+        assert st == B.RB_OK and r <= tol
+        _, L = orc.adarbfgs_run(A, np.eye(n), q, orc.SKETCH_GAUSS, 13, 0, 0, iters)
+        r_orc = orc.residual_factored(A, L)
+        Lg = export(h, n, B.RB_MIXED, B.RB_WHAT_L)
+        r_gpu_in_fp64 = orc.residual_factored(A, Lg)
+        assert abs(r_gpu_in_fp64 - r_orc) <= 0.1 * tol + 0.5 * r_orc
+        assert r_gpu_in_fp64 <= 1.1 * tol
+    finally:
+        B.rbfgs_destroy(h)
+
+
+# --------------------------------------------------------------------------
+# Comparison methods
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("prec,tol", [(B.RB_FP64, 1e-10), (B.RB_FP32, 1e-4), (B.RB_TF32X3, 1e-4)])
+def test_newton_schulz_parity(prec, tol):
+    n = 384
+    A, _, lam = wl.spd_spectrum(n, 30.0, 25)
+    Ad = to_dev(A, torch_dtype(prec))
+    h = B.newton_schulz_init(n, Ad.data_ptr(), n, prec == B.RB_FP64, prec, 0, float(lam.max()), stream_ptr())
+    try:
+        X = orc.ns_init(A, float(lam.max()))
+        for _ in range(3):
+            B.newton_schulz_step(h, 4)
+            for _ in range(4):
+                X = orc.ns_step(A, X)
+            assert rel(export(h, n, prec, B.RB_WHAT_X), X) <= tol
+    finally:
+        B.rbfgs_destroy(h)
+
+
+def test_newton_schulz_power_iteration_sigma():
+    n = 200
+    A, _, lam = wl.spd_spectrum(n, 10.0, 26)
+    Ad = to_dev(A, torch_dtype(B.RB_FP64))
+    h = B.newton_schulz_init(n, Ad.data_ptr(), n, True, B.RB_FP64, 60, 0.0, stream_ptr())
+    try:
+        assert abs(B.rbfgs_sigma(h) - orc.power_norm(A, 60)) <= 1e-12 * lam.max()
+    finally:
+        B.rbfgs_destroy(h)
+
+
+@pytest.mark.parametrize("prec,tol", [(B.RB_FP64, 1e-10), (B.RB_FP32, 1e-4)])
+def test_mr_parity(prec, tol):
+    n = 256
+    A, _, _ = wl.spd_spectrum(n, 20.0, 27)
+    Ad = to_dev(A, torch_dtype(prec))
+    h = B.mr_init(n, Ad.data_ptr(), n, prec == B.RB_FP64, prec, stream_ptr())
+    try:
+        X = orc.mr_init(A)
+        assert rel(export(h, n, prec, B.RB_WHAT_X), X) <= tol
+        B.mr_step(h, 5)
+        for _ in range(5):
+            _, X = orc.mr_step(A, X)
+        assert rel(export(h, n, prec, B.RB_WHAT_X), X) <= tol
+    finally:
+        B.rbfgs_destroy(h)
+
+
+# --------------------------------------------------------------------------
+# Failure paths, checkpoint / resume
+# --------------------------------------------------------------------------
+def test_indefinite_matrix_reports_notspd_and_keeps_iterate():
+    n, q = 40, 4
+    A = -np.eye(n)
+    h = _handle(A, B.RB_METHOD_ADARBFGS, B.RB_SKETCH_GAUSS, q, B.RB_FP64)
+    try:
+        B.adarbfgs_step(h, 3)
+        with pytest.raises(B.RbfgsError) as e:
+            B.rbfgs_sync(h)
+        assert e.value.status == B.RB_ENOTSPD
+        assert np.array_equal(export(h, n, B.RB_FP64, B.RB_WHAT_L), np.eye(n))
+    finally:
+        B.rbfgs_destroy(h)
+
+
+def test_invalid_arguments_are_rejected():
+    with pytest.raises(B.RbfgsError) as e:
+        B.rbfgs_init(0, 1, 1, 0, B.make_opts(), 0)
+    assert e.value.status == B.RB_EINVAL
+    A = to_dev(np.eye(8), torch_dtype(B.RB_FP64))
+    with pytest.raises(B.RbfgsError):
+        B.rbfgs_init(8, A.data_ptr(), 8, 1, B.make_opts(q=9), 0)
+
+
+@pytest.mark.parametrize("prec", [B.RB_FP64, B.RB_TF32X3])
+def test_checkpoint_resume_is_bit_exact(prec):
+    n, q, K = 256, 16, 12
+    A = wl.c2_matrix(n=n)
+    tdt = torch_dtype(prec)
+    h1 = _handle(A, B.RB_METHOD_ADARBFGS, B.RB_SKETCH_GAUSS, q, prec, seed=31)
+    h2 = _handle(A, B.RB_METHOD_ADARBFGS, B.RB_SKETCH_GAUSS, q, prec, seed=31)
+    try:
+        B.adarbfgs_step(h1, 2 * K)
+        B.adarbfgs_step(h2, K)
+        ck = empty_dev(n, n, tdt)
+        B.rbfgs_export(h2, B.RB_WHAT_L, ck.data_ptr(), n)
+        k = B.rbfgs_get_step(h2)
+        B.rbfgs_destroy(h2)
+        h2 = _handle(A, B.RB_METHOD_ADARBFGS, B.RB_SKETCH_GAUSS, q, prec, seed=31)
+        B.rbfgs_import(h2, B.RB_WHAT_L, ck.data_ptr(), n)
+        B.rbfgs_set_step(h2, k)
+        B.adarbfgs_step(h2, K)
+        assert np.array_equal(export(h1, n, prec, B.RB_WHAT_L), export(h2, n, prec, B.RB_WHAT_L))
+    finally:
+        B.rbfgs_destroy(h1)
+        B.rbfgs_destroy(h2)
