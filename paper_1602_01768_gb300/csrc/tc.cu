@@ -6,10 +6,13 @@
 //   warp 0      TMA producer: streams 128 x 32 tiles of op(A) and BN x 32
 //               tiles of B (FP32, 128-byte swizzle) into a STAGES-deep ring;
 //   warp 1      allocates the TMEM accumulator (BN columns x 128 lanes) and
-//               issues tcgen05.mma kind::tf32 from one elected thread;
-//   warps 4-7   (terms = 3) split each landed tile in place into hi (top 11
-//               significand bits) and lo = x - hi, then (all terms) drain the
-//               accumulator with tcgen05.ld and apply alpha/beta.
+//               issues tcgen05.mma kind::tf32 from one elected thread; both
+//               operands are K-major in shared memory;
+//   warps 4-7   per stage: an M-contiguous op(A) tile is transposed into the
+//               K-major layout, and (terms = 3) every tile is split into hi
+//               (top 11 significand bits) and lo = x - hi; after the last
+//               stage they drain the accumulator with tcgen05.ld and apply
+//               alpha/beta.
 // Every mbarrier wait is bounded (about two seconds of SM clock); a wait
 // that gives up records ST_TIMEOUT in the caller's status word and the CTA
 // winds down instead of hanging.
@@ -136,25 +139,85 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-template <int BN, int TERMS>
+template <int BN, int TERMS, int AMN>
 struct Cfg {
     static constexpr int A_BYTES = A_TILE_BYTES;
     static constexpr int B_BYTES = BN * BK * 4;
-    static constexpr int STAGE_BYTES = (A_BYTES + B_BYTES) * (TERMS == 3 ? 2 : 1);
+    // [A hi | B hi | A lo | B lo (3 terms) | A raw, M-contiguous (AMN)]
+    static constexpr int STAGE_BYTES = (A_BYTES + B_BYTES) * (TERMS == 3 ? 2 : 1) + (AMN ? A_BYTES : 0);
     static constexpr int STAGES_RAW = (200 * 1024) / STAGE_BYTES;
     static constexpr int STAGES = STAGES_RAW > 8 ? 8 : STAGES_RAW;
     static constexpr int TMEM_COLS = BN < 32 ? 32 : BN;
     static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 /*align*/ + 512 /*barriers*/;
+    static constexpr bool CONVERT = (TERMS == 3) || AMN;  // converter warps have work each stage
     static_assert(STAGES >= 2, "pipeline needs two stages");
 };
 
-template <int BN, int TERMS>
+__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+
+// In-place hi/lo split of a tile of `bytes` bytes (layout preserved).
+__device__ __forceinline__ void split_tile(unsigned char *hi, unsigned char *lo, int bytes, int t)
+{
+    float4 *a = (float4 *)hi;
+    float4 *b = (float4 *)lo;
+    for (int e = t; e < bytes / 16; e += 128) {
+        const float4 v = a[e];
+        float4 h, l;
+        h.x = tf32_hi(v.x);
+        h.y = tf32_hi(v.y);
+        h.z = tf32_hi(v.z);
+        h.w = tf32_hi(v.w);
+        l.x = v.x - h.x;
+        l.y = v.y - h.y;
+        l.z = v.z - h.z;
+        l.w = v.w - h.w;
+        a[e] = h;
+        b[e] = l;
+    }
+}
+
+// Row m = t of the K-major 128 x 32 tile (128-byte swizzle: 16-byte chunk j of
+// row m sits at chunk j ^ (m & 7)) gathered from the M-contiguous raw tile
+// (four 32-row boxes, 4 KB apart; element (m, k) in 16-byte chunk
+// (m & 31) / 4 ^ (k & 7) of K-row k).  Writes hi, and lo when lo != nullptr.
+__device__ __forceinline__ void transpose_tile(const unsigned char *raw, unsigned char *hi, unsigned char *lo, int t)
+{
+    const int m = t, c = m >> 5, mi = m & 31;
+    const unsigned char *src = raw + c * 4096 + ((mi & 3) << 2);
+#pragma unroll
+    for (int kq = 0; kq < 8; ++kq) {
+        float v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int k = 4 * kq + u;
+            v[u] = *(const float *)(src + k * 128 + ((((mi >> 2) ^ (k & 7))) << 4));
+        }
+        const int off = m * 128 + ((kq ^ (m & 7)) << 4);
+        if (lo) {
+            float4 h, l;
+            h.x = tf32_hi(v[0]);
+            h.y = tf32_hi(v[1]);
+            h.z = tf32_hi(v[2]);
+            h.w = tf32_hi(v[3]);
+            l.x = v[0] - h.x;
+            l.y = v[1] - h.y;
+            l.z = v[2] - h.z;
+            l.w = v[3] - h.w;
+            *(float4 *)(hi + off) = h;
+            *(float4 *)(lo + off) = l;
+        } else {
+            *(float4 *)(hi + off) = make_float4(v[0], v[1], v[2], v[3]);
+        }
+    }
+}
+
+template <int BN, int TERMS, int AMN>
 __global__ void __launch_bounds__(256, 1)
-k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int a_mn, int M, int N,
-          int nkb, int kb_per_split, float alpha, float beta, const float *Cin, int64_t ldcin, float *C, int64_t ldc,
+k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N, int nkb,
+          int kb_per_split, float alpha, float beta, const float *Cin, int64_t ldcin, float *C, int64_t ldc,
           float *part, const int *status, int *err)
 {
-    using CF = Cfg<BN, TERMS>;
+    using CF = Cfg<BN, TERMS, AMN>;
     constexpr int STAGES = CF::STAGES;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     if (status_bad(status)) return;  // uniform: every thread reads the same word
@@ -200,6 +263,9 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     auto stage_b = [&](int s) { return smem + s * CF::STAGE_BYTES + CF::A_BYTES; };
     auto stage_alo = [&](int s) { return smem + s * CF::STAGE_BYTES + CF::A_BYTES + CF::B_BYTES; };
     auto stage_blo = [&](int s) { return smem + s * CF::STAGE_BYTES + 2 * CF::A_BYTES + CF::B_BYTES; };
+    auto stage_raw = [&](int s) {
+        return smem + s * CF::STAGE_BYTES + (CF::A_BYTES + CF::B_BYTES) * (TERMS == 3 ? 2 : 1);
+    };
 
     if (warp == 0) {
         // ---------------- TMA producer ----------------
@@ -210,10 +276,10 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                 const uint32_t fb = smem_u32(&full[s]);
                 mbar_expect_tx(fb, CF::A_BYTES + CF::B_BYTES);
                 const int k = (kb0 + i) * BK;
-                if (a_mn) {
+                if (AMN) {
 #pragma unroll
                     for (int c = 0; c < BM / 32; ++c)
-                        tma_load_2d(smem_u32(stage_a(s) + c * 4096), &tmA, m0 + 32 * c, k, fb);
+                        tma_load_2d(smem_u32(stage_raw(s) + c * 4096), &tmA, m0 + 32 * c, k, fb);
                 } else {
                     tma_load_2d(smem_u32(stage_a(s)), &tmA, k, m0, fb);
                 }
@@ -221,13 +287,13 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
             }
         }
     } else if (warp == 1) {
-        // ---------------- MMA issuer ----------------
+        // ---------------- MMA issuer (both operands K-major in smem) ----------------
         if (lane == 0) {
-            const uint32_t idesc = idesc_tf32(BN, a_mn);
+            const uint32_t idesc = idesc_tf32(BN, 0);
             bool ok = true;
             for (int i = 0; i < nk && ok; ++i) {
                 const int s = i % STAGES;
-                const uint32_t wb = (TERMS == 3) ? smem_u32(&conv[s]) : smem_u32(&full[s]);
+                const uint32_t wb = CF::CONVERT ? smem_u32(&conv[s]) : smem_u32(&full[s]);
                 if (!mbar_wait(wb, (i / STAGES) & 1, err, abort_flag)) {
                     ok = false;
                     break;
@@ -237,15 +303,12 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                 const uint32_t a_lo = smem_u32(stage_alo(s)), b_lo = smem_u32(stage_blo(s));
 #pragma unroll
                 for (int kk = 0; kk < BK / 8; ++kk) {
-                    // A: K-major advances 32 B within the swizzle row; MN-major
-                    // advances one 8-row (1024 B) group; M-chunks 4 KB apart.
-                    const uint32_t aoff = a_mn ? kk * 1024 : kk * 32;
-                    const uint32_t alb = a_mn ? 4096 : 16, asb = 1024;
-                    const uint64_t da_hi = umma_desc(a_hi + aoff, alb, asb);
+                    // K = 8 TF32 per MMA = 32 bytes along the 128-byte swizzle row
+                    const uint64_t da_hi = umma_desc(a_hi + kk * 32, 16, 1024);
                     const uint64_t db_hi = umma_desc(b_hi + kk * 32, 16, 1024);
                     const uint32_t first = (i == 0 && kk == 0) ? 0u : 1u;
                     if (TERMS == 3) {
-                        const uint64_t da_lo = umma_desc(a_lo + aoff, alb, asb);
+                        const uint64_t da_lo = umma_desc(a_lo + kk * 32, 16, 1024);
                         const uint64_t db_lo = umma_desc(b_lo + kk * 32, 16, 1024);
                         mma_tf32(tmem, da_lo, db_hi, idesc, first);
                         mma_tf32(tmem, da_hi, db_lo, idesc, 1u);
@@ -260,41 +323,16 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         }
     } else if (warp >= 4) {
         const int t = threadIdx.x - 128;  // 0..127
-        // ---------------- hi/lo split (terms = 3) ----------------
-        if (TERMS == 3) {
+        // ---------------- operand conversion ----------------
+        if (CF::CONVERT) {
             for (int i = 0; i < nk; ++i) {
                 const int s = i % STAGES;
                 if (!mbar_wait(smem_u32(&full[s]), (i / STAGES) & 1, err, abort_flag)) break;
-                float4 *a = (float4 *)stage_a(s);
-                float4 *alo = (float4 *)stage_alo(s);
-                for (int e = t; e < CF::A_BYTES / 16; e += 128) {
-                    float4 v = a[e], h, l;
-                    h.x = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
-                    h.y = __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u);
-                    h.z = __uint_as_float(__float_as_uint(v.z) & 0xFFFFE000u);
-                    h.w = __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u);
-                    l.x = v.x - h.x;
-                    l.y = v.y - h.y;
-                    l.z = v.z - h.z;
-                    l.w = v.w - h.w;
-                    a[e] = h;
-                    alo[e] = l;
-                }
-                float4 *b = (float4 *)stage_b(s);
-                float4 *blo = (float4 *)stage_blo(s);
-                for (int e = t; e < CF::B_BYTES / 16; e += 128) {
-                    float4 v = b[e], h, l;
-                    h.x = __uint_as_float(__float_as_uint(v.x) & 0xFFFFE000u);
-                    h.y = __uint_as_float(__float_as_uint(v.y) & 0xFFFFE000u);
-                    h.z = __uint_as_float(__float_as_uint(v.z) & 0xFFFFE000u);
-                    h.w = __uint_as_float(__float_as_uint(v.w) & 0xFFFFE000u);
-                    l.x = v.x - h.x;
-                    l.y = v.y - h.y;
-                    l.z = v.z - h.z;
-                    l.w = v.w - h.w;
-                    b[e] = h;
-                    blo[e] = l;
-                }
+                if (AMN)
+                    transpose_tile(stage_raw(s), stage_a(s), TERMS == 3 ? stage_alo(s) : nullptr, t);
+                else
+                    split_tile(stage_a(s), stage_alo(s), CF::A_BYTES, t);
+                if (TERMS == 3) split_tile(stage_b(s), stage_blo(s), CF::B_BYTES, t);
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 mbar_arrive(smem_u32(&conv[s]));
             }
@@ -431,15 +469,15 @@ int tc_plan_error(tc_plan *p, cudaStream_t st)
     return e;
 }
 
-template <int BN, int TERMS>
-static int launch_bn(tc_plan *p, cudaStream_t st, const CUtensorMap &ma, const CUtensorMap &mb, int a_mn, int M,
-                     int N, int K, float alpha, float beta, const float *Cin, int64_t ldcin, float *C, int64_t ldc,
+template <int BN, int TERMS, int AMN>
+static int launch_bn(tc_plan *p, cudaStream_t st, const CUtensorMap &ma, const CUtensorMap &mb, int M, int N, int K,
+                     float alpha, float beta, const float *Cin, int64_t ldcin, float *C, int64_t ldc,
                      const int *status, int *err)
 {
-    using CF = Cfg<BN, TERMS>;
+    using CF = Cfg<BN, TERMS, AMN>;
     static bool attr = false;
     if (!attr) {
-        if (cudaFuncSetAttribute(k_tc_gemm<BN, TERMS>, cudaFuncAttributeMaxDynamicSharedMemorySize, CF::SMEM) !=
+        if (cudaFuncSetAttribute(k_tc_gemm<BN, TERMS, AMN>, cudaFuncAttributeMaxDynamicSharedMemorySize, CF::SMEM) !=
             cudaSuccess)
             return -1;
         attr = true;
@@ -464,8 +502,8 @@ static int launch_bn(tc_plan *p, cudaStream_t st, const CUtensorMap &ma, const C
         part = p->part;
     }
     dim3 grid(mt, nt, splits);
-    k_tc_gemm<BN, TERMS><<<grid, 256, CF::SMEM, st>>>(ma, mb, a_mn, M, N, nkb, kbps, alpha, beta, Cin, ldcin, C, ldc,
-                                                      part, status, err);
+    k_tc_gemm<BN, TERMS, AMN><<<grid, 256, CF::SMEM, st>>>(ma, mb, M, N, nkb, kbps, alpha, beta, Cin, ldcin, C, ldc,
+                                                           part, status, err);
     if (splits > 1) {
         dim3 g2((M + 255) / 256, N);
         k_splitk_reduce<<<g2, 256, 0, st>>>(M, N, splits, part, alpha, beta, Cin, ldcin, C, ldc);
@@ -484,12 +522,17 @@ static int launch_terms(tc_plan *p, cudaStream_t st, int a_layout, int M, int N,
     bool ok = a_mn ? make_map(&ma, A, M, K, lda, 32) : make_map(&ma, A, K, M, lda, BM);
     ok = ok && make_map(&mb, B, K, N, ldb, bn);
     if (!ok) return -4;
+#define RB_TC_CASE(BNV)                                                                                     \
+    case BNV:                                                                                                  \
+        return a_mn ? launch_bn<BNV, TERMS, 1>(p, st, ma, mb, M, N, K, alpha, beta, Cin, ldcin, C, ldc, status, err) \
+                    : launch_bn<BNV, TERMS, 0>(p, st, ma, mb, M, N, K, alpha, beta, Cin, ldcin, C, ldc, status, err);
     switch (bn) {
-    case 32: return launch_bn<32, TERMS>(p, st, ma, mb, a_mn, M, N, K, alpha, beta, Cin, ldcin, C, ldc, status, err);
-    case 64: return launch_bn<64, TERMS>(p, st, ma, mb, a_mn, M, N, K, alpha, beta, Cin, ldcin, C, ldc, status, err);
-    default:
-        return launch_bn<128, TERMS>(p, st, ma, mb, a_mn, M, N, K, alpha, beta, Cin, ldcin, C, ldc, status, err);
+        RB_TC_CASE(32)
+        RB_TC_CASE(64)
+        RB_TC_CASE(128)
+    default: return -5;
     }
+#undef RB_TC_CASE
 }
 
 static bool tma_ok(const void *ptr, int64_t ld) { return ((uintptr_t)ptr % 16 == 0) && (ld % 4 == 0); }
