@@ -190,6 +190,36 @@ rb_status mr_step(rbfgs_t h, int nsteps);
 /* Spectral-norm estimate sigma used by newton_schulz_init (synchronises). */
 rb_status rbfgs_sigma(rbfgs_t h, double *sigma);
 
+/*
+ * Host-buffer entry points (the end-to-end path of a caller whose data is in
+ * host memory).  rbfgs_load_host copies a new A from A_host (ld lda, FP32 or
+ * FP64 elements) into an existing RBFGS/AdaRBFGS handle of the same n and
+ * restarts it (X0 = I or L0 = I, k = 0, status cleared); asynchronous, so
+ * A_host must stay valid until the next synchronising call.
+ * rbfgs_export_host copies X (X = L L^T for AdaRBFGS) or L into out_host
+ * (storage type, ld); synchronises.
+ */
+rb_status rbfgs_load_host(rbfgs_t h, const void *A_host, int64_t lda, int a_is_fp64);
+rb_status rbfgs_export_host(rbfgs_t h, int what, void *out_host, int64_t ld);
+
+/*
+ * Run ONE step of the handle's method with a CUDA event recorded on its
+ * stream at every phase boundary (sketch draw, each n x n pass, q x q core,
+ * update).  ms[i] gets the device time of phase i and names[i] (if names is
+ * not NULL) its name, for i < *nphases <= cap.  The step is a real step: it
+ * advances the iterate and k.  Synchronises.
+ */
+rb_status rbfgs_profile_step(rbfgs_t h, double *ms, const char **names, int cap, int *nphases);
+
+/*
+ * Restart an RBFGS/AdaRBFGS handle on the same A: X0 = I or L0 = I, k = 0,
+ * status cleared, new sketch seed and stream.  Asynchronous.
+ */
+rb_status rbfgs_reset(rbfgs_t h, uint64_t seed, uint64_t stream_id);
+
+/* Number of kernels this library has launched since it was loaded. */
+rb_status rbfgs_launch_count(uint64_t *count);
+
 rb_status rbfgs_destroy(rbfgs_t h);
 
 const char *rbfgs_status_string(int status);

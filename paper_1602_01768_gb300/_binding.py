@@ -58,6 +58,11 @@ _SIGS = {
     "mr_init": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_void_p]),
     "mr_step": (C.c_int, [C.c_void_p, C.c_int]),
     "rbfgs_sigma": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "rbfgs_load_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int]),
+    "rbfgs_export_host": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64]),
+    "rbfgs_profile_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
+    "rbfgs_launch_count": (C.c_int, [C.c_void_p]),
+    "rbfgs_reset": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64]),
     "rbfgs_destroy": (C.c_int, [C.c_void_p]),
 }
 
@@ -198,6 +203,32 @@ def rbfgs_sigma(h):
     s = C.c_double()
     _check(_lib().rbfgs_sigma(h, C.byref(s)), "rbfgs_sigma")
     return s.value
+
+
+def rbfgs_load_host(h, A_host, lda, a_is_fp64):
+    return _check(_lib().rbfgs_load_host(h, _p(A_host), lda, int(a_is_fp64)), "rbfgs_load_host")
+
+
+def rbfgs_export_host(h, what, out_host, ld):
+    return _check(_lib().rbfgs_export_host(h, what, _p(out_host), ld), "rbfgs_export_host")
+
+
+def rbfgs_profile_step(h, cap=24):
+    ms = (C.c_double * cap)()
+    names = (C.c_char_p * cap)()
+    n = C.c_int()
+    _check(_lib().rbfgs_profile_step(h, ms, names, cap, C.byref(n)), "rbfgs_profile_step")
+    return [(names[i].decode(), ms[i]) for i in range(n.value)]
+
+
+def rbfgs_reset(h, seed, stream_id=0):
+    return _check(_lib().rbfgs_reset(h, seed, stream_id), "rbfgs_reset")
+
+
+def rbfgs_launch_count():
+    c = C.c_uint64()
+    _check(_lib().rbfgs_launch_count(C.byref(c)), "rbfgs_launch_count")
+    return c.value
 
 
 def rbfgs_destroy(h):

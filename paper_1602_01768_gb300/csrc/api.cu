@@ -44,7 +44,23 @@ struct rb_ctx {
     double *rpart = nullptr, *rsum = nullptr;
 
     tc_plan *tc = nullptr;  // tensor-core plan (FP32 storage, TF32 modes)
+
+    // phase profiling (rbfgs_profile_step): events recorded between phases
+    int prof_on = 0, prof_n = 0;
+    cudaEvent_t prof_ev[24];
+    const char *prof_name[24];
 };
+
+std::atomic<unsigned long long> g_rb_launches{0};
+
+// Phase boundary: when profiling, record an event on the handle's stream
+// closing the phase that just ended.
+static inline void mark(rb_ctx *h, const char *ended)
+{
+    if (!h->prof_on || h->prof_n >= 23) return;
+    h->prof_name[h->prof_n] = ended;
+    cudaEventRecord(h->prof_ev[++h->prof_n], h->st);
+}
 
 static void rb_free(void *&p)
 {
@@ -304,14 +320,21 @@ static void rbfgs_step_gauss(rb_ctx *h)
     T *G = (T *)h->G, *Y = (T *)h->Y;
     launch_gauss_sketch<T>(st, n, q, h->seed, h->stream_id, h->k, S, n);
     launch_copy2d<T, T>(st, n, q, S, n, S2, n, 1.0);
+    mark(h, "sketch");
     gemm_simt<T>(st, false, false, n, q, n, T(1), A, n, S, n, T(0), G, n, stp);   // G = A S
+    mark(h, "G=AS");
     launch_gram<T>(st, n, q, q, S, n, G, n, h->part, h->M);                        // M = S^T A S
+    mark(h, "gram S^TAS");
     gemm_simt<T>(st, false, false, n, q, n, T(1), X, n, G, n, T(0), Y, n, stp);   // Y = X G
+    mark(h, "Y=XG");
     launch_gram<T>(st, n, q, q, G, n, Y, n, h->part, h->Tm);                       // T = G^T X G
     launch_core_rbfgs<T>(st, q, h->M, h->Tm, (T *)h->Lam, (T *)h->B1, h->d_status);
+    mark(h, "gram T + core");
     gemm_simt<T>(st, false, false, n, q, q, T(1), S, n, (T *)h->B1, q, T(0), Wp, n, stp);  // W = S B1
     gemm_simt<T>(st, false, false, n, q, q, T(-1), Y, n, (T *)h->Lam, q, T(1), Wp, n, stp); //   - Y Lam
+    mark(h, "W");
     gemm_simt<T>(st, false, true, n, n, 2 * q, T(1), S, n, Wp, n, T(1), X, n, stp);         // X += [S W][W S]^T
+    mark(h, "update X");
 }
 
 template <typename T>
@@ -323,12 +346,16 @@ static void rbfgs_step_coord(rb_ctx *h)
     T *A = (T *)h->A, *X = (T *)h->X, *G = (T *)h->G, *Y = (T *)h->Y, *W = (T *)h->W;
     launch_coord_trace_draw(st, n, q, h->nb, h->P, h->seed, h->stream_id, h->k, h->blk);
     launch_coord_gather<T>(st, n, q, A, n, h->blk, G, n, h->M, stp);               // G = A[:, C], M = A[C, C]
+    mark(h, "draw + gather");
     gemm_simt<T>(st, false, false, n, q, n, T(1), X, n, G, n, T(0), Y, n, stp);   // Y = X G
+    mark(h, "Y=XG");
     launch_gram<T>(st, n, q, q, G, n, Y, n, h->part, h->Tm);                       // T = G^T X G
     launch_core_rbfgs<T>(st, q, h->M, h->Tm, (T *)h->Lam, (T *)h->B1, h->d_status);
+    mark(h, "gram T + core");
     gemm_simt<T>(st, false, false, n, q, q, T(-1), Y, n, (T *)h->Lam, q, T(0), W, n, stp);  // W = -Y Lam
     launch_coord_add_b1<T>(st, q, h->blk, (const T *)h->B1, W, n, stp);                     //   + S B1
     launch_coord_update<T>(st, n, q, h->blk, W, n, X, n, stp);                               // rows/cols C
+    mark(h, "update rows/cols");
 }
 
 extern "C" rb_status rbfgs_step(rbfgs_t h, int nsteps)
@@ -376,16 +403,24 @@ static void ada_step_simt(rb_ctx *h)
     T *A = (T *)h->A, *L = (T *)h->X, *St = (T *)h->St, *S = (T *)h->S, *G = (T *)h->G;
     T *W = (T *)h->W, *V = (T *)h->V, *Sh = (T *)h->Sh, *Ci = (T *)h->Cinv, *Di = (T *)h->Dinv;
     ada_draw<T>(h, St);
+    mark(h, "sketch");
     gemm_simt<T>(st, false, false, n, q, n, T(1), L, n, St, n, T(0), S, n, stp);   // S = L S~
+    mark(h, "S=LS~");
     gemm_simt<T>(st, false, false, n, q, n, T(1), A, n, S, n, T(0), G, n, stp);    // G = A S
+    mark(h, "G=AS");
     launch_gram<T>(st, n, q, q, S, n, G, n, h->part, h->M);                         // S^T A S
     launch_gram<T>(st, n, q, q, St, n, St, n, h->part, h->N);                       // S~^T S~
+    mark(h, "grams");
     launch_core_ada<T>(st, q, h->M, h->N, Ci, Di, h->d_status);                     // C^-1, D^-1
+    mark(h, "q x q core");
     gemm_simt<T>(st, true, false, q, n, n, T(1), G, n, L, n, T(0), W, q, stp);     // W = G^T L
+    mark(h, "W=G^TL");
     gemm_simt<T>(st, false, true, q, n, q, T(1), Di, q, St, n, T(0), V, q, stp);   // V = D^-1 S~^T
     gemm_simt<T>(st, false, false, q, n, q, T(-1), Ci, q, W, q, T(1), V, q, stp);  //   - C^-1 W
     gemm_simt<T>(st, false, true, n, q, q, T(1), S, n, Ci, q, T(0), Sh, n, stp);   // S^ = S C^-T
+    mark(h, "V, S^");
     gemm_simt<T>(st, false, false, n, n, q, T(1), Sh, n, V, q, T(1), L, n, stp);   // L += S^ V
+    mark(h, "update L");
 }
 
 static void ada_step_tc(rb_ctx *h)
@@ -399,18 +434,26 @@ static void ada_step_tc(rb_ctx *h)
     const int acc = (h->prec == RB_TF32) ? 1 : 3;  // split terms of the accuracy-critical products
     const int upd = (h->prec == RB_TF32X3) ? 3 : 1;
     ada_draw<float>(h, St);
+    mark(h, "sketch");
     tc_gemm_nk(h->tc, st, acc, TC_A_MN, n, q, n, L, n, St, n, S, n, stp);   // S = L S~   (A = L, M-contiguous)
+    mark(h, "S=LS~");
     tc_gemm_nk(h->tc, st, acc, TC_A_K, n, q, n, A, n, S, n, G, n, stp);     // G = A S    (A symmetric)
+    mark(h, "G=AS");
     launch_gram<float>(st, n, q, q, S, n, G, n, h->part, h->M);
     launch_gram<float>(st, n, q, q, St, n, St, n, h->part, h->N);
+    mark(h, "grams");
     launch_core_ada<float>(st, q, h->M, h->N, Ci, Di, h->d_status);
+    mark(h, "q x q core");
     tc_gemm_nk(h->tc, st, acc, TC_A_K, n, q, n, L, n, G, n, W, n, stp);     // W^T = L^T G (n x q)
+    mark(h, "W=G^TL");
     // V = D^-1 S~^T - C^-1 W, stored q x n (ld q); W^T is n x q (ld n)
     gemm_simt<float>(st, false, true, q, n, q, 1.f, Di, q, St, n, 0.f, V, q, stp);
     gemm_simt<float>(st, false, true, q, n, q, -1.f, Ci, q, W, n, 1.f, V, q, stp);
     // S^ = S C^-T stored row-major (n x q with q contiguous) for the K-major update operand
     gemm_simt<float>(st, false, true, q, n, q, 1.f, Ci, q, S, n, 0.f, Sh, q, stp);  // S^^T = C^-1 S^T (q x n)
+    mark(h, "V, S^");
     tc_update(h->tc, st, upd, n, q, Sh, V, L, n, stp);                         // L += S^ V
+    mark(h, "update L");
 }
 
 extern "C" rb_status adarbfgs_step(rbfgs_t h, int nsteps)
@@ -752,15 +795,19 @@ static void ns_step_impl(rb_ctx *h)
             const int terms = (h->prec == RB_TF32) ? 1 : 3;
             tc_gemm_nk(h->tc, st, terms, TC_A_K, n, n, n, (const float *)A, n, (const float *)X, n, (float *)P, n,
                        nullptr);                                                                   // P = A X
+            mark(h, "P=AX");
             tc_gemm_nk_axpby(h->tc, st, terms, TC_A_MN, n, n, n, -1.f, (const float *)X, n, (const float *)P, n, 2.f,
                              (const float *)X, n, (float *)Xn, n);                                 // 2X - X P
+            mark(h, "X=2X-XP");
             std::swap(h->X, h->X3);
             return;
         }
     }
     gemm_simt<T>(st, false, false, n, n, n, T(1), A, n, X, n, T(0), P, n, nullptr);      // P = A X
+    mark(h, "P=AX");
     launch_copy2d<T, T>(st, n, n, X, n, Xn, n, 2.0);                                       // Xn = 2 X
     gemm_simt<T>(st, false, false, n, n, n, T(-1), X, n, P, n, T(1), Xn, n, nullptr);    // Xn -= X P
+    mark(h, "X=2X-XP");
     std::swap(h->X, h->X3);
 }
 
@@ -839,6 +886,110 @@ extern "C" rb_status mr_step(rbfgs_t h, int nsteps)
         ++h->k;
     }
     RB_CUDA(cudaGetLastError());
+    return RB_OK;
+}
+
+extern "C" rb_status rbfgs_reset(rbfgs_t h, uint64_t seed, uint64_t stream_id)
+{
+    if (!h || (h->method != RB_METHOD_RBFGS && h->method != RB_METHOD_ADARBFGS)) return RB_EINVAL;
+    if (h->f64)
+        launch_set_identity<double>(h->st, h->n, (double *)h->X, h->n, 1.0);
+    else
+        launch_set_identity<float>(h->st, h->n, (float *)h->X, h->n, 1.0f);
+    RB_CUDA(cudaMemsetAsync(h->d_status, 0, sizeof(int), h->st));
+    h->k = 0;
+    h->seed = seed;
+    h->stream_id = stream_id;
+    RB_CUDA(cudaGetLastError());
+    return RB_OK;
+}
+
+extern "C" rb_status rbfgs_launch_count(uint64_t *count)
+{
+    if (!count) return RB_EINVAL;
+    *count = g_rb_launches.load();
+    return RB_OK;
+}
+
+extern "C" rb_status rbfgs_profile_step(rbfgs_t h, double *ms, const char **names, int cap, int *nphases)
+{
+    if (!h || !ms || !nphases || cap < 1) return RB_EINVAL;
+    for (int i = 0; i < 24; ++i) RB_CUDA(cudaEventCreate(&h->prof_ev[i]));
+    h->prof_on = 1;
+    h->prof_n = 0;
+    cudaEventRecord(h->prof_ev[0], h->st);
+    rb_status s;
+    if (h->method == RB_METHOD_RBFGS)
+        s = rbfgs_step(h, 1);
+    else if (h->method == RB_METHOD_ADARBFGS)
+        s = adarbfgs_step(h, 1);
+    else if (h->method == RB_METHOD_NS)
+        s = newton_schulz_step(h, 1);
+    else
+        s = mr_step(h, 1);
+    h->prof_on = 0;
+    cudaError_t e = cudaEventSynchronize(h->prof_ev[h->prof_n]);
+    const int np = std::min(h->prof_n, cap);
+    for (int i = 0; i < np && e == cudaSuccess; ++i) {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, h->prof_ev[i], h->prof_ev[i + 1]);
+        ms[i] = t;
+        if (names) names[i] = h->prof_name[i];
+    }
+    for (int i = 0; i < 24; ++i) cudaEventDestroy(h->prof_ev[i]);
+    *nphases = np;
+    if (s != RB_OK) return s;
+    return e == cudaSuccess ? RB_OK : RB_ECUDA;
+}
+
+extern "C" rb_status rbfgs_load_host(rbfgs_t h, const void *A_host, int64_t lda, int a_is_fp64)
+{
+    if (!h || !A_host || lda < h->n || (h->method != RB_METHOD_RBFGS && h->method != RB_METHOD_ADARBFGS))
+        return RB_EINVAL;
+    const int n = h->n;
+    const size_t in_esz = a_is_fp64 ? 8 : 4;
+    if (in_esz == h->esz) {
+        RB_CUDA(cudaMemcpy2DAsync(h->A, h->esz * n, A_host, in_esz * lda, in_esz * n, n, cudaMemcpyHostToDevice,
+                                  h->st));
+    } else {
+        void *tmp = nullptr;
+        RB_TRY(rb_alloc(&tmp, in_esz * (size_t)n * n));
+        cudaMemcpy2DAsync(tmp, in_esz * n, A_host, in_esz * lda, in_esz * n, n, cudaMemcpyHostToDevice, h->st);
+        if (a_is_fp64)
+            launch_copy2d<double, float>(h->st, n, n, (const double *)tmp, n, (float *)h->A, n, 1.0);
+        else
+            launch_copy2d<float, double>(h->st, n, n, (const float *)tmp, n, (double *)h->A, n, 1.0);
+        cudaStreamSynchronize(h->st);
+        cudaFree(tmp);
+    }
+    if (h->f64)
+        launch_set_identity<double>(h->st, n, (double *)h->X, n, 1.0);
+    else
+        launch_set_identity<float>(h->st, n, (float *)h->X, n, 1.0f);
+    RB_CUDA(cudaMemsetAsync(h->d_status, 0, sizeof(int), h->st));
+    h->k = 0;
+    if (h->method == RB_METHOD_RBFGS && h->sketch == RB_SKETCH_COORD_TRACE) {
+        rb_freet(h->P);
+        RB_TRY(build_trace_weights(h));
+    }
+    RB_CUDA(cudaGetLastError());
+    return RB_OK;
+}
+
+extern "C" rb_status rbfgs_export_host(rbfgs_t h, int what, void *out_host, int64_t ld)
+{
+    if (!h || !out_host || ld < h->n) return RB_EINVAL;
+    const int n = h->n;
+    const void *src = h->X;
+    if (what == RB_WHAT_X && h->method == RB_METHOD_ADARBFGS) {
+        RB_TRY(h->X2 ? RB_OK : rb_alloc(&h->X2, h->esz * (size_t)n * n));
+        RB_TRY(rbfgs_export(h, what, h->X2, n));
+        src = h->X2;
+    } else if (what == RB_WHAT_L && h->method != RB_METHOD_ADARBFGS) {
+        return RB_EINVAL;
+    }
+    RB_CUDA(cudaMemcpy2DAsync(out_host, h->esz * ld, src, h->esz * n, h->esz * n, n, cudaMemcpyDeviceToHost, h->st));
+    RB_CUDA(cudaStreamSynchronize(h->st));
     return RB_OK;
 }
 

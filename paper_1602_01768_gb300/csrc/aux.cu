@@ -47,7 +47,9 @@ void launch_resid_sumsq(cudaStream_t st, int n, int m, const T *Z, int64_t ldz, 
 {
     const int bx = min(ceil_div(n, 256), 32);
     dim3 grid(bx, m);
+    rb_count_launch();
     k_resid_partial<T><<<grid, 256, 0, st>>>(n, m, Z, ldz, J, part);
+    rb_count_launch();
     k_sum_fixed<<<1, 256, 0, st>>>(bx * m, part, out);
 }
 template void launch_resid_sumsq<float>(cudaStream_t, int, int, const float *, int64_t, const int *, double *,
@@ -67,6 +69,7 @@ template <typename T>
 void launch_gather_cols(cudaStream_t st, int n, int m, const T *A, int64_t lda, const int *J, T *Y, int64_t ldy)
 {
     dim3 grid(ceil_div(n, 256), m);
+    rb_count_launch();
     k_gather_cols<T><<<grid, 256, 0, st>>>(n, m, A, lda, J, Y, ldy);
 }
 template void launch_gather_cols<float>(cudaStream_t, int, int, const float *, int64_t, const int *, float *,
@@ -119,8 +122,10 @@ void launch_coord_gather(cudaStream_t st, int n, int q, const T *A, int64_t lda,
                          double *Mpad, const int *status)
 {
     dim3 grid(ceil_div(n, 256), q);
+    rb_count_launch();
     k_coord_gather<T><<<grid, 256, 0, st>>>(n, q, A, lda, blk, G, ldg, Mpad, status);
     dim3 g2(ceil_div(q, 128), q);
+    rb_count_launch();
     k_coord_pad_rows<<<g2, 128, 0, st>>>(n, q, blk, Mpad, status);
 }
 template void launch_coord_gather<float>(cudaStream_t, int, int, const float *, int64_t, const int *, float *,
@@ -141,6 +146,7 @@ __global__ void k_coord_add_b1(int q, const int *blk, const T *B1, T *W, int64_t
 template <typename T>
 void launch_coord_add_b1(cudaStream_t st, int q, const int *blk, const T *B1, T *W, int64_t ldw, const int *status)
 {
+    rb_count_launch();
     k_coord_add_b1<T><<<q, q, 0, st>>>(q, blk, B1, W, ldw, status);
 }
 template void launch_coord_add_b1<float>(cudaStream_t, int, const int *, const float *, float *, int64_t,
@@ -183,7 +189,9 @@ void launch_coord_update(cudaStream_t st, int n, int q, const int *blk, const T 
                          const int *status)
 {
     dim3 g1(ceil_div(n, 256), q);
+    rb_count_launch();
     k_coord_update_cols<T><<<g1, 256, 0, st>>>(n, q, blk, W, ldw, X, ldx, status);
+    rb_count_launch();
     k_coord_update_rows<T><<<ceil_div(n, 8), 256, 0, st>>>(n, q, blk, W, ldw, X, ldx, status);
 }
 template void launch_coord_update<float>(cudaStream_t, int, int, const int *, const float *, int64_t, float *,
@@ -243,7 +251,9 @@ void launch_mr_dots(cudaStream_t st, int n, const T *P, int64_t ldp, const T *Q,
                     double *out)
 {
     const int blocks = 512;
+    rb_count_launch();
     k_mr_dots_partial<T><<<blocks, 256, 0, st>>>(n, P, ldp, Q, ldq, part);
+    rb_count_launch();
     k_sum2_fixed<<<1, 32, 0, st>>>(blocks, part, out);
 }
 template void launch_mr_dots<float>(cudaStream_t, int, const float *, int64_t, const float *, int64_t, double *,
@@ -266,6 +276,7 @@ template <typename T>
 void launch_i_minus(cudaStream_t st, int n, T *P, int64_t ld)
 {
     dim3 grid(ceil_div(n, 256), n);
+    rb_count_launch();
     k_i_minus<T><<<grid, 256, 0, st>>>(n, P, ld);
 }
 template void launch_i_minus<float>(cudaStream_t, int, float *, int64_t);
@@ -285,6 +296,7 @@ template <typename T>
 void launch_axpy_dev(cudaStream_t st, int n, const double *dots, const T *D, int64_t ldd, T *X, int64_t ldx)
 {
     dim3 grid(ceil_div(n, 256), n);
+    rb_count_launch();
     k_axpy_dev<T><<<grid, 256, 0, st>>>(n, dots, D, ldd, X, ldx);
 }
 template void launch_axpy_dev<float>(cudaStream_t, int, const double *, const float *, int64_t, float *, int64_t);
@@ -331,9 +343,12 @@ template <typename T>
 void launch_power_iteration(cudaStream_t st, int n, const T *A, int64_t lda, int iters, double *v, double *w,
                             double *sigma)
 {
+    rb_count_launch();
     k_fill<<<ceil_div(n, 256), 256, 0, st>>>(n, v, 1.0 / sqrt((double)n));
     for (int it = 0; it < iters; ++it) {
+        rb_count_launch();
         k_gemv_sq<T><<<ceil_div(n, 8), 256, 0, st>>>(n, A, lda, v, w);
+        rb_count_launch();
         k_normalize<<<1, 256, 0, st>>>(n, w, v, sigma);
     }
 }

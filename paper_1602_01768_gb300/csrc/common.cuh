@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <atomic>
+
 #include "rbfgs.h"
 
 // Device status word bits (rb_ctx::d_status).  Kernels that modify the
@@ -68,3 +70,7 @@ __host__ __device__ __forceinline__ float u24f(uint32_t x) { return ((float)(x >
 __host__ __device__ __forceinline__ double u24d(uint32_t x) { return ((double)(x >> 8) + 0.5) * (1.0 / 16777216.0); }
 
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// Kernels launched by this library since load (host-side count, one per launch).
+extern std::atomic<unsigned long long> g_rb_launches;
+inline void rb_count_launch() { g_rb_launches.fetch_add(1, std::memory_order_relaxed); }

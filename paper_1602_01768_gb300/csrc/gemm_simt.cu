@@ -102,11 +102,13 @@ static void gemm_dispatch(cudaStream_t st, int M, int N, int K, T alpha, const T
         if (N <= 32) {
             constexpr int BM = 128, BN = 32, BK = 16, TM = 8, TN = 2;
             dim3 grid(ceil_div(M, BM), ceil_div(N, BN));
+            rb_count_launch();
             k_gemm<T, BM, BN, BK, TM, TN, TA, TB>
                 <<<grid, (BM / TM) * (BN / TN), 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, status);
         } else {
             constexpr int BM = 128, BN = 64, BK = 16, TM = 8, TN = 4;
             dim3 grid(ceil_div(M, BM), ceil_div(N, BN));
+            rb_count_launch();
             k_gemm<T, BM, BN, BK, TM, TN, TA, TB>
                 <<<grid, (BM / TM) * (BN / TN), 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, status);
         }
@@ -114,11 +116,13 @@ static void gemm_dispatch(cudaStream_t st, int M, int N, int K, T alpha, const T
         if (N <= 16) {
             constexpr int BM = 64, BN = 16, BK = 16, TM = 4, TN = 1;
             dim3 grid(ceil_div(M, BM), ceil_div(N, BN));
+            rb_count_launch();
             k_gemm<T, BM, BN, BK, TM, TN, TA, TB>
                 <<<grid, (BM / TM) * (BN / TN), 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, status);
         } else {
             constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4;
             dim3 grid(ceil_div(M, BM), ceil_div(N, BN));
+            rb_count_launch();
             k_gemm<T, BM, BN, BK, TM, TN, TA, TB>
                 <<<grid, (BM / TM) * (BN / TN), 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, status);
         }

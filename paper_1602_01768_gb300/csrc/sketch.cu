@@ -47,6 +47,7 @@ void launch_gauss_sketch(cudaStream_t st, int n, int q, uint64_t seed, uint64_t 
                          int64_t lds)
 {
     dim3 grid(ceil_div((n + 3) / 4, 128), q);
+    rb_count_launch();
     k_gauss_sketch<T><<<grid, 128, 0, st>>>(n, q, seed, stream, k, S, lds);
 }
 template void launch_gauss_sketch<float>(cudaStream_t, int, int, uint64_t, uint64_t, uint64_t, float *, int64_t);
@@ -77,6 +78,7 @@ __global__ void k_coord_trace_draw(int n, int q, int nb, const uint64_t *P, uint
 void launch_coord_trace_draw(cudaStream_t st, int n, int q, int nb, const uint64_t *P, uint64_t seed,
                              uint64_t stream, uint64_t k, int *blk)
 {
+    rb_count_launch();
     k_coord_trace_draw<<<1, 32, 0, st>>>(n, q, nb, P, seed, stream, k, blk);
 }
 
@@ -108,6 +110,7 @@ __global__ void k_floyd_draw(int n, int q, uint64_t seed, uint64_t stream, uint6
 
 void launch_floyd_draw(cudaStream_t st, int n, int q, uint64_t seed, uint64_t stream, uint64_t k, int *idx)
 {
+    rb_count_launch();
     k_floyd_draw<<<1, 32, 0, st>>>(n, q, seed, stream, k, idx);
 }
 
@@ -125,6 +128,7 @@ template <typename T>
 void launch_coord_matrix(cudaStream_t st, int n, int q, const int *idx, T *S, int64_t lds)
 {
     dim3 grid(ceil_div(n, 256), q);
+    rb_count_launch();
     k_coord_matrix<T><<<grid, 256, 0, st>>>(n, q, idx, S, lds);
 }
 template void launch_coord_matrix<float>(cudaStream_t, int, int, const int *, float *, int64_t);
@@ -144,6 +148,7 @@ template <typename T>
 void launch_block_matrix(cudaStream_t st, int n, int q, const int *blk, T *S, int64_t lds)
 {
     dim3 grid(ceil_div(n, 256), q);
+    rb_count_launch();
     k_block_matrix<T><<<grid, 256, 0, st>>>(n, q, blk, S, lds);
 }
 template void launch_block_matrix<float>(cudaStream_t, int, int, const int *, float *, int64_t);

@@ -60,7 +60,9 @@ void launch_gram(cudaStream_t st, int n, int p, int r, const T *X, int64_t ldx, 
 {
     const int nch = ceil_div(n, GRAM_CHUNK);
     dim3 grid(ceil_div(p, 32), ceil_div(r, 32), nch);
+    rb_count_launch();
     k_gram_partial<T><<<grid, 256, 0, st>>>(n, p, r, X, ldx, Y, ldy, part);
+    rb_count_launch();
     k_gram_reduce<<<ceil_div(p * r, 256), 256, 0, st>>>(nch, p * r, part, out);
 }
 template void launch_gram<float>(cudaStream_t, int, int, int, const float *, int64_t, const float *, int64_t,
@@ -173,6 +175,7 @@ void launch_core_ada(cudaStream_t st, int q, const double *M, const double *N, T
         cudaFuncSetAttribute(k_core_ada<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
         attr_set = true;
     }
+    rb_count_launch();
     k_core_ada<T><<<2, 512, smem, st>>>(q, M, N, Cinv, Dinv, status);
 }
 template void launch_core_ada<float>(cudaStream_t, int, const double *, const double *, float *, float *, int *);
@@ -234,6 +237,7 @@ void launch_core_rbfgs(cudaStream_t st, int q, const double *M, const double *Tm
         cudaFuncSetAttribute(k_core_rbfgs<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
         attr_set = true;
     }
+    rb_count_launch();
     k_core_rbfgs<T><<<1, 512, smem, st>>>(q, M, Tm, Lam, B1, status);
 }
 template void launch_core_rbfgs<float>(cudaStream_t, int, const double *, const double *, float *, float *, int *);
@@ -255,6 +259,7 @@ template <typename T>
 void launch_set_identity(cudaStream_t st, int n, T *X, int64_t ld, T diag)
 {
     dim3 grid(ceil_div(n, 256), n);
+    rb_count_launch();
     k_set_identity<T><<<grid, 256, 0, st>>>(n, X, ld, diag);
 }
 template void launch_set_identity<float>(cudaStream_t, int, float *, int64_t, float);
@@ -273,6 +278,7 @@ template <typename Ti, typename To>
 void launch_copy2d(cudaStream_t st, int rows, int cols, const Ti *X, int64_t ldx, To *Y, int64_t ldy, double alpha)
 {
     dim3 grid(ceil_div(rows, 256), cols);
+    rb_count_launch();
     k_copy2d<Ti, To><<<grid, 256, 0, st>>>(rows, cols, X, ldx, Y, ldy, alpha);
 }
 template void launch_copy2d<float, float>(cudaStream_t, int, int, const float *, int64_t, float *, int64_t, double);
@@ -293,6 +299,7 @@ __global__ void k_diag(int n, const T *A, int64_t lda, double *d)
 template <typename T>
 void launch_diag(cudaStream_t st, int n, const T *A, int64_t lda, double *d)
 {
+    rb_count_launch();
     k_diag<T><<<ceil_div(n, 256), 256, 0, st>>>(n, A, lda, d);
 }
 template void launch_diag<float>(cudaStream_t, int, const float *, int64_t, double *);

@@ -502,10 +502,12 @@ static int launch_bn(tc_plan *p, cudaStream_t st, const CUtensorMap &ma, const C
         part = p->part;
     }
     dim3 grid(mt, nt, splits);
+    rb_count_launch();
     k_tc_gemm<BN, TERMS, AMN><<<grid, 256, CF::SMEM, st>>>(ma, mb, M, N, nkb, kbps, alpha, beta, Cin, ldcin, C, ldc,
                                                            part, status, err);
     if (splits > 1) {
         dim3 g2((M + 255) / 256, N);
+        rb_count_launch();
         k_splitk_reduce<<<g2, 256, 0, st>>>(M, N, splits, part, alpha, beta, Cin, ldcin, C, ldc);
     }
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
