@@ -191,6 +191,27 @@ rb_status mr_step(rbfgs_t h, int nsteps);
 rb_status rbfgs_sigma(rbfgs_t h, double *sigma);
 
 /*
+ * The same power-iteration estimate of ||A||_2 as newton_schulz_init, for
+ * callers that cannot allocate device memory: services that fix their
+ * device-memory plan at start-up (cudaMalloc can synchronise the device and
+ * fragment a pool an outer allocator owns) or code whose framework allocator
+ * must own every byte.  The paper has no counterpart; this is a library
+ * convenience.  Allocates nothing: its scratch (two n-vectors and a scalar)
+ * lives in a static device array of the library, 1 MiB per device that loads
+ * the library, held until the process exits.
+ *   n, A_dev, lda, a_is_fp64: the SPD matrix (device pointer, column-major).
+ *   power_iters: iterations from v0 = 1/sqrt(n) (0 = 100), as for
+ *   newton_schulz_init.  *sigma_out receives ||A v|| after the last one.
+ * n > 65536 is rejected with RB_EINVAL.  The first call on a device looks
+ * up the scratch's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls share
+ * the one scratch array: calls that overlap on the GPU (other streams, other
+ * host threads) race.  Synchronises the stream.
+ */
+rb_status rbfgs_sigma_noalloc(int n, const void *A_dev, int64_t lda, int a_is_fp64, int power_iters,
+                              double *sigma_out, void *stream);
+
+/*
  * Host-buffer entry points (the end-to-end path of a caller whose data is in
  * host memory).  rbfgs_load_host copies a new A from A_host (ld lda, FP32 or
  * FP64 elements) into an existing RBFGS/AdaRBFGS handle of the same n and

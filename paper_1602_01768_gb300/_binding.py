@@ -58,6 +58,7 @@ _SIGS = {
     "mr_init": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_void_p]),
     "mr_step": (C.c_int, [C.c_void_p, C.c_int]),
     "rbfgs_sigma": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "rbfgs_sigma_noalloc": (C.c_int, [C.c_int, C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
     "rbfgs_load_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int]),
     "rbfgs_export_host": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64]),
     "rbfgs_profile_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
@@ -202,6 +203,13 @@ def mr_step(h, nsteps):
 def rbfgs_sigma(h):
     s = C.c_double()
     _check(_lib().rbfgs_sigma(h, C.byref(s)), "rbfgs_sigma")
+    return s.value
+
+
+def rbfgs_sigma_noalloc(n, A_dev, lda, a_is_fp64, power_iters=0, stream=0):
+    s = C.c_double()
+    _check(_lib().rbfgs_sigma_noalloc(n, _p(A_dev), lda, int(a_is_fp64), power_iters, C.byref(s), _p(stream)),
+           "rbfgs_sigma_noalloc")
     return s.value
 
 
