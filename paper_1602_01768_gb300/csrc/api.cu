@@ -452,7 +452,9 @@ static void ada_step_tc(rb_ctx *h)
     // S^ = S C^-T stored row-major (n x q with q contiguous) for the K-major update operand
     gemm_simt<float>(st, false, true, q, n, q, 1.f, Ci, q, S, n, 0.f, Sh, q, stp);  // S^^T = C^-1 S^T (q x n)
     mark(h, "V, S^");
-    tc_update(h->tc, st, upd, n, q, Sh, V, L, n, stp);                         // L += S^ V
+    // L += S^ V: persistent HBM-streaming kernel for the single-pass form
+    if (upd != 1 || tc_update_persistent(h->tc, st, n, q, Sh, V, L, n, stp) != 0)
+        tc_update(h->tc, st, upd, n, q, Sh, V, L, n, stp);
     mark(h, "update L");
 }
 

@@ -34,3 +34,14 @@ int tc_update(tc_plan *p, cudaStream_t st, int terms, int n, int q, const float 
 
 // Device error word of the plan's kernels (bounded waits that gave up).
 int tc_plan_error(tc_plan *p, cudaStream_t st);
+
+// Host helpers shared by the tensor-core kernels.
+struct CUtensorMap_st;
+bool tc_make_map(CUtensorMap_st *map, const float *ptr, int inner, int outer, int64_t ld, int box_inner,
+                 int box_outer, int swizzle128);
+int tc_num_sms();
+
+// Persistent rank-q update L += S^ V (see tc_update.cu); returns 0 when it
+// ran on the tensor cores, 1 when the shape needs the generic kernel.
+int tc_update_persistent(tc_plan *p, cudaStream_t st, int n, int q, const float *ShT, const float *V, float *L,
+                         int64_t ldl, const int *status);

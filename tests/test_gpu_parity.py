@@ -196,6 +196,28 @@ def test_adarbfgs_tf32x3_one_step_from_general_L():
         B.rbfgs_destroy(h)
 
 
+@pytest.mark.parametrize("n,q", [(1000, 64), (780, 32), (512, 128)])
+def test_adarbfgs_mixed_one_step_from_general_L(n, q):
+    # the single-pass TF32 persistent update kernel (ragged tiles when n % 128 != 0)
+    n = n - (n % 4)  # TMA needs 16-byte rows
+    A = wl.c2_matrix(n=n).astype(np.float32).astype(np.float64)
+    rng = np.random.default_rng(5)
+    L0 = (np.eye(n) + 0.05 * rng.standard_normal((n, n))).astype(np.float32).astype(np.float64)
+    h = _handle(A, B.RB_METHOD_ADARBFGS, B.RB_SKETCH_GAUSS, q, B.RB_MIXED, seed=14)
+    try:
+        Ld = to_dev(L0, torch_dtype(B.RB_MIXED))
+        B.rbfgs_import(h, B.RB_WHAT_L, Ld.data_ptr(), n)
+        B.rbfgs_set_step(h, 3)
+        B.adarbfgs_step(h, 1)
+        _, L1 = orc.adarbfgs_run(A, L0, q, orc.SKETCH_GAUSS, 14, 0, 3, 1)
+        Lg = export(h, n, B.RB_MIXED, B.RB_WHAT_L)
+        # single-pass TF32 on the correction S^ V only: error ~ 2^-11 |S^ V|
+        assert rel(Lg - L0, L1 - L0) <= 2e-3
+        assert rel(Lg, L1) <= 2e-4
+    finally:
+        B.rbfgs_destroy(h)
+
+
 def test_adarbfgs_mixed_reaches_tolerance_like_oracle():
     n, q, tol = 512, 32, 1e-4
     A = wl.c2_matrix(n=n).astype(np.float32).astype(np.float64)
