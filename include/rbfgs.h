@@ -87,7 +87,9 @@ typedef struct {
     uint64_t seed;      /* Philox key of the sketch stream */
     uint64_t stream_id; /* Philox counter word 3: independent streams for one seed */
     int32_t power_iters;/* Newton-Schulz: power iterations for ||A||_2 (0 = 100) */
-    int32_t reserved[7];
+    int32_t core_fp64;  /* AdaRBFGS with FP32 storage: 1 = factor the q x q matrices in FP64,
+                           0 = in FP32 (default; the matrices are only FP32-accurate there) */
+    int32_t reserved[6];
 } rb_opts;
 
 /* Fill *opts with defaults: RBFGS, Gaussian sketch, q = 8, FP64, seed 0, stream 0. */
@@ -114,8 +116,9 @@ rb_status rbfgs_step(rbfgs_t h, int nsteps);
 
 /*
  * nsteps AdaRBFGS steps (Algorithm 4, Eq. (Cholimprov)): draw S~_k,
- * S = L S~, G = A S, C C^T = S^T A S and D D^T = S~^T S~ (lower Cholesky),
- * W = G^T L, V = D^-1 S~^T - C^-1 W, L += S C^-T V.  Asynchronous.
+ * S = L S~, G = A S, C C^T = S^T A S and D D^T = S~^T S~ (lower Cholesky;
+ * FP64 for RB_FP64 storage or opts.core_fp64, else FP32), W = G^T L,
+ * V = D^-1 S~^T - C^-1 W, L += S C^-T V.  Asynchronous.
  */
 rb_status adarbfgs_step(rbfgs_t h, int nsteps);
 

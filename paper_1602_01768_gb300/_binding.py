@@ -24,7 +24,7 @@ PREC = {"fp64": RB_FP64, "fp32": RB_FP32, "tf32": RB_TF32, "tf32x3": RB_TF32X3, 
 class RbOpts(C.Structure):
     _fields_ = [("method", C.c_int32), ("sketch", C.c_int32), ("q", C.c_int32), ("prec", C.c_int32),
                 ("seed", C.c_uint64), ("stream_id", C.c_uint64), ("power_iters", C.c_int32),
-                ("reserved", C.c_int32 * 7)]
+                ("core_fp64", C.c_int32), ("reserved", C.c_int32 * 6)]
 
 
 class RbfgsError(RuntimeError):
@@ -117,10 +117,10 @@ def rbfgs_default_opts():
 
 
 def make_opts(method=RB_METHOD_RBFGS, sketch=RB_SKETCH_GAUSS, q=8, prec=RB_FP64, seed=0, stream_id=0,
-              power_iters=0):
+              power_iters=0, core_fp64=0):
     o = rbfgs_default_opts()
     o.method, o.sketch, o.q, o.prec = method, sketch, q, prec
-    o.seed, o.stream_id, o.power_iters = seed, stream_id, power_iters
+    o.seed, o.stream_id, o.power_iters, o.core_fp64 = seed, stream_id, power_iters, int(core_fp64)
     return o
 
 

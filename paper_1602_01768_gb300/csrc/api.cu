@@ -12,7 +12,7 @@
 #include "tc.cuh"
 
 struct rb_ctx {
-    int method = 0, sketch = 0, prec = 0;
+    int method = 0, sketch = 0, prec = 0, core_fp64 = 0;
     int n = 0, q = 0;
     bool f64 = false;
     uint64_t seed = 0, stream_id = 0, k = 0;
@@ -272,6 +272,7 @@ extern "C" rb_status rbfgs_init(rbfgs_t *out, int n, const void *A_dev, int64_t 
     h->esz = h->f64 ? 8 : 4;
     h->seed = opts->seed;
     h->stream_id = opts->stream_id;
+    h->core_fp64 = opts->core_fp64 ? 1 : 0;
     h->st = (cudaStream_t)stream;
     rb_status s = RB_OK;
     do {
@@ -411,7 +412,14 @@ static void ada_step_simt(rb_ctx *h)
     launch_gram<T>(st, n, q, q, S, n, G, n, h->part, h->M);                         // S^T A S
     launch_gram<T>(st, n, q, q, St, n, St, n, h->part, h->N);                       // S~^T S~
     mark(h, "grams");
-    launch_core_ada<T>(st, q, h->M, h->N, Ci, Di, h->d_status);                     // C^-1, D^-1
+    if constexpr (sizeof(T) == 4) {
+        if (!h->core_fp64)
+            launch_core_ada32(st, q, h->M, h->N, Ci, Di, h->d_status);                  // C^-1, D^-1 (FP32)
+        else
+            launch_core_ada<T>(st, q, h->M, h->N, Ci, Di, h->d_status);
+    } else {
+        launch_core_ada<T>(st, q, h->M, h->N, Ci, Di, h->d_status);                 // C^-1, D^-1 (FP64)
+    }
     mark(h, "q x q core");
     gemm_simt<T>(st, true, false, q, n, n, T(1), G, n, L, n, T(0), W, q, stp);     // W = G^T L
     mark(h, "W=G^TL");
@@ -442,7 +450,10 @@ static void ada_step_tc(rb_ctx *h)
     launch_gram<float>(st, n, q, q, S, n, G, n, h->part, h->M);
     launch_gram<float>(st, n, q, q, St, n, St, n, h->part, h->N);
     mark(h, "grams");
-    launch_core_ada<float>(st, q, h->M, h->N, Ci, Di, h->d_status);
+    if (!h->core_fp64)
+        launch_core_ada32(st, q, h->M, h->N, Ci, Di, h->d_status);
+    else
+        launch_core_ada<float>(st, q, h->M, h->N, Ci, Di, h->d_status);
     mark(h, "q x q core");
     tc_gemm_nk(h->tc, st, acc, TC_A_K, n, q, n, L, n, G, n, W, n, stp);     // W^T = L^T G (n x q)
     mark(h, "W=G^TL");

@@ -26,6 +26,7 @@ void launch_gram(cudaStream_t, int n, int p, int r, const T *X, int64_t ldx, con
                  double *out);
 template <typename T>
 void launch_core_ada(cudaStream_t, int q, const double *M, const double *N, T *Cinv, T *Dinv, int *status);
+void launch_core_ada32(cudaStream_t, int q, const double *M, const double *N, float *Cinv, float *Dinv, int *status);
 template <typename T>
 void launch_core_rbfgs(cudaStream_t, int q, const double *M, const double *Tm, T *Lam, T *B1, int *status);
 template <typename T>

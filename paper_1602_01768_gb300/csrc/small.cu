@@ -54,11 +54,69 @@ __global__ void k_gram_reduce(int nchunks, int pr, const double *part, double *o
     out[e] = s;
 }
 
+// One CTA per GRAM_CHUNK rows computing all p x r outputs (p, r <= 128):
+// rows are staged 32 at a time in shared memory; thread (tx, ty) of a 16 x 16
+// grid owns outputs (ty + 16 a, tx + 16 b).  FP32 products summed over the
+// chunk, written as one FP64 partial per chunk.
+template <typename T>
+__global__ void __launch_bounds__(256) k_gram_chunk(int n, int p, int r, const T *__restrict__ X, int64_t ldx,
+                                                    const T *__restrict__ Y, int64_t ldy, double *part)
+{
+    __shared__ T xs[32][128 + 4];
+    __shared__ T ys[32][128 + 4];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int row0 = blockIdx.x * GRAM_CHUNK;
+    T acc[8][8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) acc[a][b] = T(0);
+    for (int rb = row0; rb < row0 + GRAM_CHUNK && rb < n; rb += 32) {
+        for (int e = threadIdx.x; e < 32 * 128; e += 256) {
+            const int rr = e & 31, cc = e >> 5;
+            const int row = rb + rr;
+            xs[rr][cc] = (row < n && cc < p) ? X[row + (int64_t)cc * ldx] : T(0);
+            ys[rr][cc] = (row < n && cc < r) ? Y[row + (int64_t)cc * ldy] : T(0);
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int rr = 0; rr < 32; ++rr) {
+            T xv[8], yv[8];
+#pragma unroll
+            for (int a = 0; a < 8; ++a) xv[a] = xs[rr][ty + 16 * a];
+#pragma unroll
+            for (int b = 0; b < 8; ++b) yv[b] = ys[rr][tx + 16 * b];
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+#pragma unroll
+                for (int b = 0; b < 8; ++b) acc[a][b] = fma(xv[a], yv[b], acc[a][b]);
+        }
+        __syncthreads();
+    }
+    double *out = part + (size_t)blockIdx.x * p * r;
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) {
+            const int i = ty + 16 * a, j = tx + 16 * b;
+            if (i < p && j < r) out[i + (size_t)j * p] = (double)acc[a][b];
+        }
+}
+
 template <typename T>
 void launch_gram(cudaStream_t st, int n, int p, int r, const T *X, int64_t ldx, const T *Y, int64_t ldy,
                  double *part, double *out)
 {
     const int nch = ceil_div(n, GRAM_CHUNK);
+    if constexpr (sizeof(T) == 4) {
+        if (p <= 128 && r <= 128) {
+            rb_count_launch();
+            k_gram_chunk<T><<<nch, 256, 0, st>>>(n, p, r, X, ldx, Y, ldy, part);
+            rb_count_launch();
+            k_gram_reduce<<<ceil_div(p * r, 256), 256, 0, st>>>(nch, p * r, part, out);
+            return;
+        }
+    }
     dim3 grid(ceil_div(p, 32), ceil_div(r, 32), nch);
     rb_count_launch();
     k_gram_partial<T><<<grid, 256, 0, st>>>(n, p, r, X, ldx, Y, ldy, part);

@@ -211,9 +211,11 @@ def test_adarbfgs_mixed_one_step_from_general_L(n, q):
         B.adarbfgs_step(h, 1)
         _, L1 = orc.adarbfgs_run(A, L0, q, orc.SKETCH_GAUSS, 14, 0, 3, 1)
         Lg = export(h, n, B.RB_MIXED, B.RB_WHAT_L)
-        # single-pass TF32 on the correction S^ V only: error ~ 2^-11 |S^ V|
-        assert rel(Lg - L0, L1 - L0) <= 2e-3
-        assert rel(Lg, L1) <= 2e-4
+        # single-pass TF32 on the correction S^ V only: error ~ 2^-11 |S^ V|,
+        # so relative to L the bound scales with |L1 - L0| / |L1|
+        corr = rel(Lg - L0, L1 - L0)
+        assert corr <= 2e-3
+        assert rel(Lg, L1) <= 2e-3 * np.linalg.norm(L1 - L0) / np.linalg.norm(L1) + 1e-5
     finally:
         B.rbfgs_destroy(h)
 
