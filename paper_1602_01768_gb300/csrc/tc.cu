@@ -45,24 +45,33 @@ struct Cfg {
 
 __device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
 
-// In-place hi/lo split of a tile of `bytes` bytes (layout preserved).
-__device__ __forceinline__ void split_tile(unsigned char *hi, unsigned char *lo, int bytes, int t)
+// lo = x - hi(x) for a tile of `bytes` bytes (layout preserved).  The tensor
+// core reads an FP32 operand of kind::tf32 as its top 19 bits (the low 13
+// mantissa bits are dropped, not rounded), so the raw tile already is the hi
+// part and only lo is written.
+__device__ __forceinline__ void split_lo(const unsigned char *x, unsigned char *lo, int bytes, int t)
 {
-    float4 *a = (float4 *)hi;
+    const float4 *a = (const float4 *)x;
     float4 *b = (float4 *)lo;
     for (int e = t; e < bytes / 16; e += 128) {
         const float4 v = a[e];
-        float4 h, l;
-        h.x = tf32_hi(v.x);
-        h.y = tf32_hi(v.y);
-        h.z = tf32_hi(v.z);
-        h.w = tf32_hi(v.w);
-        l.x = v.x - h.x;
-        l.y = v.y - h.y;
-        l.z = v.z - h.z;
-        l.w = v.w - h.w;
-        a[e] = h;
+        float4 l;
+        l.x = v.x - tf32_hi(v.x);
+        l.y = v.y - tf32_hi(v.y);
+        l.z = v.z - tf32_hi(v.z);
+        l.w = v.w - tf32_hi(v.w);
         b[e] = l;
+    }
+}
+
+// lo = x - hi(x), elementwise over a column-major rows x cols panel (ld).
+__global__ void k_split_lo(int rows, int cols, const float *X, int64_t ldx, float *L, int64_t ldl)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i < rows) {
+        const float v = X[i + (int64_t)j * ldx];
+        L[i + (int64_t)j * ldl] = v - tf32_hi(v);
     }
 }
 
@@ -83,27 +92,22 @@ __device__ __forceinline__ void transpose_tile(const unsigned char *raw, unsigne
             v[u] = *(const float *)(src + k * 128 + ((((mi >> 2) ^ (k & 7))) << 4));
         }
         const int off = m * 128 + ((kq ^ (m & 7)) << 4);
+        *(float4 *)(hi + off) = make_float4(v[0], v[1], v[2], v[3]);  // the MMA truncates to TF32 itself
         if (lo) {
-            float4 h, l;
-            h.x = tf32_hi(v[0]);
-            h.y = tf32_hi(v[1]);
-            h.z = tf32_hi(v[2]);
-            h.w = tf32_hi(v[3]);
-            l.x = v[0] - h.x;
-            l.y = v[1] - h.y;
-            l.z = v[2] - h.z;
-            l.w = v[3] - h.w;
-            *(float4 *)(hi + off) = h;
+            float4 l;
+            l.x = v[0] - tf32_hi(v[0]);
+            l.y = v[1] - tf32_hi(v[1]);
+            l.z = v[2] - tf32_hi(v[2]);
+            l.w = v[3] - tf32_hi(v[3]);
             *(float4 *)(lo + off) = l;
-        } else {
-            *(float4 *)(hi + off) = make_float4(v[0], v[1], v[2], v[3]);
         }
     }
 }
 
 template <int BN, int TERMS, int AMN>
 __global__ void __launch_bounds__(256, 1)
-k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N, int nkb,
+k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+          const __grid_constant__ CUtensorMap tmBlo, int M, int N, int nkb,
           int kb_per_split, float alpha, float beta, const float *Cin, int64_t ldcin, float *C, int64_t ldc,
           float *part, const int *status, int *err)
 {
@@ -164,7 +168,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                 const int s = i % STAGES;
                 if (i >= STAGES && !mbar_wait(smem_u32(&empty[s]), ((i / STAGES) - 1) & 1, err, abort_flag)) break;
                 const uint32_t fb = smem_u32(&full[s]);
-                mbar_expect_tx(fb, CF::A_BYTES + CF::B_BYTES);
+                mbar_expect_tx(fb, CF::A_BYTES + CF::B_BYTES * (TERMS == 3 ? 2 : 1));
                 const int k = (kb0 + i) * BK;
                 if (AMN) {
 #pragma unroll
@@ -174,6 +178,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                     tma_load_2d(smem_u32(stage_a(s)), &tmA, k, m0, fb);
                 }
                 tma_load_2d(smem_u32(stage_b(s)), &tmB, k, n0, fb);
+                if (TERMS == 3) tma_load_2d(smem_u32(stage_blo(s)), &tmBlo, k, n0, fb);  // B lo, split once per call
             }
         }
     } else if (warp == 1) {
@@ -221,8 +226,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                 if (AMN)
                     transpose_tile(stage_raw(s), stage_a(s), TERMS == 3 ? stage_alo(s) : nullptr, t);
                 else
-                    split_tile(stage_a(s), stage_alo(s), CF::A_BYTES, t);
-                if (TERMS == 3) split_tile(stage_b(s), stage_blo(s), CF::B_BYTES, t);
+                    split_lo(stage_a(s), stage_alo(s), CF::A_BYTES, t);
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 mbar_arrive(smem_u32(&conv[s]));
             }
@@ -344,6 +348,8 @@ struct tc_plan {
     int prec = 0;
     float *part = nullptr;
     size_t part_cap = 0;
+    float *blo = nullptr;  // lo part of the B operand (3-term products)
+    size_t blo_cap = 0;
     int *err = nullptr;
 };
 
@@ -372,6 +378,7 @@ void tc_plan_destroy(tc_plan *p)
 {
     if (!p) return;
     if (p->part) cudaFree(p->part);
+    if (p->blo) cudaFree(p->blo);
     if (p->err) cudaFree(p->err);
     delete p;
 }
@@ -386,7 +393,8 @@ int tc_plan_error(tc_plan *p, cudaStream_t st)
 }
 
 template <int BN, int TERMS, int AMN>
-static int launch_bn(tc_plan *p, cudaStream_t st, const CUtensorMap &ma, const CUtensorMap &mb, int M, int N, int K,
+static int launch_bn(tc_plan *p, cudaStream_t st, const CUtensorMap &ma, const CUtensorMap &mb,
+                     const CUtensorMap &mblo, int M, int N, int K,
                      float alpha, float beta, const float *Cin, int64_t ldcin, float *C, int64_t ldc,
                      const int *status, int *err)
 {
@@ -419,7 +427,7 @@ static int launch_bn(tc_plan *p, cudaStream_t st, const CUtensorMap &ma, const C
     }
     dim3 grid(mt, nt, splits);
     rb_count_launch();
-    k_tc_gemm<BN, TERMS, AMN><<<grid, 256, CF::SMEM, st>>>(ma, mb, M, N, nkb, kbps, alpha, beta, Cin, ldcin, C, ldc,
+    k_tc_gemm<BN, TERMS, AMN><<<grid, 256, CF::SMEM, st>>>(ma, mb, mblo, M, N, nkb, kbps, alpha, beta, Cin, ldcin, C, ldc,
                                                            part, status, err);
     if (splits > 1) {
         dim3 g2((M + 255) / 256, N);
@@ -439,11 +447,30 @@ static int launch_terms(tc_plan *p, cudaStream_t st, int a_layout, int M, int N,
     CUtensorMap ma, mb;
     bool ok = a_mn ? make_map(&ma, A, M, K, lda, 32) : make_map(&ma, A, K, M, lda, BM);
     ok = ok && make_map(&mb, B, K, N, ldb, bn);
+    CUtensorMap mblo = mb;
+    if (TERMS == 3) {
+        // lo part of B, split once here rather than in every CTA (B is shared by all M tiles)
+        const int ldlo = (K + 3) & ~3;  // 16-byte rows for TMA
+        const size_t need = (size_t)ldlo * N;
+        if (need > p->blo_cap) {
+            if (p->blo) cudaFree(p->blo);
+            p->blo = nullptr;
+            p->blo_cap = 0;
+            if (cudaMalloc(&p->blo, need * sizeof(float)) != cudaSuccess) return -2;
+            p->blo_cap = need;
+        }
+        dim3 g((K + 255) / 256, N);
+        rb_count_launch();
+        k_split_lo<<<g, 256, 0, st>>>(K, N, B, ldb, p->blo, ldlo);
+        ok = ok && make_map(&mblo, p->blo, K, N, ldlo, bn);
+    }
     if (!ok) return -4;
 #define RB_TC_CASE(BNV)                                                                                     \
     case BNV:                                                                                                  \
-        return a_mn ? launch_bn<BNV, TERMS, 1>(p, st, ma, mb, M, N, K, alpha, beta, Cin, ldcin, C, ldc, status, err) \
-                    : launch_bn<BNV, TERMS, 0>(p, st, ma, mb, M, N, K, alpha, beta, Cin, ldcin, C, ldc, status, err);
+        return a_mn ? launch_bn<BNV, TERMS, 1>(p, st, ma, mb, mblo, M, N, K, alpha, beta, Cin, ldcin, C, ldc, status, \
+                                               err)                                                             \
+                    : launch_bn<BNV, TERMS, 0>(p, st, ma, mb, mblo, M, N, K, alpha, beta, Cin, ldcin, C, ldc, status, \
+                                               err);
     switch (bn) {
         RB_TC_CASE(32)
         RB_TC_CASE(64)
@@ -468,9 +495,15 @@ static int tc_run(tc_plan *p, cudaStream_t st, int terms, int a_layout, int M, i
         return 1;
     }
     int *err = status ? const_cast<int *>(status) : p->err;
-    if (terms == 3)
-        return launch_terms<3>(p, st, a_layout, M, N, K, alpha, A, lda, B, ldb, beta, Cin, ldcin, C, ldc, status, err);
-    return launch_terms<1>(p, st, a_layout, M, N, K, alpha, A, lda, B, ldb, beta, Cin, ldcin, C, ldc, status, err);
+    const int rc =
+        (terms == 3)
+            ? launch_terms<3>(p, st, a_layout, M, N, K, alpha, A, lda, B, ldb, beta, Cin, ldcin, C, ldc, status, err)
+            : launch_terms<1>(p, st, a_layout, M, N, K, alpha, A, lda, B, ldb, beta, Cin, ldcin, C, ldc, status, err);
+    if (rc == 0) return 0;
+    // the tensor-core launch could not be set up (tensor map or workspace): run the same product on CUDA cores
+    if (beta != 0.f && Cin != C) launch_copy2d<float, float>(st, M, N, Cin, ldcin, C, ldc, 1.0);
+    gemm_simt<float>(st, a_layout == TC_A_K, false, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, status);
+    return 1;
 }
 
 int tc_gemm_nk(tc_plan *p, cudaStream_t st, int terms, int a_layout, int M, int N, int K, const float *A, int64_t lda,
