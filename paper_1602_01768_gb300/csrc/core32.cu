@@ -14,41 +14,60 @@
 
 namespace {
 
-constexpr int CT = 512;  // threads
+constexpr int CT = 256;  // threads (register arrays of 32 need the 255-register budget)
 
 __device__ void chol_blocked(float *a, int QP, int *fail)
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int c0 = 0; c0 < QP; c0 += 32) {
         if (warp == 0) {
+            // diagonal block: lane i holds row i in registers, columns via shuffles
+            float r[32];
+#pragma unroll
+            for (int c = 0; c < 32; ++c) r[c] = a[(c0 + lane) + (c0 + c) * QP];
+            bool bad = false;
+#pragma unroll
             for (int j = 0; j < 32; ++j) {
-                const float d = a[(c0 + j) + (c0 + j) * QP];
+                const float d = __shfl_sync(0xffffffffu, r[j], j);
                 if (!(d > 0.f) || !isfinite(d)) {
-                    if (lane == 0) *fail = 1;
+                    bad = true;
                     break;
                 }
                 const float sd = sqrtf(d);
-                __syncwarp();
-                if (lane == j) a[(c0 + j) + (c0 + j) * QP] = sd;
-                if (lane > j) a[(c0 + lane) + (c0 + j) * QP] /= sd;
-                __syncwarp();
-                if (lane > j) {
-                    const float lij = a[(c0 + lane) + (c0 + j) * QP];
-                    for (int c = j + 1; c <= lane; ++c)
-                        a[(c0 + lane) + (c0 + c) * QP] -= lij * a[(c0 + c) + (c0 + j) * QP];
+                if (lane == j)
+                    r[j] = sd;
+                else if (lane > j)
+                    r[j] = r[j] / sd;
+#pragma unroll
+                for (int c = j + 1; c < 32; ++c) {
+                    const float lcj = __shfl_sync(0xffffffffu, r[j], c);
+                    if (lane >= c) r[c] -= r[j] * lcj;
                 }
-                __syncwarp();
+            }
+            if (bad) {
+                if (lane == 0) *fail = 1;
+            } else {
+#pragma unroll
+                for (int c = 0; c < 32; ++c)
+                    if (c <= lane) a[(c0 + lane) + (c0 + c) * QP] = r[c];
             }
         }
         __syncthreads();
         if (*fail) return;
-        // rows below the diagonal block: x D^T = a[r, c0:c0+32]
-        for (int r = c0 + 32 + threadIdx.x; r < QP; r += CT) {
+        // rows below the diagonal block: x D^T = a[r, c0:c0+32], row in registers
+        for (int row = c0 + 32 + threadIdx.x; row < QP; row += CT) {
+            float x[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) x[j] = a[row + (c0 + j) * QP];
+#pragma unroll
             for (int j = 0; j < 32; ++j) {
-                float s = a[r + (c0 + j) * QP];
-                for (int k = 0; k < j; ++k) s -= a[r + (c0 + k) * QP] * a[(c0 + j) + (c0 + k) * QP];
-                a[r + (c0 + j) * QP] = s / a[(c0 + j) + (c0 + j) * QP];
+                float s = x[j];
+#pragma unroll
+                for (int k = 0; k < j; ++k) s -= x[k] * a[(c0 + j) + (c0 + k) * QP];
+                x[j] = s / a[(c0 + j) + (c0 + j) * QP];
             }
+#pragma unroll
+            for (int j = 0; j < 32; ++j) a[row + (c0 + j) * QP] = x[j];
         }
         __syncthreads();
         // trailing lower triangle
@@ -74,14 +93,19 @@ __device__ void tri_inverse_blocked(const float *a, float *x, float *t, int QP)
     for (int e = threadIdx.x; e < QP * QP; e += CT) x[e] = 0.f;
     __syncthreads();
     const int NB = QP / 32;
-    if (warp < NB) {  // diagonal blocks, column per lane
+    if (warp < NB) {  // diagonal blocks, column per lane, column kept in registers
         const int o = 32 * warp, c = lane;
-        x[(o + c) + (o + c) * QP] = 1.f / a[(o + c) + (o + c) * QP];
-        for (int i = c + 1; i < 32; ++i) {
+        float xc[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
             float s = 0.f;
-            for (int k = c; k < i; ++k) s += a[(o + i) + (o + k) * QP] * x[(o + k) + (o + c) * QP];
-            x[(o + i) + (o + c) * QP] = -s / a[(o + i) + (o + i) * QP];
+#pragma unroll
+            for (int k = 0; k < i; ++k) s += a[(o + i) + (o + k) * QP] * xc[k];  // xc[k] = 0 for k < c
+            const float inv = 1.f / a[(o + i) + (o + i) * QP];
+            xc[i] = (i == c) ? inv : ((i > c) ? -s * inv : 0.f);
         }
+#pragma unroll
+        for (int i = 0; i < 32; ++i) x[(o + i) + (o + c) * QP] = xc[i];
     }
     __syncthreads();
     for (int b = 32; b < QP; b *= 2) {

@@ -45,13 +45,34 @@ __global__ void __launch_bounds__(256) k_gram_partial(int n, int p, int r, const
     }
 }
 
-__global__ void k_gram_reduce(int nchunks, int pr, const double *part, double *out)
+// out[e] = sum_c part[c][e] in a fixed order: thread group g of 8 sums the
+// chunks c = g, g + 8, ... (independent loads issued together), then the 8
+// group sums are added in order g = 0..7.  Deterministic and not latency bound.
+__global__ void __launch_bounds__(256) k_gram_reduce(int nchunks, int pr, const double *part, double *out)
 {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= pr) return;
+    __shared__ double red[8][33];
+    const int o = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int e = blockIdx.x * 32 + o;
     double s = 0.0;
-    for (int c = 0; c < nchunks; ++c) s += part[(size_t)c * pr + e];
-    out[e] = s;
+    if (e < pr) {
+        int c = g;
+        for (; c + 24 < nchunks; c += 32) {  // four independent loads in flight
+            const double a0 = part[(size_t)c * pr + e], a1 = part[(size_t)(c + 8) * pr + e];
+            const double a2 = part[(size_t)(c + 16) * pr + e], a3 = part[(size_t)(c + 24) * pr + e];
+            s += a0;
+            s += a1;
+            s += a2;
+            s += a3;
+        }
+        for (; c < nchunks; c += 8) s += part[(size_t)c * pr + e];
+    }
+    red[g][o] = s;
+    __syncthreads();
+    if (g == 0 && e < pr) {
+        double t = 0.0;
+        for (int k = 0; k < 8; ++k) t += red[k][o];
+        out[e] = t;
+    }
 }
 
 // One CTA per GRAM_CHUNK rows computing all p x r outputs (p, r <= 128):
@@ -113,7 +134,7 @@ void launch_gram(cudaStream_t st, int n, int p, int r, const T *X, int64_t ldx, 
             rb_count_launch();
             k_gram_chunk<T><<<nch, 256, 0, st>>>(n, p, r, X, ldx, Y, ldy, part);
             rb_count_launch();
-            k_gram_reduce<<<ceil_div(p * r, 256), 256, 0, st>>>(nch, p * r, part, out);
+            k_gram_reduce<<<ceil_div(p * r, 32), 256, 0, st>>>(nch, p * r, part, out);
             return;
         }
     }
@@ -121,7 +142,7 @@ void launch_gram(cudaStream_t st, int n, int p, int r, const T *X, int64_t ldx, 
     rb_count_launch();
     k_gram_partial<T><<<grid, 256, 0, st>>>(n, p, r, X, ldx, Y, ldy, part);
     rb_count_launch();
-    k_gram_reduce<<<ceil_div(p * r, 256), 256, 0, st>>>(nch, p * r, part, out);
+    k_gram_reduce<<<ceil_div(p * r, 32), 256, 0, st>>>(nch, p * r, part, out);
 }
 template void launch_gram<float>(cudaStream_t, int, int, int, const float *, int64_t, const float *, int64_t,
                                  double *, double *);
