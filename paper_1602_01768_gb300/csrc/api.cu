@@ -45,6 +45,10 @@ struct rb_ctx {
 
     tc_plan *tc = nullptr;  // tensor-core plan (FP32 storage, TF32 modes)
 
+    // side stream for the q x q work that does not need W = L^T G (fork/join by events)
+    cudaStream_t st2 = nullptr;
+    cudaEvent_t ev_sk = nullptr, ev_g = nullptr, ev_core = nullptr;
+
     // phase profiling (rbfgs_profile_step): events recorded between phases
     int prof_on = 0, prof_n = 0;
     cudaEvent_t prof_ev[24];
@@ -135,6 +139,10 @@ static void destroy_ctx(rb_ctx *h)
     rb_freet(h->rpart);
     rb_freet(h->rsum);
     tc_plan_destroy(h->tc);
+    if (h->ev_sk) cudaEventDestroy(h->ev_sk);
+    if (h->ev_g) cudaEventDestroy(h->ev_g);
+    if (h->ev_core) cudaEventDestroy(h->ev_core);
+    if (h->st2) cudaStreamDestroy(h->st2);
     delete h;
 }
 
@@ -431,6 +439,21 @@ static void ada_step_simt(rb_ctx *h)
     mark(h, "update L");
 }
 
+static bool ensure_side_stream(rb_ctx *h)
+{
+    if (h->st2) return true;
+    if (cudaStreamCreateWithFlags(&h->st2, cudaStreamNonBlocking) != cudaSuccess) return false;
+    const unsigned fl = cudaEventDisableTiming;
+    if (cudaEventCreateWithFlags(&h->ev_sk, fl) != cudaSuccess || cudaEventCreateWithFlags(&h->ev_g, fl) != cudaSuccess ||
+        cudaEventCreateWithFlags(&h->ev_core, fl) != cudaSuccess)
+        return false;
+    return true;
+}
+
+// Tensor-core step.  The q x q work runs on a side stream while the main
+// stream streams the n x n passes:
+//   main:  sketch -> S = L S~ -> G = A S -> W^T = L^T G -> [join] -> V, S^ -> L += S^ V
+//   side:  [after sketch] S~^T S~, D^-1   [after G] S^T G, C^-1
 static void ada_step_tc(rb_ctx *h)
 {
     const int n = h->n, q = h->q;
@@ -441,22 +464,39 @@ static void ada_step_tc(rb_ctx *h)
           *Di = (float *)h->Dinv;
     const int acc = (h->prec == RB_TF32) ? 1 : 3;  // split terms of the accuracy-critical products
     const int upd = (h->prec == RB_TF32X3) ? 3 : 1;
+    const bool fork = !h->core_fp64 && ensure_side_stream(h);
+    cudaStream_t side = fork ? h->st2 : st;
     ada_draw<float>(h, St);
+    if (fork) {
+        cudaEventRecord(h->ev_sk, st);
+        cudaStreamWaitEvent(side, h->ev_sk, 0);
+        launch_gram<float>(side, n, q, q, St, n, St, n, h->part, h->N);  // S~^T S~ -> D^-1
+        launch_core_ada32(side, q, h->N, nullptr, Di, nullptr, h->d_status);
+    }
     mark(h, "sketch");
     tc_gemm_nk(h->tc, st, acc, TC_A_MN, n, q, n, L, n, St, n, S, n, stp);   // S = L S~   (A = L, M-contiguous)
     mark(h, "S=LS~");
     tc_gemm_nk(h->tc, st, acc, TC_A_K, n, q, n, A, n, S, n, G, n, stp);     // G = A S    (A symmetric)
     mark(h, "G=AS");
-    launch_gram<float>(st, n, q, q, S, n, G, n, h->part, h->M);
-    launch_gram<float>(st, n, q, q, St, n, St, n, h->part, h->N);
-    mark(h, "grams");
-    if (!h->core_fp64)
-        launch_core_ada32(st, q, h->M, h->N, Ci, Di, h->d_status);
-    else
-        launch_core_ada<float>(st, q, h->M, h->N, Ci, Di, h->d_status);
-    mark(h, "q x q core");
+    if (fork) {
+        cudaEventRecord(h->ev_g, st);
+        cudaStreamWaitEvent(side, h->ev_g, 0);
+        launch_gram<float>(side, n, q, q, S, n, G, n, h->part, h->M);    // S^T A S -> C^-1
+        launch_core_ada32(side, q, h->M, nullptr, Ci, nullptr, h->d_status);
+        cudaEventRecord(h->ev_core, side);
+    } else {
+        launch_gram<float>(st, n, q, q, S, n, G, n, h->part, h->M);
+        launch_gram<float>(st, n, q, q, St, n, St, n, h->part, h->N);
+        mark(h, "grams");
+        if (!h->core_fp64)
+            launch_core_ada32(st, q, h->M, h->N, Ci, Di, h->d_status);
+        else
+            launch_core_ada<float>(st, q, h->M, h->N, Ci, Di, h->d_status);
+        mark(h, "q x q core");
+    }
     tc_gemm_nk(h->tc, st, acc, TC_A_K, n, q, n, L, n, G, n, W, n, stp);     // W^T = L^T G (n x q)
-    mark(h, "W=G^TL");
+    if (fork) cudaStreamWaitEvent(st, h->ev_core, 0);                          // join: C^-1, D^-1 ready
+    mark(h, fork ? "W=G^TL | grams+core" : "W=G^TL");
     // V = D^-1 S~^T - C^-1 W, stored q x n (ld q); W^T is n x q (ld n)
     gemm_simt<float>(st, false, true, q, n, q, 1.f, Di, q, St, n, 0.f, V, q, stp);
     gemm_simt<float>(st, false, true, q, n, q, -1.f, Ci, q, W, n, 1.f, V, q, stp);

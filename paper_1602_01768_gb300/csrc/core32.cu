@@ -132,6 +132,8 @@ __device__ void tri_inverse_blocked(const float *a, float *x, float *t, int QP)
 __global__ void __launch_bounds__(CT, 1) k_core32(int q, const double *M, const double *N, float *Cinv, float *Dinv,
                                                   int *status)
 {
+    // blockIdx.x = 0 handles M -> Cinv, 1 handles N -> Dinv; a launch of one
+    // block with M == N handles a single matrix.
     extern __shared__ float sm32[];
     __shared__ int fail;
     if (status_bad(status)) return;
@@ -177,5 +179,5 @@ void launch_core_ada32(cudaStream_t st, int q, const double *M, const double *N,
         attr = true;
     }
     rb_count_launch();
-    k_core32<<<2, CT, smem, st>>>(q, M, N, Cinv, Dinv, status);
+    k_core32<<<(N && Dinv) ? 2 : 1, CT, smem, st>>>(q, M, N, Cinv, Dinv, status);
 }
