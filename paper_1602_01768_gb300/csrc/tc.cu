@@ -4,15 +4,17 @@
 // are summed afterwards in a fixed order, so results are deterministic).
 // Warp roles, 256 threads:
 //   warp 0      TMA producer: streams 128 x 32 tiles of op(A) and BN x 32
-//               tiles of B (FP32, 128-byte swizzle) into a STAGES-deep ring;
-//   warp 1      allocates the TMEM accumulator (BN columns x 128 lanes) and
-//               issues tcgen05.mma kind::tf32 from one elected thread; both
-//               operands are K-major in shared memory;
-//   warps 4-7   per stage: an M-contiguous op(A) tile is transposed into the
-//               K-major layout, and (terms = 3) every tile is split into hi
-//               (top 11 significand bits) and lo = x - hi; after the last
-//               stage they drain the accumulator with tcgen05.ld and apply
-//               alpha/beta.
+//               tiles of B (and of B's lo part) with 128-byte swizzle into a
+//               STAGES-deep ring;
+//   warp 1      allocates TMEM and issues tcgen05.mma kind::tf32 from one
+//               elected thread, B from shared memory (K-major);
+//   warps 4-7   for 3-term products or an M-contiguous op(A): each thread
+//               takes one row of the landed A tile and writes it to TMEM as
+//               hi = x (the MMA keeps the top 11 significand bits) and
+//               lo = x - hi, so the MMA reads A from TMEM; for single-pass
+//               K-contiguous A the MMA reads the tile from shared memory.
+//               After the last stage they drain the accumulator with
+//               tcgen05.ld and apply alpha/beta.
 // Every mbarrier wait is bounded (about two seconds of SM clock); a wait
 // that gives up records ST_TIMEOUT in the caller's status word and the CTA
 // winds down instead of hanging.
@@ -31,40 +33,27 @@ using namespace tcx;
 
 template <int BN, int TERMS, int AMN>
 struct Cfg {
+    static constexpr bool CONVERT = (TERMS == 3) || AMN;  // A goes through the converter warps into TMEM
     static constexpr int A_BYTES = A_TILE_BYTES;
     static constexpr int B_BYTES = BN * BK * 4;
-    // [A hi | B hi | A lo | B lo (3 terms) | A raw, M-contiguous (AMN)]
-    static constexpr int STAGE_BYTES = (A_BYTES + B_BYTES) * (TERMS == 3 ? 2 : 1) + (AMN ? A_BYTES : 0);
-    static constexpr int STAGES_RAW = (200 * 1024) / STAGE_BYTES;
-    static constexpr int STAGES = STAGES_RAW > 8 ? 8 : STAGES_RAW;
-    static constexpr int TMEM_COLS = BN < 32 ? 32 : BN;
+    // smem stage: [A tile | B | B lo (3 terms)]; with CONVERT the A tile is the raw
+    // TMA tile (K- or M-contiguous) that the converter moves into TMEM.
+    static constexpr int STAGE_BYTES = A_BYTES + B_BYTES * (TERMS == 3 ? 2 : 1);
+    static constexpr int A_TMEM_COLS = (TERMS == 3) ? 64 : 32;  // per stage: hi (32 cols) [+ lo (32 cols)]
+    static constexpr int STAGES_SMEM = (200 * 1024) / STAGE_BYTES;
+    static constexpr int STAGES_TMEM = CONVERT ? (512 - BN) / A_TMEM_COLS : 8;
+    static constexpr int STAGES_A = STAGES_SMEM < STAGES_TMEM ? STAGES_SMEM : STAGES_TMEM;
+    static constexpr int STAGES = STAGES_A > 8 ? 8 : STAGES_A;
+    static constexpr int TMEM_COLS = CONVERT ? 512 : (BN < 32 ? 32 : BN);
     static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 /*align*/ + 512 /*barriers*/;
-    static constexpr bool CONVERT = (TERMS == 3) || AMN;  // converter warps have work each stage
     static_assert(STAGES >= 2, "pipeline needs two stages");
 };
 
 __device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
 
-// lo = x - hi(x) for a tile of `bytes` bytes (layout preserved).  The tensor
-// core reads an FP32 operand of kind::tf32 as its top 19 bits (the low 13
-// mantissa bits are dropped, not rounded), so the raw tile already is the hi
-// part and only lo is written.
-__device__ __forceinline__ void split_lo(const unsigned char *x, unsigned char *lo, int bytes, int t)
-{
-    const float4 *a = (const float4 *)x;
-    float4 *b = (float4 *)lo;
-    for (int e = t; e < bytes / 16; e += 128) {
-        const float4 v = a[e];
-        float4 l;
-        l.x = v.x - tf32_hi(v.x);
-        l.y = v.y - tf32_hi(v.y);
-        l.z = v.z - tf32_hi(v.z);
-        l.w = v.w - tf32_hi(v.w);
-        b[e] = l;
-    }
-}
-
-// lo = x - hi(x), elementwise over a column-major rows x cols panel (ld).
+// lo = x - hi(x), elementwise over a column-major rows x cols panel (ld).  The
+// tensor core reads an FP32 operand of kind::tf32 as its top 19 bits (the low
+// 13 mantissa bits are dropped, not rounded), so x itself serves as the hi part.
 __global__ void k_split_lo(int rows, int cols, const float *X, int64_t ldx, float *L, int64_t ldl)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -75,31 +64,51 @@ __global__ void k_split_lo(int rows, int cols, const float *X, int64_t ldx, floa
     }
 }
 
-// Row m = t of the K-major 128 x 32 tile (128-byte swizzle: 16-byte chunk j of
-// row m sits at chunk j ^ (m & 7)) gathered from the M-contiguous raw tile
-// (four 32-row boxes, 4 KB apart; element (m, k) in 16-byte chunk
-// (m & 31) / 4 ^ (k & 7) of K-row k).  Writes hi, and lo when lo != nullptr.
-__device__ __forceinline__ void transpose_tile(const unsigned char *raw, unsigned char *hi, unsigned char *lo, int t)
+// 32 lanes x 32 columns of 32-bit values from registers into TMEM.
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32])
 {
-    const int m = t, c = m >> 5, mi = m & 31;
-    const unsigned char *src = raw + c * 4096 + ((mi & 3) << 2);
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+        "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]),
+        "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]),
+        "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+        : "memory");
+}
+
+// D (TMEM) += A (TMEM, M rows on lanes, K on columns) x B (smem descriptor).
+__device__ __forceinline__ void mma_tf32_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                            uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+// Row m of the stage's raw A tile as 32 FP32 values.  K-contiguous tile: row m
+// is 128 bytes with 16-byte chunk j stored at chunk j ^ (m & 7).
+// M-contiguous tile: four 32-row boxes 4 KB apart; element (m, k) in 16-byte
+// chunk ((m & 31) / 4) ^ (k & 7) of the box's K-row k.
+template <int AMN>
+__device__ __forceinline__ void load_a_row(const unsigned char *raw, int m, float (&v)[32])
+{
+    if (AMN) {
+        const int mi = m & 31;
+        const unsigned char *src = raw + (m >> 5) * 4096 + ((mi & 3) << 2);
 #pragma unroll
-    for (int kq = 0; kq < 8; ++kq) {
-        float v[4];
+        for (int k = 0; k < 32; ++k) v[k] = *(const float *)(src + k * 128 + (((mi >> 2) ^ (k & 7)) << 4));
+    } else {
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int k = 4 * kq + u;
-            v[u] = *(const float *)(src + k * 128 + ((((mi >> 2) ^ (k & 7))) << 4));
-        }
-        const int off = m * 128 + ((kq ^ (m & 7)) << 4);
-        *(float4 *)(hi + off) = make_float4(v[0], v[1], v[2], v[3]);  // the MMA truncates to TF32 itself
-        if (lo) {
-            float4 l;
-            l.x = v[0] - tf32_hi(v[0]);
-            l.y = v[1] - tf32_hi(v[1]);
-            l.z = v[2] - tf32_hi(v[2]);
-            l.w = v[3] - tf32_hi(v[3]);
-            *(float4 *)(lo + off) = l;
+        for (int j = 0; j < 8; ++j) {
+            const float4 f = *(const float4 *)(raw + m * 128 + ((j ^ (m & 7)) << 4));
+            v[4 * j] = f.x;
+            v[4 * j + 1] = f.y;
+            v[4 * j + 2] = f.z;
+            v[4 * j + 3] = f.w;
         }
     }
 }
@@ -107,9 +116,8 @@ __device__ __forceinline__ void transpose_tile(const unsigned char *raw, unsigne
 template <int BN, int TERMS, int AMN>
 __global__ void __launch_bounds__(256, 1)
 k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-          const __grid_constant__ CUtensorMap tmBlo, int M, int N, int nkb,
-          int kb_per_split, float alpha, float beta, const float *Cin, int64_t ldcin, float *C, int64_t ldc,
-          float *part, const int *status, int *err)
+          const __grid_constant__ CUtensorMap tmBlo, int M, int N, int nkb, int kb_per_split, float alpha, float beta,
+          const float *Cin, int64_t ldcin, float *C, int64_t ldc, float *part, const int *status, int *err)
 {
     using CF = Cfg<BN, TERMS, AMN>;
     constexpr int STAGES = CF::STAGES;
@@ -151,15 +159,12 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = *tmem_slot;
+    const uint32_t tmem = *tmem_slot;  // accumulator: columns [0, BN); A stages after it
 
     auto stage_a = [&](int s) { return smem + s * CF::STAGE_BYTES; };
     auto stage_b = [&](int s) { return smem + s * CF::STAGE_BYTES + CF::A_BYTES; };
-    auto stage_alo = [&](int s) { return smem + s * CF::STAGE_BYTES + CF::A_BYTES + CF::B_BYTES; };
-    auto stage_blo = [&](int s) { return smem + s * CF::STAGE_BYTES + 2 * CF::A_BYTES + CF::B_BYTES; };
-    auto stage_raw = [&](int s) {
-        return smem + s * CF::STAGE_BYTES + (CF::A_BYTES + CF::B_BYTES) * (TERMS == 3 ? 2 : 1);
-    };
+    auto stage_blo = [&](int s) { return smem + s * CF::STAGE_BYTES + CF::A_BYTES + CF::B_BYTES; };
+    auto a_col = [&](int s) { return (uint32_t)(BN + s * CF::A_TMEM_COLS); };
 
     if (warp == 0) {
         // ---------------- TMA producer ----------------
@@ -168,12 +173,12 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                 const int s = i % STAGES;
                 if (i >= STAGES && !mbar_wait(smem_u32(&empty[s]), ((i / STAGES) - 1) & 1, err, abort_flag)) break;
                 const uint32_t fb = smem_u32(&full[s]);
-                mbar_expect_tx(fb, CF::A_BYTES + CF::B_BYTES * (TERMS == 3 ? 2 : 1));
+                mbar_expect_tx(fb, CF::STAGE_BYTES);
                 const int k = (kb0 + i) * BK;
                 if (AMN) {
 #pragma unroll
                     for (int c = 0; c < BM / 32; ++c)
-                        tma_load_2d(smem_u32(stage_raw(s) + c * 4096), &tmA, m0 + 32 * c, k, fb);
+                        tma_load_2d(smem_u32(stage_a(s) + c * 4096), &tmA, m0 + 32 * c, k, fb);
                 } else {
                     tma_load_2d(smem_u32(stage_a(s)), &tmA, k, m0, fb);
                 }
@@ -182,7 +187,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
             }
         }
     } else if (warp == 1) {
-        // ---------------- MMA issuer (both operands K-major in smem) ----------------
+        // ---------------- MMA issuer ----------------
         if (lane == 0) {
             const uint32_t idesc = idesc_tf32(BN, 0);
             bool ok = true;
@@ -194,22 +199,25 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                     break;
                 }
                 tc_fence_after();
-                const uint32_t a_hi = smem_u32(stage_a(s)), b_hi = smem_u32(stage_b(s));
-                const uint32_t a_lo = smem_u32(stage_alo(s)), b_lo = smem_u32(stage_blo(s));
+                const uint32_t b_hi = smem_u32(stage_b(s)), b_lo = smem_u32(stage_blo(s));
 #pragma unroll
                 for (int kk = 0; kk < BK / 8; ++kk) {
-                    // K = 8 TF32 per MMA = 32 bytes along the 128-byte swizzle row
-                    const uint64_t da_hi = umma_desc(a_hi + kk * 32, 16, 1024);
+                    // K = 8 TF32 per MMA: 32 bytes along B's 128-byte swizzle row, 8 TMEM columns of A
                     const uint64_t db_hi = umma_desc(b_hi + kk * 32, 16, 1024);
                     const uint32_t first = (i == 0 && kk == 0) ? 0u : 1u;
-                    if (TERMS == 3) {
-                        const uint64_t da_lo = umma_desc(a_lo + kk * 32, 16, 1024);
-                        const uint64_t db_lo = umma_desc(b_lo + kk * 32, 16, 1024);
-                        mma_tf32(tmem, da_lo, db_hi, idesc, first);
-                        mma_tf32(tmem, da_hi, db_lo, idesc, 1u);
-                        mma_tf32(tmem, da_hi, db_hi, idesc, 1u);
+                    if (CF::CONVERT) {
+                        const uint32_t ta_hi = tmem + a_col(s) + 8 * kk;
+                        if (TERMS == 3) {
+                            const uint64_t db_lo = umma_desc(b_lo + kk * 32, 16, 1024);
+                            mma_tf32_ts(tmem, ta_hi + 32, db_hi, idesc, first);  // lo x hi
+                            mma_tf32_ts(tmem, ta_hi, db_lo, idesc, 1u);          // hi x lo
+                            mma_tf32_ts(tmem, ta_hi, db_hi, idesc, 1u);          // hi x hi
+                        } else {
+                            mma_tf32_ts(tmem, ta_hi, db_hi, idesc, first);
+                        }
                     } else {
-                        mma_tf32(tmem, da_hi, db_hi, idesc, first);
+                        const uint64_t da = umma_desc(smem_u32(stage_a(s)) + kk * 32, 16, 1024);
+                        mma_tf32(tmem, da, db_hi, idesc, first);
                     }
                 }
                 mma_commit(smem_u32(&empty[s]));
@@ -217,17 +225,27 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
             if (ok) mma_commit(smem_u32(accf));
         }
     } else if (warp >= 4) {
-        const int t = threadIdx.x - 128;  // 0..127
-        // ---------------- operand conversion ----------------
+        const int t = threadIdx.x - 128;  // 0..127 = tile row = TMEM lane
+        const int wq = warp & 3;          // this warp's TMEM lane quarter
+        // ---------------- A operand into TMEM (hi = x, lo = x - hi(x)) ----------------
         if (CF::CONVERT) {
             for (int i = 0; i < nk; ++i) {
                 const int s = i % STAGES;
                 if (!mbar_wait(smem_u32(&full[s]), (i / STAGES) & 1, err, abort_flag)) break;
-                if (AMN)
-                    transpose_tile(stage_raw(s), stage_a(s), TERMS == 3 ? stage_alo(s) : nullptr, t);
-                else
-                    split_lo(stage_a(s), stage_alo(s), CF::A_BYTES, t);
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                float v[32];
+                load_a_row<AMN>(stage_a(s), t, v);
+                uint32_t r[32];
+                const uint32_t taddr = tmem + ((uint32_t)(32 * wq) << 16) + a_col(s);
+#pragma unroll
+                for (int k = 0; k < 32; ++k) r[k] = __float_as_uint(v[k]);
+                tmem_st32(taddr, r);
+                if (TERMS == 3) {
+#pragma unroll
+                    for (int k = 0; k < 32; ++k) r[k] = __float_as_uint(v[k] - tf32_hi(v[k]));
+                    tmem_st32(taddr + 32, r);
+                }
+                asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+                tc_fence_before();
                 mbar_arrive(smem_u32(&conv[s]));
             }
         }
@@ -235,7 +253,6 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         const bool got = mbar_wait(smem_u32(accf), 0, err, abort_flag);
         tc_fence_after();
         if (got) {
-            const int wq = warp & 3;  // TMEM lanes 32 wq .. 32 wq + 31
             const int m = m0 + 32 * wq + lane;
             const bool split = (part != nullptr);
             for (int c0 = 0; c0 < BN; c0 += 16) {
