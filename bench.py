@@ -32,6 +32,9 @@ METRIC = "time to ‖I−XA‖_F/√n≤1e-4 at n=16384 (mixed vs FP32); solves/
 N_DEFAULT, Q_DEFAULT, TOL_DEFAULT = 16384, 128, 1e-4
 CHECK_EVERY, CHECK_COLS, CONFIRM_COLS = 32, 256, 1024
 MAX_ITER = 20000
+# DRAM bytes (read + write) of one k_tc_update launch at n = 8192, q = 128, from one ncu capture
+# (profiles/tc_kernels_n8192_full.md); scaled by (n / 8192)^2 for other n at q = 128.
+UPDATE_TRAFFIC_N8192_Q128 = 279770624 + 208392448
 
 
 def parse():
@@ -296,7 +299,8 @@ def main():
     achieved = upd_bytes / (upd_ms * 1e-3) / 1e9
     roofline = {"kernel": "rank-q update L += S^ V (k_tc_gemm, 1xTF32, beta=1)", "bound": "hbm",
                 "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "peak_kind": f"{peak_kind} HBM copy", "traffic": None,
+                "peak_kind": f"{peak_kind} HBM copy",
+                "traffic": (UPDATE_TRAFFIC_N8192_Q128 * (n / 8192) ** 2) if q == 128 else None,
                 "algorithmic_bytes_per_launch": upd_bytes, "ms_per_launch": upd_ms}
     step_ms = sum(phases.values())
 
