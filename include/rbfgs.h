@@ -246,6 +246,36 @@ rb_status rbfgs_launch_count(uint64_t *count);
 
 rb_status rbfgs_destroy(rbfgs_t h);
 
+/*
+ * Batched RBFGS: many SPD problems of uneven size (n_i <= 1024), each with
+ * X0 = I and the trace-weighted coordinate-block sketch of q_i coordinates
+ * (q_i in {4, 8, ..., 32}, a multiple of 4), Philox key `seed` and counter
+ * stream stream_ids[i] (NULL: i), exactly as an rbfgs_init handle with
+ * RB_SKETCH_COORD_TRACE would draw them.  Storage FP32, the q x q Cholesky in
+ * FP64.  All problems advance in one persistent launch: CTAs pull problems
+ * from a device work queue (largest n first) and run the requested steps
+ * on each; every problem is processed by one CTA in a fixed order, so its
+ * iterates do not depend on the rest of the batch.  The round (steps, then a
+ * sampled residual per problem) is captured as a CUDA graph and replayed.
+ * A_dev[i] are device pointers (ld lda[i]) copied at creation.
+ */
+typedef struct rb_batch *rb_batch_t;
+rb_status rb_batch_create(rb_batch_t *b, int count, const int *n, const void *const *A_dev, const int64_t *lda,
+                          int a_is_fp64, const int *q, const uint64_t *stream_ids, uint64_t seed, void *stream);
+/* `steps` steps on every active problem (synchronises). */
+rb_status rb_batch_step(rb_batch_t b, int steps);
+/* Sampled residual ||I - X_i A_i||_F / sqrt(n_i) of every problem from ncols <= 64
+ * Floyd-sampled columns (key col_seed, counter stream i); out has count entries. */
+rb_status rb_batch_residual(rb_batch_t b, int ncols, uint64_t col_seed, double *out);
+/* Steps in rounds of check_every until each problem's sampled residual is <= tol (it
+ * then stops), it fails (RB_ENOTSPD in status[i]) or max_iter steps are done.
+ * iters/resid/status have count entries; returns RB_OK when all converged. */
+rb_status rb_batch_solve(rb_batch_t b, double tol, int max_iter, int check_every, int ncols, int *iters,
+                         double *resid, int *status, int *nconverged);
+/* X_i into out_dev (FP32, ld >= n_i); asynchronous. */
+rb_status rb_batch_export(rb_batch_t b, int i, void *out_dev, int64_t ld);
+rb_status rb_batch_destroy(rb_batch_t b);
+
 const char *rbfgs_status_string(int status);
 
 #ifdef __cplusplus

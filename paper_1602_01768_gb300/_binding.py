@@ -65,6 +65,14 @@ _SIGS = {
     "rbfgs_launch_count": (C.c_int, [C.c_void_p]),
     "rbfgs_reset": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64]),
     "rbfgs_destroy": (C.c_int, [C.c_void_p]),
+    "rb_batch_create": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
+                                  C.c_void_p, C.c_uint64, C.c_void_p]),
+    "rb_batch_step": (C.c_int, [C.c_void_p, C.c_int]),
+    "rb_batch_residual": (C.c_int, [C.c_void_p, C.c_int, C.c_uint64, C.c_void_p]),
+    "rb_batch_solve": (C.c_int, [C.c_void_p, C.c_double, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p,
+                                 C.c_void_p, C.c_void_p]),
+    "rb_batch_export": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64]),
+    "rb_batch_destroy": (C.c_int, [C.c_void_p]),
 }
 
 
@@ -241,3 +249,45 @@ def rbfgs_launch_count():
 
 def rbfgs_destroy(h):
     return _check(_lib().rbfgs_destroy(h), "rbfgs_destroy")
+
+
+def rb_batch_create(n_list, A_ptrs, lda_list, a_is_fp64, q_list, seed, stream_ids=None, stream=0):
+    cnt = len(n_list)
+    n_arr = (C.c_int * cnt)(*n_list)
+    q_arr = (C.c_int * cnt)(*q_list)
+    a_arr = (C.c_void_p * cnt)(*[int(p) for p in A_ptrs])
+    l_arr = (C.c_int64 * cnt)(*lda_list)
+    s_arr = (C.c_uint64 * cnt)(*stream_ids) if stream_ids is not None else None
+    b = C.c_void_p()
+    _check(_lib().rb_batch_create(C.byref(b), cnt, n_arr, a_arr, l_arr, int(a_is_fp64), q_arr,
+                                  s_arr, seed, _p(stream)), "rb_batch_create")
+    b._count = cnt
+    return b
+
+
+def rb_batch_step(b, steps):
+    return _check(_lib().rb_batch_step(b, steps), "rb_batch_step")
+
+
+def rb_batch_residual(b, count, ncols, col_seed):
+    out = (C.c_double * count)()
+    _check(_lib().rb_batch_residual(b, ncols, col_seed, out), "rb_batch_residual")
+    return list(out)
+
+
+def rb_batch_solve(b, count, tol, max_iter, check_every, ncols):
+    it = (C.c_int * count)()
+    r = (C.c_double * count)()
+    st = (C.c_int * count)()
+    nc = C.c_int()
+    rc = _check(_lib().rb_batch_solve(b, tol, max_iter, check_every, ncols, it, r, st, C.byref(nc)),
+                "rb_batch_solve")
+    return rc, list(it), list(r), list(st), nc.value
+
+
+def rb_batch_export(b, i, out_dev, ld):
+    return _check(_lib().rb_batch_export(b, i, _p(out_dev), ld), "rb_batch_export")
+
+
+def rb_batch_destroy(b):
+    return _check(_lib().rb_batch_destroy(b), "rb_batch_destroy")

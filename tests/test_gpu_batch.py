@@ -1,0 +1,96 @@
+"""Batched coordinate RBFGS (one persistent launch for many uneven problems):
+parity with the FP64 oracle per problem, independence from the batch's
+composition, and the solve loop."""
+import numpy as np
+import pytest
+
+import paper_1602_01768_gb300._binding as B
+from oracle import oracle as orc
+from paper_1602_01768_gb300 import workloads as wl
+
+from gpu_util import empty_dev, from_dev, rel, stream_ptr, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def _problems(count, seed, nmax=220):
+    out = []
+    for A, q, kappa in wl.c4_problems(count=count * 4, seed=seed):
+        if A.shape[0] <= nmax:
+            out.append((A.astype(np.float32).astype(np.float64), q, kappa))
+        if len(out) == count:
+            break
+    return out
+
+
+def _create(probs, seed, stream_ids=None):
+    import torch
+
+    devs = [to_dev(A, torch.float32) for A, _, _ in probs]
+    n = [A.shape[0] for A, _, _ in probs]
+    b = B.rb_batch_create(n, [d.data_ptr() for d in devs], n, False, [q for _, q, _ in probs], seed,
+                          stream_ids=stream_ids, stream=stream_ptr())
+    return b, n
+
+
+def _export(b, i, n):
+    import torch
+
+    out = empty_dev(n, n, torch.float32)
+    B.rb_batch_export(b, i, out.data_ptr(), n)
+    return from_dev(out)
+
+
+def test_batch_matches_oracle_per_problem():
+    probs = _problems(8, 4)
+    seed, steps = 77, 60
+    b, n = _create(probs, seed)
+    try:
+        B.rb_batch_step(b, steps)
+        for i, (A, q, _) in enumerate(probs):
+            _, X = orc.rbfgs_run(A, np.eye(n[i]), q, orc.SKETCH_COORD_TRACE, seed, i, 0, steps)
+            assert rel(_export(b, i, n[i]), X) <= 1e-4, (i, n[i], q)
+    finally:
+        B.rb_batch_destroy(b)
+
+
+def test_batch_result_is_independent_of_the_mix():
+    probs = _problems(10, 5)
+    b, n = _create(probs, 9)
+    b1, n1 = _create([probs[3]], 9, stream_ids=[3])
+    try:
+        B.rb_batch_step(b, 25)
+        B.rb_batch_step(b1, 25)
+        assert np.array_equal(_export(b, 3, n[3]), _export(b1, 0, n1[0]))
+    finally:
+        B.rb_batch_destroy(b)
+        B.rb_batch_destroy(b1)
+
+
+def test_batch_solve_converges_and_residual_is_honest():
+    # well-conditioned problems so that coordinate RBFGS reaches the tolerance quickly
+    probs = []
+    for i, n in enumerate((40, 72, 128, 36, 100)):
+        A, _, _ = wl.spd_spectrum(n, 3.0, 300 + i)
+        probs.append((A.astype(np.float32).astype(np.float64), (4, 8, 16, 32, 8)[i], 3.0))
+    b, n = _create(probs, 21)
+    try:
+        rc, iters, resid, status, nconv = B.rb_batch_solve(b, len(probs), 1e-3, 20000, 50, 16)
+        assert nconv == len(probs) and rc == B.RB_OK, (resid, status)
+        for i, (A, q, _) in enumerate(probs):
+            X = _export(b, i, n[i])
+            exact = orc.residual(A, X)
+            assert exact <= 3e-3, (i, exact, resid[i])
+            assert iters[i] > 0 and status[i] == B.RB_OK
+    finally:
+        B.rb_batch_destroy(b)
+
+
+def test_batch_rejects_bad_sizes():
+    import torch
+
+    A = to_dev(np.eye(8), torch.float32)
+    with pytest.raises(B.RbfgsError):
+        B.rb_batch_create([8], [A.data_ptr()], [8], False, [6], 0, stream=stream_ptr())  # q not a multiple of 4
+    with pytest.raises(B.RbfgsError):
+        B.rb_batch_create([2000], [A.data_ptr()], [2000], False, [8], 0, stream=stream_ptr())  # n > 1024
