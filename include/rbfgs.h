@@ -133,6 +133,20 @@ rb_status adarbfgs_step(rbfgs_t h, int nsteps);
 rb_status rbfgs_residual(rbfgs_t h, int ncols, uint64_t col_seed, double *out);
 
 /*
+ * Non-blocking form of rbfgs_residual: rbfgs_residual_start queues the
+ * residual kernels and the copy of its sum (and of the status word) to
+ * pinned host memory on the handle's stream; rbfgs_residual_poll sets
+ * *ready = 0 while that is in flight, else *ready = 1 and *out (or the
+ * recorded device failure).  One check in flight per handle.
+ */
+rb_status rbfgs_residual_start(rbfgs_t h, int ncols, uint64_t col_seed);
+rb_status rbfgs_residual_poll(rbfgs_t h, int *ready, double *out);
+
+/* Device bytes rbfgs_init (plus a residual check of up to 1024 columns) allocates
+ * for an n x n problem with these options -- the admission test of the server. */
+rb_status rbfgs_footprint(int n, const rb_opts *opts, size_t *bytes);
+
+/*
  * Run steps until the sampled residual (check_cols columns, check_every
  * steps apart; a final exact or sampled confirmation with confirm_cols,
  * 0 = exact) is <= tol, or max_iter steps are done.  *iters gets the steps
@@ -275,6 +289,51 @@ rb_status rb_batch_solve(rb_batch_t b, double tol, int max_iter, int check_every
 /* X_i into out_dev (FP32, ld >= n_i); asynchronous. */
 rb_status rb_batch_export(rb_batch_t b, int i, void *out_dev, int64_t ld);
 rb_status rb_batch_destroy(rb_batch_t b);
+
+/*
+ * Serving loop with continuous batching (AdaRBFGS, Gaussian sketch).
+ * rb_srv_create starts a scheduler thread on the current device.  Each
+ * submitted request (an SPD A, tol, seed; q = 0 picks 32 round(sqrt(n)/32),
+ * at least 32) waits in a FIFO queue until its device footprint
+ * (rbfgs_footprint, plus a staging copy when A is in host memory) fits in
+ * hbm_budget_bytes and fewer than max_live requests are running; it then
+ * gets its own handle and stream, advances check_every steps at a time with
+ * non-blocking residual checks of check_cols sampled columns, and finishes
+ * when the residual is <= tol, after max_iter steps (RB_NOTCONV) or on a
+ * failure.  At the finish its factor L (FP32, ld ldo) is copied to `out`
+ * (device or host per out_on_device; NULL = discard) and its memory is
+ * released, which admits the next queued requests.  A and out must stay
+ * valid until the request is reported done.  A request's iterates depend
+ * only on its own (A, q, seed), not on the other requests in flight.
+ */
+typedef struct rb_srv *rb_srv_t;
+typedef struct {
+    int64_t ticket;
+    int32_t status;   /* RB_OK, RB_NOTCONV or an error */
+    int32_t iters;
+    double resid;     /* last sampled residual */
+    double latency_s; /* submit -> done */
+    double queue_s;   /* submit -> admitted */
+    int32_t n, q;
+} rb_srv_result;
+typedef struct {
+    int32_t completed, failed, queued, live;
+    double p50_s, p99_s;  /* latency percentiles of finished requests */
+    double solves_per_s;  /* completed / (last finish - first submit) */
+    uint64_t hbm_in_use;  /* admitted footprint */
+} rb_srv_summary;
+rb_status rb_srv_create(rb_srv_t *s, size_t hbm_budget_bytes, int max_live, int prec, int check_every,
+                        int check_cols, int max_iter);
+/* RB_ENOMEM when the request alone exceeds the budget. */
+rb_status rb_srv_submit(rb_srv_t s, int n, const void *A, int a_on_device, int64_t lda, int a_is_fp64, double tol,
+                        uint64_t seed, int q, void *out, int out_on_device, int64_t ldo, int64_t *ticket);
+rb_status rb_srv_poll(rb_srv_t s, int64_t ticket, int *done);
+/* Blocks until the request is done (RB_ETIMEOUT after timeout_s), fills *res and
+ * retires the ticket. */
+rb_status rb_srv_wait(rb_srv_t s, int64_t ticket, double timeout_s, rb_srv_result *res);
+rb_status rb_srv_stats(rb_srv_t s, rb_srv_summary *stats);
+/* Finishes every submitted request, then stops the scheduler. */
+rb_status rb_srv_destroy(rb_srv_t s);
 
 const char *rbfgs_status_string(int status);
 

@@ -73,6 +73,16 @@ _SIGS = {
                                  C.c_void_p, C.c_void_p]),
     "rb_batch_export": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64]),
     "rb_batch_destroy": (C.c_int, [C.c_void_p]),
+    "rbfgs_residual_start": (C.c_int, [C.c_void_p, C.c_int, C.c_uint64]),
+    "rbfgs_residual_poll": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "rbfgs_footprint": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p]),
+    "rb_srv_create": (C.c_int, [C.c_void_p, C.c_size_t, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]),
+    "rb_srv_submit": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int64, C.c_int, C.c_double,
+                                C.c_uint64, C.c_int, C.c_void_p, C.c_int, C.c_int64, C.c_void_p]),
+    "rb_srv_poll": (C.c_int, [C.c_void_p, C.c_int64, C.c_void_p]),
+    "rb_srv_wait": (C.c_int, [C.c_void_p, C.c_int64, C.c_double, C.c_void_p]),
+    "rb_srv_stats": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "rb_srv_destroy": (C.c_int, [C.c_void_p]),
 }
 
 
@@ -291,3 +301,67 @@ def rb_batch_export(b, i, out_dev, ld):
 
 def rb_batch_destroy(b):
     return _check(_lib().rb_batch_destroy(b), "rb_batch_destroy")
+
+
+def rbfgs_residual_start(h, ncols, col_seed):
+    return _check(_lib().rbfgs_residual_start(h, ncols, col_seed), "rbfgs_residual_start")
+
+
+def rbfgs_residual_poll(h):
+    ready = C.c_int()
+    out = C.c_double()
+    _check(_lib().rbfgs_residual_poll(h, C.byref(ready), C.byref(out)), "rbfgs_residual_poll")
+    return bool(ready.value), out.value
+
+
+def rbfgs_footprint(n, opts):
+    b = C.c_size_t()
+    _check(_lib().rbfgs_footprint(n, C.byref(opts), C.byref(b)), "rbfgs_footprint")
+    return b.value
+
+
+class SrvResult(C.Structure):
+    _fields_ = [("ticket", C.c_int64), ("status", C.c_int32), ("iters", C.c_int32), ("resid", C.c_double),
+                ("latency_s", C.c_double), ("queue_s", C.c_double), ("n", C.c_int32), ("q", C.c_int32)]
+
+
+class SrvStats(C.Structure):
+    _fields_ = [("completed", C.c_int32), ("failed", C.c_int32), ("queued", C.c_int32), ("live", C.c_int32),
+                ("p50_s", C.c_double), ("p99_s", C.c_double), ("solves_per_s", C.c_double),
+                ("hbm_in_use", C.c_uint64)]
+
+
+def rb_srv_create(hbm_budget_bytes, max_live, prec=RB_MIXED, check_every=32, check_cols=256, max_iter=20000):
+    s = C.c_void_p()
+    _check(_lib().rb_srv_create(C.byref(s), hbm_budget_bytes, max_live, prec, check_every, check_cols, max_iter),
+           "rb_srv_create")
+    return s
+
+
+def rb_srv_submit(s, n, A, a_on_device, lda, a_is_fp64, tol, seed, q=0, out=None, out_on_device=False, ldo=0):
+    t = C.c_int64()
+    _check(_lib().rb_srv_submit(s, n, _p(A), int(a_on_device), lda, int(a_is_fp64), tol, seed, q, _p(out),
+                                int(out_on_device), ldo, C.byref(t)), "rb_srv_submit")
+    return t.value
+
+
+def rb_srv_poll(s, ticket):
+    d = C.c_int()
+    _check(_lib().rb_srv_poll(s, ticket, C.byref(d)), "rb_srv_poll")
+    return bool(d.value)
+
+
+def rb_srv_wait(s, ticket, timeout_s=600.0):
+    r = SrvResult()
+    _check(_lib().rb_srv_wait(s, ticket, timeout_s, C.byref(r)), "rb_srv_wait")
+    return r
+
+
+def rb_srv_stats(s):
+    st = SrvStats()
+    _check(_lib().rb_srv_stats(s, C.byref(st)), "rb_srv_stats")
+    return st
+
+
+def rb_srv_destroy(s):
+    return _check(_lib().rb_srv_destroy(s), "rb_srv_destroy")

@@ -49,6 +49,14 @@ struct rb_ctx {
     cudaStream_t st2 = nullptr;
     cudaEvent_t ev_sk = nullptr, ev_g = nullptr, ev_core = nullptr;
 
+    // asynchronous residual check (rbfgs_residual_start / _poll)
+    int *h_J = nullptr;           // pinned column sample
+    int h_J_cap = 0;
+    double *h_rsum = nullptr;     // pinned sum of squares
+    int *h_status = nullptr;      // pinned copy of the status word
+    cudaEvent_t ev_res = nullptr;
+    int res_m = 0, res_pending = 0;
+
     // phase profiling (rbfgs_profile_step): events recorded between phases
     int prof_on = 0, prof_n = 0;
     cudaEvent_t prof_ev[24];
@@ -139,6 +147,10 @@ static void destroy_ctx(rb_ctx *h)
     rb_freet(h->rpart);
     rb_freet(h->rsum);
     tc_plan_destroy(h->tc);
+    if (h->h_J) cudaFreeHost(h->h_J);
+    if (h->h_rsum) cudaFreeHost(h->h_rsum);
+    if (h->h_status) cudaFreeHost(h->h_status);
+    if (h->ev_res) cudaEventDestroy(h->ev_res);
     if (h->ev_sk) cudaEventDestroy(h->ev_sk);
     if (h->ev_g) cudaEventDestroy(h->ev_g);
     if (h->ev_core) cudaEventDestroy(h->ev_core);
@@ -627,6 +639,81 @@ extern "C" rb_status rbfgs_residual(rbfgs_t h, int ncols, uint64_t col_seed, dou
     const double r = sqrt(sum / m);
     if (!isfinite(r)) return RB_ENONFINITE;
     *out = r;
+    return RB_OK;
+}
+
+extern "C" rb_status rbfgs_residual_start(rbfgs_t h, int ncols, uint64_t col_seed)
+{
+    if (!h || ncols < 0) return RB_EINVAL;
+    const int n = h->n;
+    const bool exact = (ncols == 0 || ncols >= n);
+    const int m = exact ? n : ncols;
+    RB_TRY(ensure_resid_ws(h, m));
+    if (!h->ev_res) {
+        RB_CUDA(cudaEventCreateWithFlags(&h->ev_res, cudaEventDisableTiming));
+        RB_CUDA(cudaMallocHost(&h->h_rsum, sizeof(double)));
+        RB_CUDA(cudaMallocHost(&h->h_status, sizeof(int)));
+    }
+    cudaStream_t st = h->st;
+    const int *J = nullptr;
+    if (!exact) {
+        if (m > h->h_J_cap) {  // grown once; reused while no check is in flight
+            if (h->h_J) cudaFreeHost(h->h_J);
+            h->h_J = nullptr;
+            h->h_J_cap = 0;
+            RB_CUDA(cudaMallocHost(&h->h_J, sizeof(int) * m));
+            h->h_J_cap = m;
+        }
+        std::vector<int> hj;
+        host_floyd(col_seed, n, m, hj);
+        memcpy(h->h_J, hj.data(), sizeof(int) * m);
+        RB_CUDA(cudaMemcpyAsync(h->J, h->h_J, sizeof(int) * m, cudaMemcpyHostToDevice, st));
+        J = h->J;
+    }
+    if (h->f64)
+        resid_launch<double>(h, exact, m, J);
+    else
+        resid_launch<float>(h, exact, m, J);
+    RB_CUDA(cudaMemcpyAsync(h->h_rsum, h->rsum, sizeof(double), cudaMemcpyDeviceToHost, st));
+    RB_CUDA(cudaMemcpyAsync(h->h_status, h->d_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RB_CUDA(cudaEventRecord(h->ev_res, st));
+    h->res_m = m;
+    h->res_pending = 1;
+    return RB_OK;
+}
+
+extern "C" rb_status rbfgs_residual_poll(rbfgs_t h, int *ready, double *out)
+{
+    if (!h || !ready || !out || !h->res_pending) return RB_EINVAL;
+    const cudaError_t q = cudaEventQuery(h->ev_res);
+    if (q == cudaErrorNotReady) {
+        *ready = 0;
+        return RB_OK;
+    }
+    if (q != cudaSuccess) return RB_ECUDA;
+    *ready = 1;
+    h->res_pending = 0;
+    const int s = *h->h_status;
+    if (s & ST_NOTSPD) return RB_ENOTSPD;
+    if (s & ST_NONFINITE) return RB_ENONFINITE;
+    if (s & ST_TIMEOUT) return RB_ETIMEOUT;
+    const double r = sqrt(*h->h_rsum / h->res_m);
+    if (!isfinite(r)) return RB_ENONFINITE;
+    *out = r;
+    return RB_OK;
+}
+
+extern "C" rb_status rbfgs_footprint(int n, const rb_opts *opts, size_t *bytes)
+{
+    if (n < 1 || !opts || !bytes) return RB_EINVAL;
+    const size_t e = (opts->prec == RB_FP64) ? 8 : 4, q = (size_t)opts->q, nn = (size_t)n * n;
+    size_t b = 2 * nn * e;                                // A and the iterate
+    b += 10 * (size_t)n * q * e + 4 * q * q * 8;          // panels and q x q matrices
+    b += (size_t)((n + 127) / 128) * q * q * 8;           // Gram chunk partials
+    b += 3 * (size_t)n * 1024 * e;                        // residual workspace (<= 1024 columns)
+    if (opts->method == RB_METHOD_RBFGS) b += 3 * (size_t)n * q * e;
+    b += 2 * (size_t)n * q * e;                           // tensor-core operand splits
+    *bytes = b + (1u << 20);
     return RB_OK;
 }
 
