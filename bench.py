@@ -51,6 +51,12 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="budget of the oracle sample")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=96)
+    ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--batch-steps", type=int, default=2000)
     return ap.parse_args()
 
 
@@ -229,6 +235,68 @@ def config(args, form):
             "residual_check": f"every {CHECK_EVERY} steps on {CHECK_COLS} columns, confirmed on {CONFIRM_COLS}"}
 
 
+def run_serving(B, wl, args):
+    """Open-loop Poisson stream (first --serve-requests requests of the seeded stream) through
+    the continuous-batching server: mixed form, check every 32 steps on 128 columns."""
+    import numpy as np
+    import torch
+
+    stream = wl.c5_stream(requests=args.serve_requests, rate=args.serve_rate)
+    mats = {}
+    for r in stream:  # inputs built before the clock starts (device-resident)
+        mats[r["seed"]] = wl.c5_matrix(r["n"], r["seed"], device="cuda")
+    torch.cuda.synchronize()
+    budget = wl.WORKLOADS["c5_serving"]["budget_bytes"]
+    s = B.rb_srv_create(budget, 64, B.RB_MIXED, 32, 128, 4000)
+    tickets = []
+    t0 = time.perf_counter()
+    for r in stream:
+        wait = r["t"] - (time.perf_counter() - t0)
+        if wait > 0:
+            time.sleep(wait)
+        A = mats[r["seed"]]
+        tickets.append(B.rb_srv_submit(s, r["n"], A.data_ptr(), True, r["n"], False, r["tol"], r["seed"], r["q"]))
+    res = [B.rb_srv_wait(s, t, 3600.0) for t in tickets]
+    wall = time.perf_counter() - t0
+    st = B.rb_srv_stats(s)
+    B.rb_srv_destroy(s)
+    ok = [r for r in res if r.status == B.RB_OK]
+    lat = sorted(r.latency_s for r in res)
+    return {"workload": f"first {len(stream)} requests of the Poisson stream at {args.serve_rate:g} req/s, "
+                        "n log-uniform in [512, 8192], A = M^T M/(2n) + 1e-3 I, tol in {1e-3,1e-4,1e-6}, "
+                        "q = 32 round(sqrt(n)/32), mixed form, HBM budget 120 GiB, <= 64 live",
+            "requests": len(res), "converged": len(ok), "not_converged_in_4000_steps": len(res) - len(ok),
+            "solves_per_s": len(res) / wall, "p50_s": lat[len(lat) // 2],
+            "p99_s": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)],
+            "mean_queue_s": statistics.mean(r.queue_s for r in res), "wall_s": wall,
+            "server_p50_s": st.p50_s, "server_p99_s": st.p99_s}
+
+
+def run_batched(B, wl, args):
+    """512 uneven SPD problems, coordinate RBFGS, one persistent launch per round of 100 steps."""
+    import numpy as np
+    import torch
+
+    probs = wl.c4_problems(count=args.batch_count)
+    devs = [torch.from_numpy(np.ascontiguousarray(A.T)).float().cuda() for A, _, _ in probs]
+    n = [A.shape[0] for A, _, _ in probs]
+    q = [qq for _, qq, _ in probs]
+    b = B.rb_batch_create(n, [d.data_ptr() for d in devs], n, False, q, 4,
+                          stream=torch.cuda.current_stream().cuda_stream)
+    B.rb_batch_step(b, 10)  # warm-up (also captures the round graph shape)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rc, iters, resid, status, nconv = B.rb_batch_solve(b, len(n), 1e-5, args.batch_steps, 100, 16)
+    wall = time.perf_counter() - t0
+    B.rb_batch_destroy(b)
+    steps = sum(iters)
+    return {"workload": f"{len(n)} problems, n log-uniform in [32, 1024], kappa log-uniform in [1e1, 1e4], "
+                        "coordinate blocks q in {4,8,16,32} with trace probabilities, tol 1e-5, "
+                        f"at most {args.batch_steps} steps each",
+            "converged": nconv, "problem_steps_per_s": steps / wall, "wall_s": wall,
+            "median_resid": float(np.median(resid)), "max_resid": float(np.max(resid))}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -341,6 +409,16 @@ def main():
         e2e = {"value": world * args.steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": 4 * n * n,
                "d2h_bytes_per_step": 4 * n * n, "seconds_per_step": e2e_s / args.steps}
 
+    # ---- serving loop on the request-stream workload (bounded sample, open loop) ----
+    serving = None
+    if not args.no_serve:
+        serving = run_serving(B, wl, args)
+
+    # ---- batched coordinate RBFGS (one persistent launch per round) ----
+    batched = None
+    if not args.no_batch:
+        batched = run_batched(B, wl, args)
+
     # ---- CPU oracle on a bounded sample (rank 0, N = 1 only) ----
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -361,6 +439,7 @@ def main():
                "latency_s": {"p50": statistics.median(lat), "p99": p99},
                "fp32_form": fp32, "roofline": roofline, "phases_ms": phases, "step_ms": step_ms,
                "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
+               "serving": serving, "batched": batched,
                "wall_s": wall}
         print(json.dumps(out), flush=True)
     if world > 1:

@@ -1,0 +1,67 @@
+"""The n = 16384, q = 128 workload in the launch configuration the benchmark
+times (mixed form): one step against the FP64 oracle's step, then a solve to
+1e-4 whose factor is checked by the oracle in FP64 on sampled columns."""
+import numpy as np
+import pytest
+
+import paper_1602_01768_gb300._binding as B
+from oracle import oracle as orc
+from paper_1602_01768_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+N, Q, TOL = 16384, 128, 1e-4
+
+
+@pytest.fixture(scope="module")
+def c3():
+    import torch
+
+    A = wl.c3_matrix(n=N, device="cuda")  # FP32, symmetric
+    torch.cuda.synchronize()
+    A64 = np.asfortranarray(A.double().cpu().numpy())
+    return A, A64
+
+
+def _handle(A, prec):
+    import torch
+
+    o = B.make_opts(method=B.RB_METHOD_ADARBFGS, sketch=B.RB_SKETCH_GAUSS, q=Q, prec=prec, seed=3)
+    return B.rbfgs_init(N, A.data_ptr(), N, False, o, torch.cuda.current_stream().cuda_stream)
+
+
+def _L(h):
+    import torch
+
+    out = torch.empty(N, N, dtype=torch.float32, device="cuda")
+    B.rbfgs_export(h, B.RB_WHAT_L, out.data_ptr(), N)
+    torch.cuda.synchronize()
+    return out.cpu().numpy().T.astype(np.float64)  # column-major view
+
+
+def test_first_step_matches_oracle_at_full_size(c3):
+    A, A64 = c3
+    h = _handle(A, B.RB_MIXED)
+    try:
+        B.adarbfgs_step(h, 1)
+        Lg = _L(h)
+    finally:
+        B.rbfgs_destroy(h)
+    _, L1 = orc.adarbfgs_run(A64, np.eye(N), Q, orc.SKETCH_GAUSS, 3, 0, 0, 1)
+    I = np.eye(N)
+    # the correction S^ V carries single-pass TF32 rounding (2^-11) and FP32 sketch differences
+    corr = np.linalg.norm(Lg - L1) / np.linalg.norm(L1 - I)
+    assert corr <= 2e-3, corr
+
+
+def test_solve_to_tolerance_checked_in_fp64(c3):
+    A, A64 = c3
+    h = _handle(A, B.RB_MIXED)
+    try:
+        st, iters, r = B.rbfgs_solve(h, TOL, 20000, 32, 256, 1024)
+        assert st == B.RB_OK and r <= TOL
+        L = _L(h)
+    finally:
+        B.rbfgs_destroy(h)
+    r64 = orc.residual_sampled(A64, 4, 12345, L=L)
+    assert r64 <= 2 * TOL, (r64, r, iters)
