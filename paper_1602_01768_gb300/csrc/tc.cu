@@ -40,11 +40,12 @@ struct Cfg {
     // TMA tile (K- or M-contiguous) that the converter moves into TMEM.
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES * (TERMS == 3 ? 2 : 1);
     static constexpr int A_TMEM_COLS = (TERMS == 3) ? 64 : 32;  // per stage: hi (32 cols) [+ lo (32 cols)]
+    // TMEM: two chunk accumulators (2 BN columns), then the A stages
     static constexpr int STAGES_SMEM = (200 * 1024) / STAGE_BYTES;
-    static constexpr int STAGES_TMEM = CONVERT ? (512 - BN) / A_TMEM_COLS : 8;
+    static constexpr int STAGES_TMEM = CONVERT ? (512 - 2 * BN) / A_TMEM_COLS : 8;
     static constexpr int STAGES_A = STAGES_SMEM < STAGES_TMEM ? STAGES_SMEM : STAGES_TMEM;
     static constexpr int STAGES = STAGES_A > 8 ? 8 : STAGES_A;
-    static constexpr int TMEM_COLS = CONVERT ? 512 : (BN < 32 ? 32 : BN);
+    static constexpr int TMEM_COLS = CONVERT ? 512 : (2 * BN < 32 ? 32 : 2 * BN);
     static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 /*align*/ + 512 /*barriers*/;
     static_assert(STAGES >= 2, "pipeline needs two stages");
 };
@@ -129,8 +130,9 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     uint64_t *full = (uint64_t *)bar_area;
     uint64_t *conv = full + STAGES;
     uint64_t *empty = conv + STAGES;
-    uint64_t *accf = empty + STAGES;
-    uint32_t *tmem_slot = (uint32_t *)(accf + 1);
+    uint64_t *chunk_full = empty + STAGES;  // [2] accumulator b holds a finished K chunk
+    uint64_t *chunk_free = chunk_full + 2;  // [2] accumulator b drained
+    uint32_t *tmem_slot = (uint32_t *)(chunk_free + 2);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5;
@@ -146,7 +148,10 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
             mbar_init(smem_u32(&conv[s]), 128);
             mbar_init(smem_u32(&empty[s]), 1);
         }
-        mbar_init(smem_u32(accf), 1);
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&chunk_full[b]), 1);
+            mbar_init(smem_u32(&chunk_free[b]), 128);
+        }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -159,12 +164,13 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem = *tmem_slot;  // accumulator: columns [0, BN); A stages after it
+    const uint32_t tmem = *tmem_slot;  // accumulators: columns [0, 2 BN); A stages after them
 
     auto stage_a = [&](int s) { return smem + s * CF::STAGE_BYTES; };
     auto stage_b = [&](int s) { return smem + s * CF::STAGE_BYTES + CF::A_BYTES; };
     auto stage_blo = [&](int s) { return smem + s * CF::STAGE_BYTES + CF::A_BYTES + CF::B_BYTES; };
-    auto a_col = [&](int s) { return (uint32_t)(BN + s * CF::A_TMEM_COLS); };
+    auto a_col = [&](int s) { return (uint32_t)(2 * BN + s * CF::A_TMEM_COLS); };
+    const int nchunks = (nk + CHUNK_KB - 1) / CHUNK_KB;
 
     if (warp == 0) {
         // ---------------- TMA producer ----------------
@@ -193,45 +199,81 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
             bool ok = true;
             for (int i = 0; i < nk && ok; ++i) {
                 const int s = i % STAGES;
+                const int c = i / CHUNK_KB, b = c & 1, ic = i % CHUNK_KB;
+                if (ic == 0 && c >= 2 &&
+                    !mbar_wait(smem_u32(&chunk_free[b]), ((c >> 1) - 1) & 1, err, abort_flag)) {
+                    ok = false;
+                    break;
+                }
                 const uint32_t wb = CF::CONVERT ? smem_u32(&conv[s]) : smem_u32(&full[s]);
                 if (!mbar_wait(wb, (i / STAGES) & 1, err, abort_flag)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
+                const uint32_t dacc = tmem + (uint32_t)(b * BN);
                 const uint32_t b_hi = smem_u32(stage_b(s)), b_lo = smem_u32(stage_blo(s));
 #pragma unroll
                 for (int kk = 0; kk < BK / 8; ++kk) {
                     // K = 8 TF32 per MMA: 32 bytes along B's 128-byte swizzle row, 8 TMEM columns of A
                     const uint64_t db_hi = umma_desc(b_hi + kk * 32, 16, 1024);
-                    const uint32_t first = (i == 0 && kk == 0) ? 0u : 1u;
+                    const uint32_t first = (ic == 0 && kk == 0) ? 0u : 1u;  // each chunk starts a fresh sum
                     if (CF::CONVERT) {
                         const uint32_t ta_hi = tmem + a_col(s) + 8 * kk;
                         if (TERMS == 3) {
                             const uint64_t db_lo = umma_desc(b_lo + kk * 32, 16, 1024);
-                            mma_tf32_ts(tmem, ta_hi + 32, db_hi, idesc, first);  // lo x hi
-                            mma_tf32_ts(tmem, ta_hi, db_lo, idesc, 1u);          // hi x lo
-                            mma_tf32_ts(tmem, ta_hi, db_hi, idesc, 1u);          // hi x hi
+                            mma_tf32_ts(dacc, ta_hi + 32, db_hi, idesc, first);  // lo x hi
+                            mma_tf32_ts(dacc, ta_hi, db_lo, idesc, 1u);          // hi x lo
+                            mma_tf32_ts(dacc, ta_hi, db_hi, idesc, 1u);          // hi x hi
                         } else {
-                            mma_tf32_ts(tmem, ta_hi, db_hi, idesc, first);
+                            mma_tf32_ts(dacc, ta_hi, db_hi, idesc, first);
                         }
                     } else {
                         const uint64_t da = umma_desc(smem_u32(stage_a(s)) + kk * 32, 16, 1024);
-                        mma_tf32(tmem, da, db_hi, idesc, first);
+                        mma_tf32(dacc, da, db_hi, idesc, first);
                     }
                 }
                 mma_commit(smem_u32(&empty[s]));
+                if (ic == CHUNK_KB - 1 || i == nk - 1) mma_commit(smem_u32(&chunk_full[b]));
             }
-            if (ok) mma_commit(smem_u32(accf));
         }
     } else if (warp >= 4) {
         const int t = threadIdx.x - 128;  // 0..127 = tile row = TMEM lane
         const int wq = warp & 3;          // this warp's TMEM lane quarter
+        // Running sum of the finished K chunks, one tile row per thread, added on
+        // the CUDA cores with round-to-nearest.  The tensor core's FP32 accumulation
+        // drifts toward zero over long K (about one truncation per MMA step, relative
+        // to the growing sum); restarting it every CHUNK_KB k-blocks bounds that drift.
+        float run[BN];
+#pragma unroll
+        for (int j = 0; j < BN; ++j) run[j] = 0.f;
+        int drained = 0;
+        bool ok = true;
+        auto drain = [&](int c) {
+            const int b = c & 1;
+            if (!mbar_wait(smem_u32(&chunk_full[b]), (c >> 1) & 1, err, abort_flag)) {
+                ok = false;
+                return;
+            }
+            tc_fence_after();
+#pragma unroll
+            for (int c0 = 0; c0 < BN; c0 += 16) {
+                uint32_t r[16];
+                tmem_ld16(tmem + ((uint32_t)(32 * wq) << 16) + (uint32_t)(b * BN + c0), r);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) run[c0 + j] += __uint_as_float(r[j]);
+            }
+            tc_fence_before();
+            mbar_arrive(smem_u32(&chunk_free[b]));
+        };
         // ---------------- A operand into TMEM (hi = x, lo = x - hi(x)) ----------------
         if (CF::CONVERT) {
-            for (int i = 0; i < nk; ++i) {
+            for (int i = 0; i < nk && ok; ++i) {
                 const int s = i % STAGES;
-                if (!mbar_wait(smem_u32(&full[s]), (i / STAGES) & 1, err, abort_flag)) break;
+                if (!mbar_wait(smem_u32(&full[s]), (i / STAGES) & 1, err, abort_flag)) {
+                    ok = false;
+                    break;
+                }
                 float v[32];
                 load_a_row<AMN>(stage_a(s), t, v);
                 uint32_t r[32];
@@ -247,27 +289,25 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                 asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 tc_fence_before();
                 mbar_arrive(smem_u32(&conv[s]));
+                // chunk c - 2 is drained once chunk c - 1 is fully converted, before the
+                // first conversion of chunk c (whose MMA needs that accumulator)
+                if ((i + 1) % CHUNK_KB == 0 && (i + 1) / CHUNK_KB >= 2) drain(drained++);
             }
         }
+        while (ok && drained < nchunks) drain(drained++);
         // ---------------- epilogue ----------------
-        const bool got = mbar_wait(smem_u32(accf), 0, err, abort_flag);
-        tc_fence_after();
-        if (got) {
+        if (ok) {
             const int m = m0 + 32 * wq + lane;
             const bool split = (part != nullptr);
-            for (int c0 = 0; c0 < BN; c0 += 16) {
-                uint32_t r[16];
-                tmem_ld16(tmem + ((uint32_t)(32 * wq) << 16) + (uint32_t)c0, r);
-                if (m < M) {
+            if (m < M) {
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const int nn = n0 + c0 + j;
-                        if (nn >= N) break;
-                        const float v = __uint_as_float(r[j]);
+                for (int j = 0; j < BN; ++j) {
+                    const int nn = n0 + j;
+                    if (nn < N) {
                         if (split) {
-                            part[(size_t)blockIdx.z * M * N + m + (size_t)nn * M] = v;
+                            part[(size_t)blockIdx.z * M * N + m + (size_t)nn * M] = run[j];
                         } else {
-                            float o = alpha * v;
+                            float o = alpha * run[j];
                             if (beta != 0.f) o = fmaf(beta, Cin[m + (int64_t)nn * ldcin], o);
                             C[m + (int64_t)nn * ldc] = o;
                         }

@@ -9,6 +9,8 @@ namespace tcx {
 constexpr int BM = 128;
 constexpr int BK = 32;  // 32 FP32 = one 128-byte swizzle row
 constexpr int A_TILE_BYTES = BM * BK * 4;
+// k-blocks per tensor-core accumulation chunk (CHUNK_KB x BK = 512 of K, 64 MMA steps)
+constexpr int CHUNK_KB = 16;
 constexpr long long WAIT_LIMIT_CYCLES = 1ll << 32;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
