@@ -365,7 +365,7 @@ def main():
     upd_ms = phases.get("update L", float("nan"))
     upd_bytes = 2 * 4 * n * n + 2 * 4 * n * q  # read + write L, read S^ and V
     achieved = upd_bytes / (upd_ms * 1e-3) / 1e9
-    roofline = {"kernel": "rank-q update L += S^ V (k_tc_gemm, 1xTF32, beta=1)", "bound": "hbm",
+    roofline = {"kernel": "rank-q update L += S^ V (k_tc_update, persistent, 1xTF32)", "bound": "hbm",
                 "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "peak_kind": f"{peak_kind} HBM copy",
                 "traffic": (UPDATE_TRAFFIC_N8192_Q128 * (n / 8192) ** 2) if q == 128 else None,

@@ -45,9 +45,11 @@ struct rb_ctx {
 
     tc_plan *tc = nullptr;  // tensor-core plan (FP32 storage, TF32 modes)
 
-    // side stream for the q x q work that does not need W = L^T G (fork/join by events)
-    cudaStream_t st2 = nullptr;
-    cudaEvent_t ev_sk = nullptr, ev_g = nullptr, ev_core = nullptr;
+    // Tensor-core step: the n x n passes run on a high-priority internal stream
+    // st1 and the q x q work on a low-priority side stream st2 (fork/join by
+    // events, joined back into the handle's stream at the end of each step).
+    cudaStream_t st1 = nullptr, st2 = nullptr;
+    cudaEvent_t ev_sk = nullptr, ev_g = nullptr, ev_core = nullptr, ev_in = nullptr, ev_out = nullptr;
 
     // asynchronous residual check (rbfgs_residual_start / _poll)
     int *h_J = nullptr;           // pinned column sample
@@ -154,6 +156,9 @@ static void destroy_ctx(rb_ctx *h)
     if (h->ev_sk) cudaEventDestroy(h->ev_sk);
     if (h->ev_g) cudaEventDestroy(h->ev_g);
     if (h->ev_core) cudaEventDestroy(h->ev_core);
+    if (h->ev_in) cudaEventDestroy(h->ev_in);
+    if (h->ev_out) cudaEventDestroy(h->ev_out);
+    if (h->st1) cudaStreamDestroy(h->st1);
     if (h->st2) cudaStreamDestroy(h->st2);
     delete h;
 }
@@ -453,22 +458,36 @@ static void ada_step_simt(rb_ctx *h)
 
 static bool ensure_side_stream(rb_ctx *h)
 {
-    if (h->st2) return true;
-    if (cudaStreamCreateWithFlags(&h->st2, cudaStreamNonBlocking) != cudaSuccess) return false;
+    if (h->st1 && h->st2 && h->ev_out) return true;
+    int least = 0, greatest = 0;
+    cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (!h->st1 && cudaStreamCreateWithPriority(&h->st1, cudaStreamNonBlocking, greatest) != cudaSuccess) return false;
+    if (!h->st2 && cudaStreamCreateWithPriority(&h->st2, cudaStreamNonBlocking, least) != cudaSuccess) return false;
     const unsigned fl = cudaEventDisableTiming;
-    if (cudaEventCreateWithFlags(&h->ev_sk, fl) != cudaSuccess || cudaEventCreateWithFlags(&h->ev_g, fl) != cudaSuccess ||
-        cudaEventCreateWithFlags(&h->ev_core, fl) != cudaSuccess)
-        return false;
+    for (cudaEvent_t *e : {&h->ev_sk, &h->ev_g, &h->ev_core, &h->ev_in, &h->ev_out})
+        if (!*e && cudaEventCreateWithFlags(e, fl) != cudaSuccess) return false;
     return true;
 }
 
-// Tensor-core step.  The q x q work runs on a side stream while the main
-// stream streams the n x n passes:
+// SMs that the stream-K GEMMs leave to the side stream while it runs the
+// Gram products and the q x q core.
+constexpr int SIDE_SMS = 8;
+
+// Tensor-core step.  The q x q work runs on a low-priority side stream while
+// the n x n passes run on a high-priority one; the GEMMs that overlap side
+// work leave SIDE_SMS SMs free for it:
 //   main:  sketch -> S = L S~ -> G = A S -> W^T = L^T G -> [join] -> V, S^ -> L += S^ V
-//   side:  [after sketch] S~^T S~, D^-1   [after G] S^T G, C^-1
+//   side:            [after S]  S~^T S~, D^-1   [after G]  S^T G, C^-1
 static void ada_step_tc(rb_ctx *h)
 {
     const int n = h->n, q = h->q;
+    const bool fork = !h->core_fp64 && ensure_side_stream(h);
+    cudaStream_t user = h->st;
+    if (fork) {  // run the step on st1 (every helper launches on h->st), joined to the caller's stream
+        cudaEventRecord(h->ev_in, user);
+        cudaStreamWaitEvent(h->st1, h->ev_in, 0);
+        h->st = h->st1;
+    }
     cudaStream_t st = h->st;
     const int *stp = h->d_status;
     float *A = (float *)h->A, *L = (float *)h->X, *St = (float *)h->St, *S = (float *)h->S, *G = (float *)h->G;
@@ -476,20 +495,20 @@ static void ada_step_tc(rb_ctx *h)
           *Di = (float *)h->Dinv;
     const int acc = (h->prec == RB_TF32) ? 1 : 3;  // split terms of the accuracy-critical products
     const int upd = (h->prec == RB_TF32X3) ? 3 : 1;
-    const bool fork = !h->core_fp64 && ensure_side_stream(h);
+    const int rsv = fork ? SIDE_SMS : 0;
     cudaStream_t side = fork ? h->st2 : st;
     ada_draw<float>(h, St);
+    mark(h, "sketch");
+    tc_gemm_nk(h->tc, st, acc, TC_A_MN, n, q, n, L, n, St, n, S, n, stp);       // S = L S~   (A = L, M-contiguous)
     if (fork) {
         cudaEventRecord(h->ev_sk, st);
         cudaStreamWaitEvent(side, h->ev_sk, 0);
         launch_gram<float>(side, n, q, q, St, n, St, n, h->part, h->N);  // S~^T S~ -> D^-1
         launch_core_ada32(side, q, h->N, nullptr, Di, nullptr, h->d_status);
     }
-    mark(h, "sketch");
-    tc_gemm_nk(h->tc, st, acc, TC_A_MN, n, q, n, L, n, St, n, S, n, stp);   // S = L S~   (A = L, M-contiguous)
     mark(h, "S=LS~");
-    tc_gemm_nk(h->tc, st, acc, TC_A_K, n, q, n, A, n, S, n, G, n, stp);     // G = A S    (A symmetric)
-    mark(h, "G=AS");
+    tc_gemm_nk(h->tc, st, acc, TC_A_K, n, q, n, A, n, S, n, G, n, stp, rsv);  // G = A S    (A symmetric)
+    mark(h, fork ? "G=AS | D core" : "G=AS");
     if (fork) {
         cudaEventRecord(h->ev_g, st);
         cudaStreamWaitEvent(side, h->ev_g, 0);
@@ -506,9 +525,9 @@ static void ada_step_tc(rb_ctx *h)
             launch_core_ada<float>(st, q, h->M, h->N, Ci, Di, h->d_status);
         mark(h, "q x q core");
     }
-    tc_gemm_nk(h->tc, st, acc, TC_A_K, n, q, n, L, n, G, n, W, n, stp);     // W^T = L^T G (n x q)
-    if (fork) cudaStreamWaitEvent(st, h->ev_core, 0);                          // join: C^-1, D^-1 ready
-    mark(h, fork ? "W=G^TL | grams+core" : "W=G^TL");
+    tc_gemm_nk(h->tc, st, acc, TC_A_K, n, q, n, L, n, G, n, W, n, stp, rsv);  // W^T = L^T G (n x q)
+    if (fork) cudaStreamWaitEvent(st, h->ev_core, 0);                            // join: C^-1, D^-1 ready
+    mark(h, fork ? "W=G^TL | C core" : "W=G^TL");
     // V = D^-1 S~^T - C^-1 W, stored q x n (ld q); W^T is n x q (ld n)
     gemm_simt<float>(st, false, true, q, n, q, 1.f, Di, q, St, n, 0.f, V, q, stp);
     gemm_simt<float>(st, false, true, q, n, q, -1.f, Ci, q, W, n, 1.f, V, q, stp);
@@ -519,6 +538,11 @@ static void ada_step_tc(rb_ctx *h)
     if (upd != 1 || tc_update_persistent(h->tc, st, n, q, Sh, V, L, n, stp) != 0)
         tc_update(h->tc, st, upd, n, q, Sh, V, L, n, stp);
     mark(h, "update L");
+    if (fork) {
+        cudaEventRecord(h->ev_out, h->st1);
+        h->st = user;
+        cudaStreamWaitEvent(user, h->ev_out, 0);
+    }
 }
 
 extern "C" rb_status adarbfgs_step(rbfgs_t h, int nsteps)

@@ -1,6 +1,7 @@
-// core32.cu -- blocked FP32 q x q core of AdaRBFGS for the FP32-storage
-// modes: lower Cholesky C C^T = S^T A S (and D D^T = S~^T S~) and the
-// inverse of each factor, one CTA per matrix, everything in shared memory.
+// core32.cu -- FP32 q x q core of AdaRBFGS for the FP32-storage modes:
+// lower Cholesky C C^T = S^T A S (and D D^T = S~^T S~) and the inverse of
+// each factor, one CTA per matrix.  q <= 128 takes k_core_blk (32 x 32 blocks,
+// block GEMMs between a few barriers); larger q the older blocked kernel:
 //
 // Cholesky: 32-column panels; the 32 x 32 diagonal block is factored by one
 // warp (row per lane, warp-synchronous), the rows below it are solved in
@@ -166,11 +167,189 @@ __global__ void __launch_bounds__(CT, 1) k_core32(int q, const double *M, const 
     }
 }
 
+// q <= 128: blocked right-looking factorisation on 32 x 32 blocks (q padded
+// to 32 nb with the identity, whose factor and inverse are the identity).
+// Per block column p:
+//   warp 0       factors the diagonal block (row per lane, shuffles) and
+//                inverts it (column per lane, forward substitution);
+//   all threads  panel L_ip = A_ip X_pp^T, then the trailing update
+//                A_ij -= L_ip L_jp^T of the lower block triangle;
+// then the off-diagonal blocks of X = L^-1 by block diagonals d = 1, 2, ..:
+//   T = sum_{k=j}^{i-1} L_ik X_kj,  X_ij = -X_ii T   (i = j + d).
+// Every phase but the diagonal block is a set of small GEMMs, so the kernel
+// needs a handful of barriers instead of one per column.
+constexpr int KT = 512;   // threads
+constexpr int LDK = 129;  // padded leading dimension: row and column walks are conflict-free
+
+__device__ __forceinline__ float &ak(float *m, int i, int j) { return m[i + j * LDK]; }
+
+__global__ void __launch_bounds__(KT, 1) k_core_blk(int q, const double *M, const double *N, float *Cinv,
+                                                    float *Dinv, int *status)
+{
+    extern __shared__ float smk[];
+    float *a = smk;               // A, overwritten by L (lower blocks)
+    float *x = smk + 128 * LDK;   // X = L^-1 (lower blocks); upper blocks hold T
+    __shared__ int fail;
+    if (status_bad(status)) return;
+    const double *src = blockIdx.x == 0 ? M : N;
+    float *dst = blockIdx.x == 0 ? Cinv : Dinv;
+    const int nb = (q + 31) / 32, QP = 32 * nb;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) fail = 0;
+    // coalesced load of the padded matrix (thread: one row, every fourth column) ...
+    {
+        const int i = tid & 127, j0 = tid >> 7;
+        float v[32];
+#pragma unroll
+        for (int u = 0; u < 32; ++u) {
+            const int j = j0 + 4 * u;
+            v[u] = (i < q && j < q) ? (float)src[i + (size_t)j * q] : (i == j ? 1.f : 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < 32; ++u) ak(a, i, j0 + 4 * u) = v[u];
+    }
+    __syncthreads();
+    // ... then the lower triangle takes the symmetric part 0.5 (a_ij + a_ji) (upper left as it is)
+    for (int e = tid; e < QP * QP; e += KT) {
+        const int i = e % QP, j = e / QP;
+        if (i > j) ak(a, i, j) = 0.5f * (ak(a, i, j) + ak(a, j, i));
+    }
+    __syncthreads();
+    for (int p = 0; p < nb; ++p) {
+        const int o = 32 * p;
+        if (warp == 0) {
+            // ---- diagonal block: L_pp in place (lane = row); compact loops keep the
+            // code small (this runs once per block column, mostly alone on the SM) ----
+            bool bad = false;
+            for (int j = 0; j < 32; ++j) {
+                const float d = ak(a, o + j, o + j);
+                bad = bad || !(d > 0.f) || !isfinite(d);
+                const float sd = sqrtf(d), inv = 1.f / sd;
+                float lij = 0.f;
+                if (lane > j) {
+                    lij = ak(a, o + lane, o + j) * inv;
+                    ak(a, o + lane, o + j) = lij;
+                } else if (lane == j) {
+                    ak(a, o + j, o + j) = sd;
+                }
+                __syncwarp();
+                for (int c = j + 1; c <= lane; ++c) ak(a, o + lane, o + c) -= lij * ak(a, o + c, o + j);
+                __syncwarp();
+            }
+            if (bad) {
+                if (lane == 0) fail = 1;
+            } else {
+                // ---- X_pp = L_pp^-1 (lane = column, kept in its column of x) ----
+                for (int i = 0; i < 32; ++i) {
+                    float s0 = (i == lane) ? 1.f : 0.f, s1 = 0.f;
+                    int k = lane;
+                    for (; k + 1 < i; k += 2) {
+                        s0 -= ak(a, o + i, o + k) * ak(x, o + k, o + lane);
+                        s1 -= ak(a, o + i, o + k + 1) * ak(x, o + k + 1, o + lane);
+                    }
+                    if (k < i) s0 -= ak(a, o + i, o + k) * ak(x, o + k, o + lane);
+                    ak(x, o + i, o + lane) = (i >= lane) ? (s0 + s1) / ak(a, o + i, o + i) : 0.f;
+                }
+            }
+        }
+        __syncthreads();
+        if (fail) {
+            if (tid == 0) atomicOr(status, ST_NOTSPD);
+            return;
+        }
+        // ---- panel: L_ip = A_ip X_pp^T, i > p (into registers, then stored) ----
+        const int npanel = (nb - 1 - p) * 1024;
+        float pv[6];
+#pragma unroll
+        for (int u = 0; u < 6; ++u) {
+            const int e = tid + u * KT;
+            pv[u] = 0.f;
+            if (e < npanel) {
+                const int blk = e >> 10, w = e & 1023, r = w & 31, c = w >> 5;  // row r, column c of block
+                const int i = o + 32 * (blk + 1) + r;
+                float sacc = 0.f;
+#pragma unroll 8
+                for (int k = 0; k <= c; ++k) sacc += ak(a, i, o + k) * ak(x, o + c, o + k);  // X_pp lower: k <= c
+                pv[u] = sacc;
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < 6; ++u) {
+            const int e = tid + u * KT;
+            if (e < npanel) {
+                const int blk = e >> 10, w = e & 1023, r = w & 31, c = w >> 5;
+                ak(a, o + 32 * (blk + 1) + r, o + c) = pv[u];
+            }
+        }
+        __syncthreads();
+        // ---- trailing update: A_ij -= L_ip L_jp^T, p < j <= i ----
+        const int m = nb - 1 - p;            // trailing blocks per side
+        const int ntr = m * (m + 1) / 2 * 1024;  // lower block triangle incl. diagonal blocks
+        for (int e = tid; e < ntr; e += KT) {
+            int blk = e >> 10, bj = 0;
+            while (blk >= m - bj) {  // column-major packing of the lower block triangle
+                blk -= m - bj;
+                ++bj;
+            }
+            const int bi = bj + blk, w = e & 1023, r = w & 31, c = w >> 5;
+            const int i = o + 32 * (bi + 1) + r, j = o + 32 * (bj + 1) + c;
+            float sacc = 0.f;
+#pragma unroll 8
+            for (int k = 0; k < 32; ++k) sacc += ak(a, i, o + k) * ak(a, j, o + k);
+            ak(a, i, j) -= sacc;
+        }
+        __syncthreads();
+    }
+    // ---- off-diagonal blocks of X by block diagonals ----
+    for (int d = 1; d < nb; ++d) {
+        const int nt = (nb - d) * 1024;
+        // T_(j+d, j) = sum_{k=j}^{j+d-1} L_(j+d, k) X_(k, j), stored in the upper block (j, j+d) of x
+        for (int e = tid; e < nt; e += KT) {
+            const int bj = e >> 10, w = e & 1023, r = w & 31, c = w >> 5, bi = bj + d;
+            float sacc = 0.f;
+            for (int bk = bj; bk < bi; ++bk) {
+#pragma unroll 8
+                for (int k = 0; k < 32; ++k) sacc += ak(a, 32 * bi + r, 32 * bk + k) * ak(x, 32 * bk + k, 32 * bj + c);
+            }
+            ak(x, 32 * bj + r, 32 * bi + c) = sacc;  // transposed slot: row r of T at (bj, bi)
+        }
+        __syncthreads();
+        // X_(i, j) = -X_ii T,  X_ii lower
+        for (int e = tid; e < nt; e += KT) {
+            const int bj = e >> 10, w = e & 1023, r = w & 31, c = w >> 5, bi = bj + d;
+            float sacc = 0.f;
+#pragma unroll 8
+            for (int k = 0; k <= r; ++k) sacc += ak(x, 32 * bi + r, 32 * bi + k) * ak(x, 32 * bj + k, 32 * bi + c);
+            ak(x, 32 * bi + r, 32 * bj + c) = -sacc;
+        }
+        __syncthreads();
+    }
+    // ---- write X (lower; the upper triangle is zero) ----
+    for (int e = tid; e < q * q; e += KT) {
+        const int r = e % q, c = e / q;
+        const float v = (r >= c) ? ak(x, r, c) : 0.f;
+        if (!isfinite(v)) atomicOr(status, ST_NONFINITE);
+        dst[e] = v;
+    }
+}
+
 }  // namespace
 
 void launch_core_ada32(cudaStream_t st, int q, const double *M, const double *N, float *Cinv, float *Dinv,
                        int *status)
 {
+    if (q <= 128) {
+        static bool fattr = false;
+        const size_t fsm = sizeof(float) * (2 * 128 * LDK);
+        if (!fattr) {
+            cudaFuncSetAttribute(k_core_blk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
+            fattr = true;
+        }
+        rb_count_launch();
+        k_core_blk<<<(N && Dinv) ? 2 : 1, KT, fsm, st>>>(q, M, N, Cinv, Dinv, status);
+        return;
+    }
     const int QP = ((q + 31) / 32) * 32;
     const size_t smem = sizeof(float) * (2 * QP * QP + QP * QP / 4 + 32);
     static bool attr = false;

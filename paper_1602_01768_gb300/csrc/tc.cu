@@ -1,20 +1,24 @@
 // tc.cu -- tcgen05 / TMA GEMM for sm_103a (see tc.cuh for the contract).
 //
-// One CTA computes a 128 x BN tile of C over a range of K (split-K partials
-// are summed afterwards in a fixed order, so results are deterministic).
-// Warp roles, 256 threads:
+// Work is cut into units of one 128 x 32 k-block of one 128 x BN output tile.
+// When the output has fewer tiles than the GPU has SMs the launch is
+// stream-K: one CTA per SM, each taking an equal contiguous run of units in
+// (tile, k-block) order; every piece of a tile that a CTA covers (a segment)
+// is written as a partial tile and the pieces are summed afterwards in CTA
+// order, so results are deterministic.  Otherwise each CTA owns one tile.
+// Warp roles, 384 threads:
 //   warp 0      TMA producer: streams 128 x 32 tiles of op(A) and BN x 32
 //               tiles of B (and of B's lo part) with 128-byte swizzle into a
 //               STAGES-deep ring;
 //   warp 1      allocates TMEM and issues tcgen05.mma kind::tf32 from one
 //               elected thread, B from shared memory (K-major);
-//   warps 4-7   for 3-term products or an M-contiguous op(A): each thread
-//               takes one row of the landed A tile and writes it to TMEM as
-//               hi = x (the MMA keeps the top 11 significand bits) and
-//               lo = x - hi, so the MMA reads A from TMEM; for single-pass
-//               K-contiguous A the MMA reads the tile from shared memory.
-//               After the last stage they drain the accumulator with
-//               tcgen05.ld and apply alpha/beta.
+//   warps 4-7   converter: each thread takes one row of the landed A tile and
+//               writes to TMEM what the MMA reads from there: lo = x - hi(x)
+//               for 3-term products (hi = x itself: the MMA keeps the top 11
+//               significand bits) and, for an M-contiguous op(A), hi too; a
+//               K-contiguous hi is read from shared memory directly;
+//   warps 8-11  drain the chunk accumulators (tcgen05.ld), keep the running
+//               sums and write the output or stream-K partial tiles.
 // Every mbarrier wait is bounded (about two seconds of SM clock); a wait
 // that gives up records ST_TIMEOUT in the caller's status word and the CTA
 // winds down instead of hanging.
@@ -33,13 +37,18 @@ using namespace tcx;
 
 template <int BN, int TERMS, int AMN>
 struct Cfg {
-    static constexpr bool CONVERT = (TERMS == 3) || AMN;  // A goes through the converter warps into TMEM
+    // The A tile lands in shared memory by TMA.  A K-contiguous tile feeds the
+    // MMA's hi products from there; the converter warps write what the MMA
+    // cannot read from shared memory into TMEM: the lo part (3 terms) and, for
+    // an M-contiguous tile, the hi part as well (transposed to lanes = rows).
+    static constexpr bool HI_TMEM = AMN != 0;
+    static constexpr bool LO_TMEM = TERMS == 3;
+    static constexpr bool CONVERT = HI_TMEM || LO_TMEM;
+    static constexpr int LO_OFF = HI_TMEM ? 32 : 0;  // TMEM column of lo within a stage
     static constexpr int A_BYTES = A_TILE_BYTES;
     static constexpr int B_BYTES = BN * BK * 4;
-    // smem stage: [A tile | B | B lo (3 terms)]; with CONVERT the A tile is the raw
-    // TMA tile (K- or M-contiguous) that the converter moves into TMEM.
-    static constexpr int STAGE_BYTES = A_BYTES + B_BYTES * (TERMS == 3 ? 2 : 1);
-    static constexpr int A_TMEM_COLS = (TERMS == 3) ? 64 : 32;  // per stage: hi (32 cols) [+ lo (32 cols)]
+    static constexpr int STAGE_BYTES = A_BYTES + B_BYTES * (TERMS == 3 ? 2 : 1);  // [A | B | B lo]
+    static constexpr int A_TMEM_COLS = 32 * ((HI_TMEM ? 1 : 0) + (LO_TMEM ? 1 : 0));
     // TMEM: two chunk accumulators (2 BN columns), then the A stages
     static constexpr int STAGES_SMEM = (200 * 1024) / STAGE_BYTES;
     static constexpr int STAGES_TMEM = CONVERT ? (512 - 2 * BN) / A_TMEM_COLS : 8;
@@ -65,16 +74,14 @@ __global__ void k_split_lo(int rows, int cols, const float *X, int64_t ldx, floa
     }
 }
 
-// 32 lanes x 32 columns of 32-bit values from registers into TMEM.
-__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32])
+// 32 lanes x 16 columns of 32-bit values from registers into TMEM.
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16])
 {
     asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-        "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr),
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16};" ::"r"(taddr),
         "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
-        "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]),
-        "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]),
-        "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+        "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
         : "memory");
 }
 
@@ -90,35 +97,40 @@ __device__ __forceinline__ void mma_tf32_ts(uint32_t d_tmem, uint32_t a_tmem, ui
         : "memory");
 }
 
-// Row m of the stage's raw A tile as 32 FP32 values.  K-contiguous tile: row m
-// is 128 bytes with 16-byte chunk j stored at chunk j ^ (m & 7).
-// M-contiguous tile: four 32-row boxes 4 KB apart; element (m, k) in 16-byte
-// chunk ((m & 31) / 4) ^ (k & 7) of the box's K-row k.
+// Half h (K columns 16h .. 16h + 15) of row m of the stage's raw A tile.
+// K-contiguous tile: row m is 128 bytes with 16-byte chunk j stored at chunk
+// j ^ (m & 7).  M-contiguous tile: four 32-row boxes 4 KB apart; element
+// (m, k) in 16-byte chunk ((m & 31) / 4) ^ (k & 7) of the box's K-row k.
 template <int AMN>
-__device__ __forceinline__ void load_a_row(const unsigned char *raw, int m, float (&v)[32])
+__device__ __forceinline__ void load_a_half(const unsigned char *raw, int m, int h, float (&v)[16])
 {
     if (AMN) {
         const int mi = m & 31;
         const unsigned char *src = raw + (m >> 5) * 4096 + ((mi & 3) << 2);
 #pragma unroll
-        for (int k = 0; k < 32; ++k) v[k] = *(const float *)(src + k * 128 + (((mi >> 2) ^ (k & 7)) << 4));
+        for (int kk = 0; kk < 16; ++kk) {
+            const int k = 16 * h + kk;
+            v[kk] = *(const float *)(src + k * 128 + (((mi >> 2) ^ (k & 7)) << 4));
+        }
     } else {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
+        for (int jj = 0; jj < 4; ++jj) {
+            const int j = 4 * h + jj;
             const float4 f = *(const float4 *)(raw + m * 128 + ((j ^ (m & 7)) << 4));
-            v[4 * j] = f.x;
-            v[4 * j + 1] = f.y;
-            v[4 * j + 2] = f.z;
-            v[4 * j + 3] = f.w;
+            v[4 * jj] = f.x;
+            v[4 * jj + 1] = f.y;
+            v[4 * jj + 2] = f.z;
+            v[4 * jj + 3] = f.w;
         }
     }
 }
 
 template <int BN, int TERMS, int AMN>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(384, 1)
 k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-          const __grid_constant__ CUtensorMap tmBlo, int M, int N, int nkb, int kb_per_split, float alpha, float beta,
-          const float *Cin, int64_t ldcin, float *C, int64_t ldc, float *part, const int *status, int *err)
+          const __grid_constant__ CUtensorMap tmBlo, int M, int N, int mt, int nkb, long long U, int maxseg,
+          float alpha, float beta, const float *Cin, int64_t ldcin, float *C, int64_t ldc, float *part,
+          const int *status, int *err)
 {
     using CF = Cfg<BN, TERMS, AMN>;
     constexpr int STAGES = CF::STAGES;
@@ -137,10 +149,13 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int m0 = blockIdx.x * BM;
-    const int n0 = blockIdx.y * BN;
-    const int kb0 = blockIdx.z * kb_per_split;
-    const int nk = min(nkb - kb0, kb_per_split);
+    // This CTA's units [u_b, u_e): unit u is k-block u % nkb of tile u / nkb;
+    // tile t covers rows (t % mt) BM and columns (t / mt) BN.  A segment is the
+    // run of this CTA's units inside one tile; a chunk is at most CHUNK_KB
+    // units of a segment, counted from the segment start.
+    const int u_b = (int)(U * blockIdx.x / gridDim.x), u_e = (int)(U * (blockIdx.x + 1) / gridDim.x);
+    const int nk = u_e - u_b;
+    const int t_b = u_b / nkb, kb_b = u_b - t_b * nkb;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
@@ -170,17 +185,17 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     auto stage_b = [&](int s) { return smem + s * CF::STAGE_BYTES + CF::A_BYTES; };
     auto stage_blo = [&](int s) { return smem + s * CF::STAGE_BYTES + CF::A_BYTES + CF::B_BYTES; };
     auto a_col = [&](int s) { return (uint32_t)(2 * BN + s * CF::A_TMEM_COLS); };
-    const int nchunks = (nk + CHUNK_KB - 1) / CHUNK_KB;
 
     if (warp == 0) {
-        // ---------------- TMA producer ----------------
+        // ---------------- TMA producer (warp 0) ----------------
         if (lane == 0) {
+            int t = t_b, kb = kb_b, m0 = (t % mt) * BM, n0 = (t / mt) * BN;
             for (int i = 0; i < nk; ++i) {
                 const int s = i % STAGES;
                 if (i >= STAGES && !mbar_wait(smem_u32(&empty[s]), ((i / STAGES) - 1) & 1, err, abort_flag)) break;
                 const uint32_t fb = smem_u32(&full[s]);
                 mbar_expect_tx(fb, CF::STAGE_BYTES);
-                const int k = (kb0 + i) * BK;
+                const int k = kb * BK;
                 if (AMN) {
 #pragma unroll
                     for (int c = 0; c < BM / 32; ++c)
@@ -190,128 +205,152 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                 }
                 tma_load_2d(smem_u32(stage_b(s)), &tmB, k, n0, fb);
                 if (TERMS == 3) tma_load_2d(smem_u32(stage_blo(s)), &tmBlo, k, n0, fb);  // B lo, split once per call
+                if (++kb == nkb) {
+                    kb = 0;
+                    ++t;
+                    m0 = (t % mt) * BM;
+                    n0 = (t / mt) * BN;
+                }
             }
         }
     } else if (warp == 1) {
-        // ---------------- MMA issuer ----------------
+        // ---------------- MMA issuer (warp 1) ----------------
         if (lane == 0) {
             const uint32_t idesc = idesc_tf32(BN, 0);
-            bool ok = true;
-            for (int i = 0; i < nk && ok; ++i) {
+            int c = -1;           // chunk being accumulated
+            int kb = kb_b, p = 0;  // k-block in the tile, position in the segment
+            for (int i = 0; i < nk; ++i) {
                 const int s = i % STAGES;
-                const int c = i / CHUNK_KB, b = c & 1, ic = i % CHUNK_KB;
-                if (ic == 0 && c >= 2 &&
-                    !mbar_wait(smem_u32(&chunk_free[b]), ((c >> 1) - 1) & 1, err, abort_flag)) {
-                    ok = false;
+                const bool cstart = (p % CHUNK_KB) == 0;
+                const bool cend = ((p + 1) % CHUNK_KB) == 0 || kb + 1 == nkb || i + 1 == nk;
+                if (cstart) ++c;
+                const int b = c & 1;
+                if (cstart && c >= 2 && !mbar_wait(smem_u32(&chunk_free[b]), ((c >> 1) - 1) & 1, err, abort_flag))
                     break;
-                }
                 const uint32_t wb = CF::CONVERT ? smem_u32(&conv[s]) : smem_u32(&full[s]);
-                if (!mbar_wait(wb, (i / STAGES) & 1, err, abort_flag)) {
-                    ok = false;
-                    break;
-                }
+                if (!mbar_wait(wb, (i / STAGES) & 1, err, abort_flag)) break;
                 tc_fence_after();
                 const uint32_t dacc = tmem + (uint32_t)(b * BN);
-                const uint32_t b_hi = smem_u32(stage_b(s)), b_lo = smem_u32(stage_blo(s));
+                const uint32_t a_s = smem_u32(stage_a(s)), b_hi = smem_u32(stage_b(s)), b_lo = smem_u32(stage_blo(s));
+                const uint32_t ta = tmem + a_col(s);
 #pragma unroll
                 for (int kk = 0; kk < BK / 8; ++kk) {
-                    // K = 8 TF32 per MMA: 32 bytes along B's 128-byte swizzle row, 8 TMEM columns of A
+                    // K = 8 TF32 per MMA: 32 bytes along a 128-byte swizzle row, 8 TMEM columns
                     const uint64_t db_hi = umma_desc(b_hi + kk * 32, 16, 1024);
-                    const uint32_t first = (ic == 0 && kk == 0) ? 0u : 1u;  // each chunk starts a fresh sum
-                    if (CF::CONVERT) {
-                        const uint32_t ta_hi = tmem + a_col(s) + 8 * kk;
-                        if (TERMS == 3) {
-                            const uint64_t db_lo = umma_desc(b_lo + kk * 32, 16, 1024);
-                            mma_tf32_ts(dacc, ta_hi + 32, db_hi, idesc, first);  // lo x hi
-                            mma_tf32_ts(dacc, ta_hi, db_lo, idesc, 1u);          // hi x lo
-                            mma_tf32_ts(dacc, ta_hi, db_hi, idesc, 1u);          // hi x hi
-                        } else {
-                            mma_tf32_ts(dacc, ta_hi, db_hi, idesc, first);
-                        }
+                    const uint32_t first = (cstart && kk == 0) ? 0u : 1u;  // each chunk starts a fresh sum
+                    auto mma_hi = [&](uint64_t db, uint32_t accum) {       // A hi x db
+                        if (CF::HI_TMEM)
+                            mma_tf32_ts(dacc, ta + 8 * kk, db, idesc, accum);
+                        else
+                            mma_tf32(dacc, umma_desc(a_s + kk * 32, 16, 1024), db, idesc, accum);
+                    };
+                    if (TERMS == 3) {
+                        mma_tf32_ts(dacc, ta + CF::LO_OFF + 8 * kk, db_hi, idesc, first);  // lo x hi
+                        mma_hi(umma_desc(b_lo + kk * 32, 16, 1024), 1u);                  // hi x lo
+                        mma_hi(db_hi, 1u);                                                 // hi x hi
                     } else {
-                        const uint64_t da = umma_desc(smem_u32(stage_a(s)) + kk * 32, 16, 1024);
-                        mma_tf32(dacc, da, db_hi, idesc, first);
+                        mma_hi(db_hi, first);
                     }
                 }
                 mma_commit(smem_u32(&empty[s]));
-                if (ic == CHUNK_KB - 1 || i == nk - 1) mma_commit(smem_u32(&chunk_full[b]));
+                if (cend) mma_commit(smem_u32(&chunk_full[b]));
+                ++p;
+                if (++kb == nkb) {
+                    kb = 0;
+                    p = 0;
+                }
             }
         }
-    } else if (warp >= 4) {
-        const int t = threadIdx.x - 128;  // 0..127 = tile row = TMEM lane
-        const int wq = warp & 3;          // this warp's TMEM lane quarter
-        // Running sum of the finished K chunks, one tile row per thread, added on
-        // the CUDA cores with round-to-nearest.  The tensor core's FP32 accumulation
-        // drifts toward zero over long K (about one truncation per MMA step, relative
-        // to the growing sum); restarting it every CHUNK_KB k-blocks bounds that drift.
-        float run[BN];
-#pragma unroll
-        for (int j = 0; j < BN; ++j) run[j] = 0.f;
-        int drained = 0;
-        bool ok = true;
-        auto drain = [&](int c) {
-            const int b = c & 1;
-            if (!mbar_wait(smem_u32(&chunk_full[b]), (c >> 1) & 1, err, abort_flag)) {
-                ok = false;
-                return;
-            }
-            tc_fence_after();
-#pragma unroll
-            for (int c0 = 0; c0 < BN; c0 += 16) {
-                uint32_t r[16];
-                tmem_ld16(tmem + ((uint32_t)(32 * wq) << 16) + (uint32_t)(b * BN + c0), r);
-#pragma unroll
-                for (int j = 0; j < 16; ++j) run[c0 + j] += __uint_as_float(r[j]);
-            }
-            tc_fence_before();
-            mbar_arrive(smem_u32(&chunk_free[b]));
-        };
-        // ---------------- A operand into TMEM (hi = x, lo = x - hi(x)) ----------------
+    } else if (warp >= 4 && warp < 8) {
+        // ---------------- converter (warps 4-7): A lo [and hi] into TMEM ----------------
         if (CF::CONVERT) {
-            for (int i = 0; i < nk && ok; ++i) {
+            const int r = threadIdx.x - 128;  // tile row = TMEM lane
+            const uint32_t lane_base = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+            for (int i = 0; i < nk; ++i) {
                 const int s = i % STAGES;
-                if (!mbar_wait(smem_u32(&full[s]), (i / STAGES) & 1, err, abort_flag)) {
-                    ok = false;
-                    break;
-                }
-                float v[32];
-                load_a_row<AMN>(stage_a(s), t, v);
-                uint32_t r[32];
-                const uint32_t taddr = tmem + ((uint32_t)(32 * wq) << 16) + a_col(s);
+                if (!mbar_wait(smem_u32(&full[s]), (i / STAGES) & 1, err, abort_flag)) break;
+                const uint32_t taddr = lane_base + a_col(s);
 #pragma unroll
-                for (int k = 0; k < 32; ++k) r[k] = __float_as_uint(v[k]);
-                tmem_st32(taddr, r);
-                if (TERMS == 3) {
+                for (int h = 0; h < 2; ++h) {
+                    float v[16];
+                    load_a_half<AMN>(stage_a(s), r, h, v);
+                    uint32_t w[16];
+                    if (CF::HI_TMEM) {
 #pragma unroll
-                    for (int k = 0; k < 32; ++k) r[k] = __float_as_uint(v[k] - tf32_hi(v[k]));
-                    tmem_st32(taddr + 32, r);
+                        for (int k = 0; k < 16; ++k) w[k] = __float_as_uint(v[k]);
+                        tmem_st16(taddr + 16 * h, w);
+                    }
+                    if (CF::LO_TMEM) {
+#pragma unroll
+                        for (int k = 0; k < 16; ++k) w[k] = __float_as_uint(v[k] - tf32_hi(v[k]));
+                        tmem_st16(taddr + CF::LO_OFF + 16 * h, w);
+                    }
                 }
                 asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 tc_fence_before();
                 mbar_arrive(smem_u32(&conv[s]));
-                // chunk c - 2 is drained once chunk c - 1 is fully converted, before the
-                // first conversion of chunk c (whose MMA needs that accumulator)
-                if ((i + 1) % CHUNK_KB == 0 && (i + 1) / CHUNK_KB >= 2) drain(drained++);
             }
         }
-        while (ok && drained < nchunks) drain(drained++);
-        // ---------------- epilogue ----------------
-        if (ok) {
-            const int m = m0 + 32 * wq + lane;
-            const bool split = (part != nullptr);
-            if (m < M) {
+    } else if (warp >= 8) {
+        // ---------------- drain and epilogue (warps 8-11) ----------------
+        // Running sum of the finished K chunks, one tile row per thread, added on
+        // the CUDA cores with round-to-nearest.  The tensor core's FP32 accumulation
+        // drifts toward zero over long K (about one truncation per MMA step, relative
+        // to the growing sum); restarting it every CHUNK_KB k-blocks bounds that drift.
+        const int wq = warp & 3;  // this warp's TMEM lane quarter
+        float run[BN];
 #pragma unroll
-                for (int j = 0; j < BN; ++j) {
-                    const int nn = n0 + j;
-                    if (nn < N) {
-                        if (split) {
-                            part[(size_t)blockIdx.z * M * N + m + (size_t)nn * M] = run[j];
-                        } else {
-                            float o = alpha * run[j];
-                            if (beta != 0.f) o = fmaf(beta, Cin[m + (int64_t)nn * ldcin], o);
-                            C[m + (int64_t)nn * ldc] = o;
+        for (int j = 0; j < BN; ++j) run[j] = 0.f;
+        int u = u_b, t = t_b, kb = kb_b, c = 0;
+        bool fresh = true;  // next chunk starts a segment
+        while (u < u_e) {
+            const int len = min(CHUNK_KB, min(nkb - kb, u_e - u));
+            const int b = c & 1;
+            if (!mbar_wait(smem_u32(&chunk_full[b]), (c >> 1) & 1, err, abort_flag)) break;
+            tc_fence_after();
+            // the first chunk of a segment starts the sum: clear the running value by mask
+            const uint32_t keep = fresh ? 0u : 0xFFFFFFFFu;
+#pragma unroll
+            for (int c0 = 0; c0 < BN; c0 += 16) {
+                uint32_t rr[16];
+                tmem_ld16(tmem + ((uint32_t)(32 * wq) << 16) + (uint32_t)(b * BN + c0), rr);
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    run[c0 + j] = __uint_as_float(__float_as_uint(run[c0 + j]) & keep) + __uint_as_float(rr[j]);
+            }
+            tc_fence_before();
+            mbar_arrive(smem_u32(&chunk_free[b]));
+            u += len;
+            kb += len;
+            ++c;
+            fresh = (kb == nkb || u == u_e);
+            if (fresh) {
+                // segment finished: the whole tile (write C) or a partial tile in
+                // slot (CTA, segment index) of the workspace
+                if (part == nullptr) {
+                    const int m = (t % mt) * BM + 32 * wq + lane, n0 = (t / mt) * BN;
+                    if (m < M) {
+                        float *cp = C + m + (int64_t)n0 * ldc;
+                        const float *ci = Cin + m + (int64_t)n0 * ldcin;
+#pragma unroll
+                        for (int j = 0; j < BN; ++j) {
+                            if (n0 + j < N) {
+                                float o = alpha * run[j];
+                                if (beta != 0.f) o = fmaf(beta, *ci, o);
+                                *cp = o;
+                            }
+                            cp += ldc;
+                            ci += ldcin;
                         }
                     }
+                } else {
+                    float *dst = part + ((size_t)blockIdx.x * maxseg + (t - t_b)) * (BM * BN) + 32 * wq + lane;
+#pragma unroll
+                    for (int j = 0; j < BN; ++j) dst[j * BM] = run[j];
+                }
+                if (kb == nkb) {
+                    kb = 0;
+                    ++t;
                 }
             }
         }
@@ -326,18 +365,40 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     }
 }
 
-// C = alpha sum_z part[z] + beta Cin, fixed order over z.
-__global__ void k_splitk_reduce(int M, int N, int splits, const float *part, float alpha, float beta,
-                                const float *Cin, int64_t ldcin, float *C, int64_t ldc)
+// Stream-K fix-up: C = alpha (sum of the partial tiles of every CTA whose
+// units overlap the tile, in CTA order) + beta Cin.  Block (tile, 32-column
+// group), thread = tile row.
+__global__ void k_streamk_reduce(int M, int N, int mt, int bn, int nkb, long long U, int G, int maxseg,
+                                 const float *part, float alpha, float beta, const float *Cin, int64_t ldcin,
+                                 float *C, int64_t ldc, const int *status)
 {
-    const int m = blockIdx.x * blockDim.x + threadIdx.x;
-    const int nn = blockIdx.y;
+    if (status_bad(status)) return;
+    const int t = blockIdx.x, r = threadIdx.x, j0 = blockIdx.y * 32;
+    const int m = (t % mt) * BM + r, n0 = (t / mt) * bn + j0;
+    const long long t0 = (long long)t * nkb, t1 = t0 + nkb;
+    int b = (int)(t0 * G / U);  // first CTA whose units reach into the tile
+    while (b + 1 < G && U * (b + 1) / G <= t0) ++b;
+    float s[32];
+#pragma unroll
+    for (int jj = 0; jj < 32; ++jj) s[jj] = 0.f;
+    for (; b < G; ++b) {
+        const long long u0 = U * b / G, u1 = U * (b + 1) / G;
+        if (u0 >= t1) break;
+        if (u1 == u0) continue;  // a CTA without units
+        const float *pp = part + ((size_t)b * maxseg + (size_t)(t - u0 / nkb)) * (BM * bn) + r + (size_t)j0 * BM;
+#pragma unroll
+        for (int jj = 0; jj < 32; ++jj) s[jj] += pp[(size_t)jj * BM];
+    }
     if (m >= M) return;
-    float s = 0.f;
-    for (int z = 0; z < splits; ++z) s += part[(size_t)z * M * N + m + (size_t)nn * M];
-    float o = alpha * s;
-    if (beta != 0.f) o = fmaf(beta, Cin[m + (int64_t)nn * ldcin], o);
-    C[m + (int64_t)nn * ldc] = o;
+#pragma unroll
+    for (int jj = 0; jj < 32; ++jj) {
+        const int nn = n0 + jj;
+        if (nn < N) {
+            float o = alpha * s[jj];
+            if (beta != 0.f) o = fmaf(beta, Cin[m + (int64_t)nn * ldcin], o);
+            C[m + (int64_t)nn * ldc] = o;
+        }
+    }
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
@@ -453,7 +514,7 @@ template <int BN, int TERMS, int AMN>
 static int launch_bn(tc_plan *p, cudaStream_t st, const CUtensorMap &ma, const CUtensorMap &mb,
                      const CUtensorMap &mblo, int M, int N, int K,
                      float alpha, float beta, const float *Cin, int64_t ldcin, float *C, int64_t ldc,
-                     const int *status, int *err)
+                     const int *status, int *err, int reserve)
 {
     using CF = Cfg<BN, TERMS, AMN>;
     static bool attr = false;
@@ -466,13 +527,20 @@ static int launch_bn(tc_plan *p, cudaStream_t st, const CUtensorMap &ma, const C
     const int mt = (M + BM - 1) / BM, nt = (N + BN - 1) / BN;
     const int nkb = (K + BK - 1) / BK;
     const int tiles = mt * nt;
-    int splits = 1;
-    if (tiles < g_num_sms) splits = std::max(1, std::min(g_num_sms / tiles, nkb / 4));
-    const int kbps = (nkb + splits - 1) / splits;
-    splits = (nkb + kbps - 1) / kbps;
+    const long long U = (long long)tiles * nkb;
+    // stream-K when the tiles alone leave SMs idle and each SM still gets a few
+    // k-blocks; `reserve` SMs are left free for work on other streams
+    const int sms = std::max(1, g_num_sms - std::max(0, reserve));
+    const bool streamk = tiles < sms && U >= 4LL * sms;
+    const int G = streamk ? sms : tiles;
+    int maxseg = 1;
     float *part = nullptr;
-    if (splits > 1) {
-        const size_t need = (size_t)splits * M * N;
+    if (streamk) {
+        for (int b = 0; b < G; ++b) {
+            const long long u0 = U * b / G, u1 = U * (b + 1) / G;
+            if (u1 > u0) maxseg = std::max(maxseg, (int)((u1 - 1) / nkb - u0 / nkb + 1));
+        }
+        const size_t need = (size_t)G * maxseg * BM * BN;
         if (need > p->part_cap) {
             if (p->part) cudaFree(p->part);
             p->part = nullptr;
@@ -482,14 +550,13 @@ static int launch_bn(tc_plan *p, cudaStream_t st, const CUtensorMap &ma, const C
         }
         part = p->part;
     }
-    dim3 grid(mt, nt, splits);
     rb_count_launch();
-    k_tc_gemm<BN, TERMS, AMN><<<grid, 256, CF::SMEM, st>>>(ma, mb, mblo, M, N, nkb, kbps, alpha, beta, Cin, ldcin, C, ldc,
-                                                           part, status, err);
-    if (splits > 1) {
-        dim3 g2((M + 255) / 256, N);
+    k_tc_gemm<BN, TERMS, AMN><<<G, 384, CF::SMEM, st>>>(ma, mb, mblo, M, N, mt, nkb, U, maxseg, alpha, beta, Cin,
+                                                        ldcin, C, ldc, part, status, err);
+    if (streamk) {
         rb_count_launch();
-        k_splitk_reduce<<<g2, 256, 0, st>>>(M, N, splits, part, alpha, beta, Cin, ldcin, C, ldc);
+        k_streamk_reduce<<<dim3(tiles, BN / 32), BM, 0, st>>>(M, N, mt, BN, nkb, U, G, maxseg, part, alpha, beta, Cin,
+                                                              ldcin, C, ldc, status);
     }
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
@@ -497,7 +564,7 @@ static int launch_bn(tc_plan *p, cudaStream_t st, const CUtensorMap &ma, const C
 template <int TERMS>
 static int launch_terms(tc_plan *p, cudaStream_t st, int a_layout, int M, int N, int K, float alpha, const float *A,
                         int64_t lda, const float *B, int64_t ldb, float beta, const float *Cin, int64_t ldcin,
-                        float *C, int64_t ldc, const int *status, int *err)
+                        float *C, int64_t ldc, const int *status, int *err, int reserve)
 {
     const int a_mn = (a_layout == TC_A_MN);
     const int bn = N <= 32 ? 32 : N <= 64 ? 64 : 128;
@@ -525,9 +592,9 @@ static int launch_terms(tc_plan *p, cudaStream_t st, int a_layout, int M, int N,
 #define RB_TC_CASE(BNV)                                                                                     \
     case BNV:                                                                                                  \
         return a_mn ? launch_bn<BNV, TERMS, 1>(p, st, ma, mb, mblo, M, N, K, alpha, beta, Cin, ldcin, C, ldc, status, \
-                                               err)                                                             \
+                                               err, reserve)                                                    \
                     : launch_bn<BNV, TERMS, 0>(p, st, ma, mb, mblo, M, N, K, alpha, beta, Cin, ldcin, C, ldc, status, \
-                                               err);
+                                               err, reserve);
     switch (bn) {
         RB_TC_CASE(32)
         RB_TC_CASE(64)
@@ -541,7 +608,7 @@ static bool tma_ok(const void *ptr, int64_t ld) { return ((uintptr_t)ptr % 16 ==
 
 static int tc_run(tc_plan *p, cudaStream_t st, int terms, int a_layout, int M, int N, int K, float alpha,
                   const float *A, int64_t lda, const float *B, int64_t ldb, float beta, const float *Cin,
-                  int64_t ldcin, float *C, int64_t ldc, const int *status)
+                  int64_t ldcin, float *C, int64_t ldc, const int *status, int reserve = 0)
 {
     if (M <= 0 || N <= 0) return 0;
     const bool ok = p && K > 0 && tma_ok(A, lda) && tma_ok(B, ldb);
@@ -554,8 +621,10 @@ static int tc_run(tc_plan *p, cudaStream_t st, int terms, int a_layout, int M, i
     int *err = status ? const_cast<int *>(status) : p->err;
     const int rc =
         (terms == 3)
-            ? launch_terms<3>(p, st, a_layout, M, N, K, alpha, A, lda, B, ldb, beta, Cin, ldcin, C, ldc, status, err)
-            : launch_terms<1>(p, st, a_layout, M, N, K, alpha, A, lda, B, ldb, beta, Cin, ldcin, C, ldc, status, err);
+            ? launch_terms<3>(p, st, a_layout, M, N, K, alpha, A, lda, B, ldb, beta, Cin, ldcin, C, ldc, status, err,
+                              reserve)
+            : launch_terms<1>(p, st, a_layout, M, N, K, alpha, A, lda, B, ldb, beta, Cin, ldcin, C, ldc, status, err,
+                              reserve);
     if (rc == 0) return 0;
     // the tensor-core launch could not be set up (tensor map or workspace): run the same product on CUDA cores
     if (beta != 0.f && Cin != C) launch_copy2d<float, float>(st, M, N, Cin, ldcin, C, ldc, 1.0);
@@ -564,9 +633,9 @@ static int tc_run(tc_plan *p, cudaStream_t st, int terms, int a_layout, int M, i
 }
 
 int tc_gemm_nk(tc_plan *p, cudaStream_t st, int terms, int a_layout, int M, int N, int K, const float *A, int64_t lda,
-               const float *B, int64_t ldb, float *C, int64_t ldc, const int *status)
+               const float *B, int64_t ldb, float *C, int64_t ldc, const int *status, int reserve_sms)
 {
-    return tc_run(p, st, terms, a_layout, M, N, K, 1.f, A, lda, B, ldb, 0.f, nullptr, 0, C, ldc, status);
+    return tc_run(p, st, terms, a_layout, M, N, K, 1.f, A, lda, B, ldb, 0.f, nullptr, 0, C, ldc, status, reserve_sms);
 }
 
 int tc_gemm_nk_axpby(tc_plan *p, cudaStream_t st, int terms, int a_layout, int M, int N, int K, float alpha,

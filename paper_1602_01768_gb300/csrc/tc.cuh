@@ -22,8 +22,11 @@ void tc_plan_destroy(tc_plan *p);
 
 // Returns 0 when launched on the tensor cores, 1 when it fell back to the
 // SIMT kernel (shape or alignment outside what TMA accepts), <0 on error.
+// A stream-K launch (fewer output tiles than SMs) uses all SMs but
+// reserve_sms, which stay free for kernels on other streams.
 int tc_gemm_nk(tc_plan *p, cudaStream_t st, int terms, int a_layout, int M, int N, int K, const float *A,
-               int64_t lda, const float *B, int64_t ldb, float *C, int64_t ldc, const int *status);
+               int64_t lda, const float *B, int64_t ldb, float *C, int64_t ldc, const int *status,
+               int reserve_sms = 0);
 int tc_gemm_nk_axpby(tc_plan *p, cudaStream_t st, int terms, int a_layout, int M, int N, int K, float alpha,
                      const float *A, int64_t lda, const float *B, int64_t ldb, float beta, const float *Cin,
                      int64_t ldcin, float *C, int64_t ldc);
