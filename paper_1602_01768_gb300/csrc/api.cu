@@ -25,7 +25,10 @@ struct rb_ctx {
 
     // n x q panels (ld n) and q x n panels (ld q)
     void *St = nullptr, *S = nullptr, *G = nullptr, *Y = nullptr, *Sh = nullptr;
-    void *W = nullptr, *V = nullptr;
+    void *W = nullptr, *V = nullptr;  // W shares St's allocation (see alloc_sketch_workspace)
+    float *Bv = nullptr, *Bs = nullptr;  // tensor-core V and S^: [D^-T; -C^-T] (2q x q) and C^-T (q x q)
+    float *Mf = nullptr, *Nf = nullptr;  // FP32 Gram products S^T A S and S~^T S~ (tensor-core path)
+    tc_plan *tc2 = nullptr;              // plan (own workspace) for the side stream's tensor-core GEMMs
     void *P3 = nullptr;  // RBFGS: [S | W | S], n x 3q
     void *Cinv = nullptr, *Dinv = nullptr, *Lam = nullptr, *B1 = nullptr;  // q x q
     double *part = nullptr, *M = nullptr, *N = nullptr, *Tm = nullptr;
@@ -129,9 +132,16 @@ extern "C" const char *rbfgs_status_string(int s)
 static void destroy_ctx(rb_ctx *h)
 {
     if (!h) return;
-    void **bufs[] = {&h->A, &h->X, &h->X2, &h->X3, &h->St, &h->S, &h->G, &h->Y, &h->Sh, &h->W,
+    h->W = nullptr;  // part of St's allocation
+    void **bufs[] = {&h->A, &h->X, &h->X2, &h->X3, &h->St, &h->S, &h->G, &h->Y, &h->Sh,
                      &h->V, &h->P3, &h->Cinv, &h->Dinv, &h->Lam, &h->B1, &h->R1, &h->R2, &h->R3};
     for (void **b : bufs) rb_free(*b);
+    rb_freet(h->Bv);
+    rb_freet(h->Bs);
+    rb_freet(h->Mf);
+    rb_freet(h->Nf);
+    if (h->tc2) tc_plan_destroy(h->tc2);
+    h->tc2 = nullptr;
     rb_freet(h->part);
     rb_freet(h->M);
     rb_freet(h->N);
@@ -250,12 +260,19 @@ static rb_status alloc_sketch_workspace(rb_ctx *h)
     const size_t n = h->n, q = h->q, e = h->esz;
     const size_t nq = n * q * e, qq = q * q * e;
     const int nch = ceil_div(h->n, GRAM_CHUNK);
-    RB_TRY(rb_alloc(&h->St, nq));
+    // St and W side by side: [S~ | W^T] is the n x 2q M-contiguous operand of V^T
+    RB_TRY(rb_alloc(&h->St, 2 * nq));
+    h->W = (char *)h->St + nq;
     RB_TRY(rb_alloc(&h->S, nq));
     RB_TRY(rb_alloc(&h->G, nq));
     RB_TRY(rb_alloc(&h->Y, nq));
     RB_TRY(rb_alloc(&h->Sh, nq));
-    RB_TRY(rb_alloc(&h->W, nq));
+    if (!h->f64) {
+        RB_TRY(rb_alloc(&h->Bv, 2 * q * q * sizeof(float)));
+        RB_TRY(rb_alloc(&h->Bs, q * q * sizeof(float)));
+        RB_TRY(rb_alloc(&h->Mf, q * q * sizeof(float)));
+        RB_TRY(rb_alloc(&h->Nf, q * q * sizeof(float)));
+    }
     RB_TRY(rb_alloc(&h->V, nq));
     RB_TRY(rb_alloc(&h->Cinv, qq));
     RB_TRY(rb_alloc(&h->Dinv, qq));
@@ -497,14 +514,25 @@ static void ada_step_tc(rb_ctx *h)
     const int upd = (h->prec == RB_TF32X3) ? 3 : 1;
     const int rsv = fork ? SIDE_SMS : 0;
     cudaStream_t side = fork ? h->st2 : st;
+    // V and S^ on the tensor cores: the cores write their inverses transposed
+    // straight into the B operands (needs q <= 128 and 16-byte rows)
+    bool tcv = fork && q <= 128 && q % 4 == 0 && n % 4 == 0;
+    if (tcv && !h->tc2) tcv = (h->tc2 = tc_plan_create(n, q, h->prec)) != nullptr;
+    // the side stream's Gram products run stream-K on the SIDE_SMS SMs the main GEMMs leave free
+    const int side_rsv = std::max(0, tc_num_sms() - SIDE_SMS);
     ada_draw<float>(h, St);
     mark(h, "sketch");
     tc_gemm_nk(h->tc, st, acc, TC_A_MN, n, q, n, L, n, St, n, S, n, stp);       // S = L S~   (A = L, M-contiguous)
     if (fork) {
         cudaEventRecord(h->ev_sk, st);
         cudaStreamWaitEvent(side, h->ev_sk, 0);
-        launch_gram<float>(side, n, q, q, St, n, St, n, h->part, h->N);  // S~^T S~ -> D^-1
-        launch_core_ada32(side, q, h->N, nullptr, Di, nullptr, h->d_status);
+        if (tcv) {  // S~^T S~ (3 x TF32) -> D^-T into the top of Bv
+            tc_gemm_nk(h->tc2, side, 3, TC_A_K, q, q, n, St, n, St, n, h->Nf, q, stp, side_rsv);
+            launch_core_tr32(side, q, h->Nf, nullptr, h->Bv, 2 * q, 1.f, nullptr, 0, 0.f, h->d_status);
+        } else {
+            launch_gram<float>(side, n, q, q, St, n, St, n, h->part, h->N);  // S~^T S~ -> D^-1
+            launch_core_ada32(side, q, h->N, nullptr, Di, nullptr, h->d_status);
+        }
     }
     mark(h, "S=LS~");
     tc_gemm_nk(h->tc, st, acc, TC_A_K, n, q, n, A, n, S, n, G, n, stp, rsv);  // G = A S    (A symmetric)
@@ -512,8 +540,13 @@ static void ada_step_tc(rb_ctx *h)
     if (fork) {
         cudaEventRecord(h->ev_g, st);
         cudaStreamWaitEvent(side, h->ev_g, 0);
-        launch_gram<float>(side, n, q, q, S, n, G, n, h->part, h->M);    // S^T A S -> C^-1
-        launch_core_ada32(side, q, h->M, nullptr, Ci, nullptr, h->d_status);
+        if (tcv) {  // S^T A S = S^T G (3 x TF32) -> -C^-T into the bottom of Bv, C^-T into Bs
+            tc_gemm_nk(h->tc2, side, 3, TC_A_K, q, q, n, S, n, G, n, h->Mf, q, stp, side_rsv);
+            launch_core_tr32(side, q, h->Mf, nullptr, h->Bv + q, 2 * q, -1.f, h->Bs, q, 1.f, h->d_status);
+        } else {
+            launch_gram<float>(side, n, q, q, S, n, G, n, h->part, h->M);    // S^T A S -> C^-1
+            launch_core_ada32(side, q, h->M, nullptr, Ci, nullptr, h->d_status);
+        }
         cudaEventRecord(h->ev_core, side);
     } else {
         launch_gram<float>(st, n, q, q, S, n, G, n, h->part, h->M);
@@ -528,11 +561,18 @@ static void ada_step_tc(rb_ctx *h)
     tc_gemm_nk(h->tc, st, acc, TC_A_K, n, q, n, L, n, G, n, W, n, stp, rsv);  // W^T = L^T G (n x q)
     if (fork) cudaStreamWaitEvent(st, h->ev_core, 0);                            // join: C^-1, D^-1 ready
     mark(h, fork ? "W=G^TL | C core" : "W=G^TL");
-    // V = D^-1 S~^T - C^-1 W, stored q x n (ld q); W^T is n x q (ld n)
-    gemm_simt<float>(st, false, true, q, n, q, 1.f, Di, q, St, n, 0.f, V, q, stp);
-    gemm_simt<float>(st, false, true, q, n, q, -1.f, Ci, q, W, n, 1.f, V, q, stp);
-    // S^ = S C^-T stored row-major (n x q with q contiguous) for the K-major update operand
-    gemm_simt<float>(st, false, true, q, n, q, 1.f, Ci, q, S, n, 0.f, Sh, q, stp);  // S^^T = C^-1 S^T (q x n)
+    if (tcv) {
+        // V^T = [S~ | W^T] [D^-T; -C^-T] (n x q), written transposed: V is q x n (ld q)
+        tc_gemm_nk_t(h->tc, st, acc, TC_A_MN, n, q, 2 * q, St, n, h->Bv, 2 * q, V, q, stp);
+        // S^ = S C^-T, written transposed (row-major n x q) for the K-major update operand
+        tc_gemm_nk_t(h->tc, st, upd, TC_A_MN, n, q, q, S, n, h->Bs, q, Sh, q, stp);
+    } else {
+        // V = D^-1 S~^T - C^-1 W, stored q x n (ld q); W^T is n x q (ld n)
+        gemm_simt<float>(st, false, true, q, n, q, 1.f, Di, q, St, n, 0.f, V, q, stp);
+        gemm_simt<float>(st, false, true, q, n, q, -1.f, Ci, q, W, n, 1.f, V, q, stp);
+        // S^ = S C^-T stored row-major (n x q with q contiguous) for the K-major update operand
+        gemm_simt<float>(st, false, true, q, n, q, 1.f, Ci, q, S, n, 0.f, Sh, q, stp);  // S^^T = C^-1 S^T (q x n)
+    }
     mark(h, "V, S^");
     // L += S^ V: persistent HBM-streaming kernel for the single-pass form
     if (upd != 1 || tc_update_persistent(h->tc, st, n, q, Sh, V, L, n, stp) != 0)

@@ -178,21 +178,35 @@ __global__ void __launch_bounds__(CT, 1) k_core32(int q, const double *M, const 
 //   T = sum_{k=j}^{i-1} L_ik X_kj,  X_ij = -X_ii T   (i = j + d).
 // Every phase but the diagonal block is a set of small GEMMs, so the kernel
 // needs a handful of barriers instead of one per column.
+// One matrix of a core launch: the Gram matrix it factors (FP64, q x q) and
+// where X = L^-1 goes: plainly (dst, lower, ld q) and as up to two scaled
+// transposes s X^T (xt1 / xt2 with their leading dimensions); null skips.
+struct CoreOut {
+    const double *src;
+    const float *srcf;  // FP32 Gram matrix instead of src when not null
+    float *dst;
+    float *xt1;
+    int ld1;
+    float s1;
+    float *xt2;
+    int ld2;
+    float s2;
+};
+
 constexpr int KT = 512;   // threads
 constexpr int LDK = 129;  // padded leading dimension: row and column walks are conflict-free
 
 __device__ __forceinline__ float &ak(float *m, int i, int j) { return m[i + j * LDK]; }
 
-__global__ void __launch_bounds__(KT, 1) k_core_blk(int q, const double *M, const double *N, float *Cinv,
-                                                    float *Dinv, int *status)
+__global__ void __launch_bounds__(KT, 1) k_core_blk(int q, CoreOut o0, CoreOut o1, int *status)
 {
     extern __shared__ float smk[];
     float *a = smk;               // A, overwritten by L (lower blocks)
     float *x = smk + 128 * LDK;   // X = L^-1 (lower blocks); upper blocks hold T
     __shared__ int fail;
     if (status_bad(status)) return;
-    const double *src = blockIdx.x == 0 ? M : N;
-    float *dst = blockIdx.x == 0 ? Cinv : Dinv;
+    const CoreOut &out = blockIdx.x == 0 ? o0 : o1;
+    const double *src = out.src;
     const int nb = (q + 31) / 32, QP = 32 * nb;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) fail = 0;
@@ -203,7 +217,8 @@ __global__ void __launch_bounds__(KT, 1) k_core_blk(int q, const double *M, cons
 #pragma unroll
         for (int u = 0; u < 32; ++u) {
             const int j = j0 + 4 * u;
-            v[u] = (i < q && j < q) ? (float)src[i + (size_t)j * q] : (i == j ? 1.f : 0.f);
+            v[u] = (i < q && j < q) ? (out.srcf ? out.srcf[i + (size_t)j * q] : (float)src[i + (size_t)j * q])
+                                    : (i == j ? 1.f : 0.f);
         }
 #pragma unroll
         for (int u = 0; u < 32; ++u) ak(a, i, j0 + 4 * u) = v[u];
@@ -325,29 +340,48 @@ __global__ void __launch_bounds__(KT, 1) k_core_blk(int q, const double *M, cons
         }
         __syncthreads();
     }
-    // ---- write X (lower; the upper triangle is zero) ----
+    // ---- write X (lower; the upper triangle is zero) and the scaled transposes ----
     for (int e = tid; e < q * q; e += KT) {
         const int r = e % q, c = e / q;
         const float v = (r >= c) ? ak(x, r, c) : 0.f;
         if (!isfinite(v)) atomicOr(status, ST_NONFINITE);
-        dst[e] = v;
+        if (out.dst) out.dst[e] = v;
+        // transposes walk r fastest over their own columns: entry (c, r) of X^T is X(r, c)
+        const float w = (c >= r) ? ak(x, c, r) : 0.f;  // X(c, r) = X^T(r, c)
+        if (out.xt1) out.xt1[r + (size_t)c * out.ld1] = out.s1 * w;
+        if (out.xt2) out.xt2[r + (size_t)c * out.ld2] = out.s2 * w;
     }
 }
 
+void launch_core_blk(cudaStream_t st, int q, const CoreOut &o0, const CoreOut *o1, int *status)
+{
+    static bool fattr = false;
+    const size_t fsm = sizeof(float) * (2 * 128 * LDK);
+    if (!fattr) {
+        cudaFuncSetAttribute(k_core_blk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
+        fattr = true;
+    }
+    rb_count_launch();
+    k_core_blk<<<o1 ? 2 : 1, KT, fsm, st>>>(q, o0, o1 ? *o1 : o0, status);
+}
+
 }  // namespace
+
+bool launch_core_tr32(cudaStream_t st, int q, const float *M, float *Xinv, float *xt1, int ld1, float s1,
+                      float *xt2, int ld2, float s2, int *status)
+{
+    if (q > 128) return false;
+    launch_core_blk(st, q, CoreOut{nullptr, M, Xinv, xt1, ld1, s1, xt2, ld2, s2}, nullptr, status);
+    return true;
+}
 
 void launch_core_ada32(cudaStream_t st, int q, const double *M, const double *N, float *Cinv, float *Dinv,
                        int *status)
 {
     if (q <= 128) {
-        static bool fattr = false;
-        const size_t fsm = sizeof(float) * (2 * 128 * LDK);
-        if (!fattr) {
-            cudaFuncSetAttribute(k_core_blk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm);
-            fattr = true;
-        }
-        rb_count_launch();
-        k_core_blk<<<(N && Dinv) ? 2 : 1, KT, fsm, st>>>(q, M, N, Cinv, Dinv, status);
+        CoreOut o0{M, nullptr, Cinv, nullptr, 0, 0.f, nullptr, 0, 0.f},
+            o1{N, nullptr, Dinv, nullptr, 0, 0.f, nullptr, 0, 0.f};
+        launch_core_blk(st, q, o0, (N && Dinv) ? &o1 : nullptr, status);
         return;
     }
     const int QP = ((q + 31) / 32) * 32;

@@ -27,6 +27,11 @@ void launch_gram(cudaStream_t, int n, int p, int r, const T *X, int64_t ldx, con
 template <typename T>
 void launch_core_ada(cudaStream_t, int q, const double *M, const double *N, T *Cinv, T *Dinv, int *status);
 void launch_core_ada32(cudaStream_t, int q, const double *M, const double *N, float *Cinv, float *Dinv, int *status);
+// q <= 128: X = L^-1 of one FP32 Gram matrix (L L^T = sym(M)), written to
+// Xinv (lower, ld q; may be null) and as s1 X^T into xt1 (ld1) and s2 X^T
+// into xt2 (ld2) (either may be null).  Returns false for q > 128.
+bool launch_core_tr32(cudaStream_t, int q, const float *M, float *Xinv, float *xt1, int ld1, float s1, float *xt2,
+                      int ld2, float s2, int *status);
 template <typename T>
 void launch_core_rbfgs(cudaStream_t, int q, const double *M, const double *Tm, T *Lam, T *B1, int *status);
 template <typename T>

@@ -129,7 +129,7 @@ template <int BN, int TERMS, int AMN>
 __global__ void __launch_bounds__(384, 1)
 k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
           const __grid_constant__ CUtensorMap tmBlo, int M, int N, int mt, int nkb, long long U, int maxseg,
-          float alpha, float beta, const float *Cin, int64_t ldcin, float *C, int64_t ldc, float *part,
+          float alpha, float beta, const float *Cin, int64_t ldcin, float *C, int64_t ldc, int ctrans, float *part,
           const int *status, int *err)
 {
     using CF = Cfg<BN, TERMS, AMN>;
@@ -330,8 +330,11 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                 if (part == nullptr) {
                     const int m = (t % mt) * BM + 32 * wq + lane, n0 = (t / mt) * BN;
                     if (m < M) {
-                        float *cp = C + m + (int64_t)n0 * ldc;
-                        const float *ci = Cin + m + (int64_t)n0 * ldcin;
+                        // element (m, n) at C[m + n ldc], or at C[n + m ldc] when ctrans
+                        const int64_t sm = ctrans ? ldc : 1, sn = ctrans ? 1 : ldc;
+                        const int64_t si = ctrans ? ldcin : 1, sj = ctrans ? 1 : ldcin;
+                        float *cp = C + m * sm + (int64_t)n0 * sn;
+                        const float *ci = Cin + m * si + (int64_t)n0 * sj;
 #pragma unroll
                         for (int j = 0; j < BN; ++j) {
                             if (n0 + j < N) {
@@ -339,8 +342,8 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                                 if (beta != 0.f) o = fmaf(beta, *ci, o);
                                 *cp = o;
                             }
-                            cp += ldc;
-                            ci += ldcin;
+                            cp += sn;
+                            ci += sj;
                         }
                     }
                 } else {
@@ -370,7 +373,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
 // group), thread = tile row.
 __global__ void k_streamk_reduce(int M, int N, int mt, int bn, int nkb, long long U, int G, int maxseg,
                                  const float *part, float alpha, float beta, const float *Cin, int64_t ldcin,
-                                 float *C, int64_t ldc, const int *status)
+                                 float *C, int64_t ldc, int ctrans, const int *status)
 {
     if (status_bad(status)) return;
     const int t = blockIdx.x, r = threadIdx.x, j0 = blockIdx.y * 32;
@@ -390,13 +393,14 @@ __global__ void k_streamk_reduce(int M, int N, int mt, int bn, int nkb, long lon
         for (int jj = 0; jj < 32; ++jj) s[jj] += pp[(size_t)jj * BM];
     }
     if (m >= M) return;
+    const int64_t sm = ctrans ? ldc : 1, sn = ctrans ? 1 : ldc, si = ctrans ? ldcin : 1, sj = ctrans ? 1 : ldcin;
 #pragma unroll
     for (int jj = 0; jj < 32; ++jj) {
         const int nn = n0 + jj;
         if (nn < N) {
             float o = alpha * s[jj];
-            if (beta != 0.f) o = fmaf(beta, Cin[m + (int64_t)nn * ldcin], o);
-            C[m + (int64_t)nn * ldc] = o;
+            if (beta != 0.f) o = fmaf(beta, Cin[m * si + (int64_t)nn * sj], o);
+            C[m * sm + (int64_t)nn * sn] = o;
         }
     }
 }
@@ -514,7 +518,7 @@ template <int BN, int TERMS, int AMN>
 static int launch_bn(tc_plan *p, cudaStream_t st, const CUtensorMap &ma, const CUtensorMap &mb,
                      const CUtensorMap &mblo, int M, int N, int K,
                      float alpha, float beta, const float *Cin, int64_t ldcin, float *C, int64_t ldc,
-                     const int *status, int *err, int reserve)
+                     const int *status, int *err, int reserve, int ctrans)
 {
     using CF = Cfg<BN, TERMS, AMN>;
     static bool attr = false;
@@ -531,7 +535,7 @@ static int launch_bn(tc_plan *p, cudaStream_t st, const CUtensorMap &ma, const C
     // stream-K when the tiles alone leave SMs idle and each SM still gets a few
     // k-blocks; `reserve` SMs are left free for work on other streams
     const int sms = std::max(1, g_num_sms - std::max(0, reserve));
-    const bool streamk = tiles < sms && U >= 4LL * sms;
+    const bool streamk = tiles < sms && U >= 4LL * sms && nkb >= 4 * CHUNK_KB;  // short K: one tile per CTA
     const int G = streamk ? sms : tiles;
     int maxseg = 1;
     float *part = nullptr;
@@ -552,11 +556,11 @@ static int launch_bn(tc_plan *p, cudaStream_t st, const CUtensorMap &ma, const C
     }
     rb_count_launch();
     k_tc_gemm<BN, TERMS, AMN><<<G, 384, CF::SMEM, st>>>(ma, mb, mblo, M, N, mt, nkb, U, maxseg, alpha, beta, Cin,
-                                                        ldcin, C, ldc, part, status, err);
+                                                        ldcin, C, ldc, ctrans, part, status, err);
     if (streamk) {
         rb_count_launch();
         k_streamk_reduce<<<dim3(tiles, BN / 32), BM, 0, st>>>(M, N, mt, BN, nkb, U, G, maxseg, part, alpha, beta, Cin,
-                                                              ldcin, C, ldc, status);
+                                                              ldcin, C, ldc, ctrans, status);
     }
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
@@ -564,7 +568,7 @@ static int launch_bn(tc_plan *p, cudaStream_t st, const CUtensorMap &ma, const C
 template <int TERMS>
 static int launch_terms(tc_plan *p, cudaStream_t st, int a_layout, int M, int N, int K, float alpha, const float *A,
                         int64_t lda, const float *B, int64_t ldb, float beta, const float *Cin, int64_t ldcin,
-                        float *C, int64_t ldc, const int *status, int *err, int reserve)
+                        float *C, int64_t ldc, const int *status, int *err, int reserve, int ctrans)
 {
     const int a_mn = (a_layout == TC_A_MN);
     const int bn = N <= 32 ? 32 : N <= 64 ? 64 : 128;
@@ -592,9 +596,9 @@ static int launch_terms(tc_plan *p, cudaStream_t st, int a_layout, int M, int N,
 #define RB_TC_CASE(BNV)                                                                                     \
     case BNV:                                                                                                  \
         return a_mn ? launch_bn<BNV, TERMS, 1>(p, st, ma, mb, mblo, M, N, K, alpha, beta, Cin, ldcin, C, ldc, status, \
-                                               err, reserve)                                                    \
+                                               err, reserve, ctrans)                                            \
                     : launch_bn<BNV, TERMS, 0>(p, st, ma, mb, mblo, M, N, K, alpha, beta, Cin, ldcin, C, ldc, status, \
-                                               err, reserve);
+                                               err, reserve, ctrans);
     switch (bn) {
         RB_TC_CASE(32)
         RB_TC_CASE(64)
@@ -608,10 +612,11 @@ static bool tma_ok(const void *ptr, int64_t ld) { return ((uintptr_t)ptr % 16 ==
 
 static int tc_run(tc_plan *p, cudaStream_t st, int terms, int a_layout, int M, int N, int K, float alpha,
                   const float *A, int64_t lda, const float *B, int64_t ldb, float beta, const float *Cin,
-                  int64_t ldcin, float *C, int64_t ldc, const int *status, int reserve = 0)
+                  int64_t ldcin, float *C, int64_t ldc, const int *status, int reserve = 0, int ctrans = 0)
 {
     if (M <= 0 || N <= 0) return 0;
     const bool ok = p && K > 0 && tma_ok(A, lda) && tma_ok(B, ldb);
+    if (!ok && ctrans) return -6;  // the SIMT kernels have no transposed output
     if (!ok) {
         // SIMT fallback: alpha op(A) B + beta Cin (Cin copied to C first when distinct)
         if (beta != 0.f && Cin != C) launch_copy2d<float, float>(st, M, N, Cin, ldcin, C, ldc, 1.0);
@@ -622,10 +627,11 @@ static int tc_run(tc_plan *p, cudaStream_t st, int terms, int a_layout, int M, i
     const int rc =
         (terms == 3)
             ? launch_terms<3>(p, st, a_layout, M, N, K, alpha, A, lda, B, ldb, beta, Cin, ldcin, C, ldc, status, err,
-                              reserve)
+                              reserve, ctrans)
             : launch_terms<1>(p, st, a_layout, M, N, K, alpha, A, lda, B, ldb, beta, Cin, ldcin, C, ldc, status, err,
-                              reserve);
+                              reserve, ctrans);
     if (rc == 0) return 0;
+    if (ctrans) return rc;
     // the tensor-core launch could not be set up (tensor map or workspace): run the same product on CUDA cores
     if (beta != 0.f && Cin != C) launch_copy2d<float, float>(st, M, N, Cin, ldcin, C, ldc, 1.0);
     gemm_simt<float>(st, a_layout == TC_A_K, false, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, status);
@@ -636,6 +642,13 @@ int tc_gemm_nk(tc_plan *p, cudaStream_t st, int terms, int a_layout, int M, int 
                const float *B, int64_t ldb, float *C, int64_t ldc, const int *status, int reserve_sms)
 {
     return tc_run(p, st, terms, a_layout, M, N, K, 1.f, A, lda, B, ldb, 0.f, nullptr, 0, C, ldc, status, reserve_sms);
+}
+
+int tc_gemm_nk_t(tc_plan *p, cudaStream_t st, int terms, int a_layout, int M, int N, int K, const float *A,
+                 int64_t lda, const float *B, int64_t ldb, float *C, int64_t ldc, const int *status, int reserve_sms)
+{
+    return tc_run(p, st, terms, a_layout, M, N, K, 1.f, A, lda, B, ldb, 0.f, nullptr, 0, C, ldc, status, reserve_sms,
+                  1);
 }
 
 int tc_gemm_nk_axpby(tc_plan *p, cudaStream_t st, int terms, int a_layout, int M, int N, int K, float alpha,

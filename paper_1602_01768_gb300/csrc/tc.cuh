@@ -27,6 +27,11 @@ void tc_plan_destroy(tc_plan *p);
 int tc_gemm_nk(tc_plan *p, cudaStream_t st, int terms, int a_layout, int M, int N, int K, const float *A,
                int64_t lda, const float *B, int64_t ldb, float *C, int64_t ldc, const int *status,
                int reserve_sms = 0);
+// Same product with C written transposed: element (m, n) at C[n + m ldc]
+// (C^T column-major).  Tensor cores only: returns <0 where that is not possible.
+int tc_gemm_nk_t(tc_plan *p, cudaStream_t st, int terms, int a_layout, int M, int N, int K, const float *A,
+                 int64_t lda, const float *B, int64_t ldb, float *C, int64_t ldc, const int *status,
+                 int reserve_sms = 0);
 int tc_gemm_nk_axpby(tc_plan *p, cudaStream_t st, int terms, int a_layout, int M, int N, int K, float alpha,
                      const float *A, int64_t lda, const float *B, int64_t ldb, float beta, const float *Cin,
                      int64_t ldcin, float *C, int64_t ldc);
