@@ -83,27 +83,124 @@ static void philox_at(uint64_t seed, uint32_t w0, uint32_t w1, uint64_t k, uint6
 /* 24-bit uniform in (0,1): ((x >> 8) + 1/2) * 2^-24, exact in binary32 and binary64. */
 static double u24(uint32_t x) { return ((double)(x >> 8) + 0.5) * (1.0 / 16777216.0); }
 
+static float f32_of_bits(uint32_t b)
+{
+    float f;
+    memcpy(&f, &b, 4);
+    return f;
+}
+static uint32_t bits_of_f32(float f)
+{
+    uint32_t b;
+    memcpy(&b, &f, 4);
+    return b;
+}
+
+/*
+ * The Gaussian sketch is defined through binary32 arithmetic in a fixed order
+ * (each step one correctly rounded IEEE operation; polynomials by fmaf in
+ * Horner order), so that any IEEE platform reproduces it bit for bit.  The
+ * elementary functions are written out from their Taylor series:
+ *
+ * ln u for u in (0, 1): u = m 2^e with m in [sqrt(1/2), sqrt(2)) (exact),
+ * ln m = 2 atanh(s), s = (m - 1) / (m + 1), |s| < 0.1716, and
+ * atanh(s) = s + s^3/3 + s^5/5 + s^7/7 + s^9/9 (the next term is below
+ * 2e-9 relative); ln u = e ln2_hi + (e ln2_lo + ln m) with ln2_hi holding 16
+ * significant bits, so e ln2_hi is exact.
+ */
+#define ORC_LN2_HI 0.693145751953125f
+#define ORC_LN2_LO 1.42860676e-06f
+
+float orc_logf32(float u)
+{
+    uint32_t b = bits_of_f32(u);
+    int e = (int)((b >> 23) & 0xffu) - 127;
+    float m = f32_of_bits((b & 0x007fffffu) | 0x3f800000u); /* [1, 2) */
+    if (m > 1.41421354f) {
+        m = m * 0.5f; /* exact */
+        e += 1;
+    }
+    const float s = (m - 1.0f) / (m + 1.0f); /* m - 1 exact (Sterbenz) */
+    const float s2 = s * s;
+    float p = fmaf(s2, 0.111111112f, 0.142857149f); /* 1/9, 1/7 */
+    p = fmaf(s2, p, 0.200000003f);                  /* 1/5 */
+    p = fmaf(s2, p, 0.333333343f);                  /* 1/3 */
+    const float at = fmaf(s * s2, p, s);            /* atanh(s) */
+    const float lm = 2.0f * at;                     /* exact */
+    const float t = fmaf((float)e, ORC_LN2_LO, lm);
+    return (float)e * ORC_LN2_HI + t;
+}
+
+/*
+ * sin(pi x) and cos(pi x) for x in [0, 2]: k = nearest integer to 2x (2x is
+ * exact), r = x - k/2 in [-1/4, 1/4] (exact), t = pi r (rounded), the Taylor
+ * polynomials of sin t (to t^11) and cos t (to t^12), then the quarter turn
+ * k mod 4 selects and signs them.
+ */
+#define ORC_PI_F 3.14159274f
+
+void orc_sincospif32(float x, float *sp, float *cp)
+{
+    const float k = rintf(2.0f * x);
+    const float r = x - 0.5f * k;
+    const float t = r * ORC_PI_F;
+    const float t2 = t * t;
+    float ps = fmaf(t2, -2.50521079e-08f, 2.75573188e-06f); /* -1/11!, 1/9! */
+    ps = fmaf(t2, ps, -1.98412701e-04f);                    /* -1/7! */
+    ps = fmaf(t2, ps, 8.33333377e-03f);                     /* 1/5! */
+    ps = fmaf(t2, ps, -0.166666672f);                       /* -1/3! */
+    const float sn = fmaf(t * t2, ps, t);
+    float pc = fmaf(t2, 2.08767570e-09f, -2.75573188e-07f); /* 1/12!, -1/10! */
+    pc = fmaf(t2, pc, 2.48015876e-05f);                     /* 1/8! */
+    pc = fmaf(t2, pc, -1.38888892e-03f);                    /* -1/6! */
+    pc = fmaf(t2, pc, 4.16666679e-02f);                     /* 1/4! */
+    pc = fmaf(t2, pc, -0.5f);                               /* -1/2! */
+    const float cs = fmaf(t2, pc, 1.0f);
+    switch ((int)k & 3) {
+    case 0: *sp = sn; *cp = cs; break;
+    case 1: *sp = cs; *cp = -sn; break;
+    case 2: *sp = -sn; *cp = -cs; break;
+    default: *sp = -cs; *cp = sn; break;
+    }
+}
+
+/* Round a finite binary32 value to the nearest TF32 value (10 stored fraction
+ * bits), ties to even. */
+float orc_round_tf32(float z)
+{
+    uint32_t b = bits_of_f32(z);
+    const uint32_t r = b & 0x1fffu;
+    b &= ~0x1fffu;
+    if (r > 0x1000u || (r == 0x1000u && (b & 0x2000u))) b += 0x2000u;
+    return f32_of_bits(b);
+}
+
 /*
  * Gaussian sketch S~ (n x q) for step k.  The paper draws S~ with i.i.d.
  * standard normal entries (Sec. 9.3, AdaRBFGS_gauss; Sec. 10); it does not
- * fix a generator.  Reading used here: entries (4r+t, j), t = 0..3, come from
- * one Philox block with counter (r, j, k, stream) and key (seed_lo, seed_hi),
- * turned into normals by the Box-Muller transform on word pairs (0,1), (2,3):
- *   rad = sqrt(-2 ln u_a),  z_a = rad cos(2 pi u_b),  z_b = rad sin(2 pi u_b).
+ * fix a generator or a precision.  Reading used here: entries (4r+t, j),
+ * t = 0..3, come from one Philox block with counter (r, j, k, stream) and key
+ * (seed_lo, seed_hi), turned into normals by the Box-Muller transform on word
+ * pairs (0,1), (2,3):
+ *   rad = sqrt(-2 ln u_a),  z_a = rad cos(2 pi u_b),  z_b = rad sin(2 pi u_b),
+ * evaluated in binary32 as above and rounded to the nearest TF32 value, so
+ * every entry carries 11 significant bits and is exact in one tensor-core pass.
  */
 void orc_gauss_sketch(uint64_t seed, uint64_t stream, uint64_t k, int n, int q, double *S)
 {
-    const double two_pi = 6.283185307179586476925286766559;
     for (int j = 0; j < q; ++j) {
         for (int r = 0; 4 * r < n; ++r) {
             uint32_t w[4];
             philox_at(seed, (uint32_t)r, (uint32_t)j, k, stream, w);
             double z[4];
             for (int p = 0; p < 2; ++p) {
-                double rad = sqrt(-2.0 * log(u24(w[2 * p])));
-                double ang = two_pi * u24(w[2 * p + 1]);
-                z[2 * p] = rad * cos(ang);
-                z[2 * p + 1] = rad * sin(ang);
+                /* binary32 uniforms: above 1/2 the 25-bit value rounds to even (1 is possible, giving 0) */
+                const float ua = (float)u24(w[2 * p]), ub = (float)u24(w[2 * p + 1]);
+                const float rad = sqrtf(-2.0f * orc_logf32(ua));
+                float sn, cs;
+                orc_sincospif32(2.0f * ub, &sn, &cs);
+                z[2 * p] = orc_round_tf32(rad * cs);
+                z[2 * p + 1] = orc_round_tf32(rad * sn);
             }
             for (int t = 0; t < 4 && 4 * r + t < n; ++t) S[(4 * r + t) + (size_t)j * n] = z[t];
         }

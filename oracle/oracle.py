@@ -46,6 +46,9 @@ def lib():
             "orc_residual": (d, [i, p, p]),
             "orc_residual_factored": (d, [i, p, p]),
             "orc_residual_sampled": (d, [i, p, p, p, i, u64]),
+            "orc_logf32": (C.c_float, [C.c_float]),
+            "orc_sincospif32": (None, [C.c_float, p, p]),
+            "orc_round_tf32": (C.c_float, [C.c_float]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -70,6 +73,22 @@ def philox(ctr, key):
     out = np.zeros(4, dtype=np.uint32)
     lib().orc_philox4x32_10(_ptr(c), _ptr(k), _ptr(out))
     return out
+
+
+def logf32(u):
+    """The sketch generator's binary32 natural log (oracle.c, orc_logf32)."""
+    return np.float32(lib().orc_logf32(float(np.float32(u))))
+
+
+def sincospif32(x):
+    """The sketch generator's binary32 (sin(pi x), cos(pi x)) (orc_sincospif32)."""
+    s, c = C.c_float(), C.c_float()
+    lib().orc_sincospif32(float(np.float32(x)), C.byref(s), C.byref(c))
+    return np.float32(s.value), np.float32(c.value)
+
+
+def round_tf32(z):
+    return np.float32(lib().orc_round_tf32(float(np.float32(z))))
 
 
 def gauss_sketch(seed, stream, k, n, q):

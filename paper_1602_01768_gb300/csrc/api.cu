@@ -522,12 +522,13 @@ static void ada_step_tc(rb_ctx *h)
     const int side_rsv = std::max(0, tc_num_sms() - SIDE_SMS);
     ada_draw<float>(h, St);
     mark(h, "sketch");
-    tc_gemm_nk(h->tc, st, acc, TC_A_MN, n, q, n, L, n, St, n, S, n, stp);       // S = L S~   (A = L, M-contiguous)
+    // S = L S~ (A = L, M-contiguous); S~ is exact in TF32, so the split needs only L's two parts
+    tc_gemm_nk(h->tc, st, acc == 3 ? 2 : acc, TC_A_MN, n, q, n, L, n, St, n, S, n, stp);
     if (fork) {
         cudaEventRecord(h->ev_sk, st);
         cudaStreamWaitEvent(side, h->ev_sk, 0);
-        if (tcv) {  // S~^T S~ (3 x TF32) -> D^-T into the top of Bv
-            tc_gemm_nk(h->tc2, side, 3, TC_A_K, q, q, n, St, n, St, n, h->Nf, q, stp, side_rsv);
+        if (tcv) {  // S~^T S~ (products exact: S~ is TF32) -> D^-T into the top of Bv
+            tc_gemm_nk(h->tc2, side, 1, TC_A_K, q, q, n, St, n, St, n, h->Nf, q, stp, side_rsv);
             launch_core_tr32(side, q, h->Nf, nullptr, h->Bv, 2 * q, 1.f, nullptr, 0, 0.f, h->d_status);
         } else {
             launch_gram<float>(side, n, q, q, St, n, St, n, h->part, h->N);  // S~^T S~ -> D^-1

@@ -42,7 +42,7 @@ struct Cfg {
     // cannot read from shared memory into TMEM: the lo part (3 terms) and, for
     // an M-contiguous tile, the hi part as well (transposed to lanes = rows).
     static constexpr bool HI_TMEM = AMN != 0;
-    static constexpr bool LO_TMEM = TERMS == 3;
+    static constexpr bool LO_TMEM = TERMS >= 2;
     static constexpr bool CONVERT = HI_TMEM || LO_TMEM;
     static constexpr int LO_OFF = HI_TMEM ? 32 : 0;  // TMEM column of lo within a stage
     static constexpr int A_BYTES = A_TILE_BYTES;
@@ -248,6 +248,9 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                         mma_tf32_ts(dacc, ta + CF::LO_OFF + 8 * kk, db_hi, idesc, first);  // lo x hi
                         mma_hi(umma_desc(b_lo + kk * 32, 16, 1024), 1u);                  // hi x lo
                         mma_hi(db_hi, 1u);                                                 // hi x hi
+                    } else if (TERMS == 2) {  // B exact in TF32
+                        mma_tf32_ts(dacc, ta + CF::LO_OFF + 8 * kk, db_hi, idesc, first);  // lo x B
+                        mma_hi(db_hi, 1u);                                                 // hi x B
                     } else {
                         mma_hi(db_hi, first);
                     }
@@ -625,11 +628,12 @@ static int tc_run(tc_plan *p, cudaStream_t st, int terms, int a_layout, int M, i
     }
     int *err = status ? const_cast<int *>(status) : p->err;
     const int rc =
-        (terms == 3)
-            ? launch_terms<3>(p, st, a_layout, M, N, K, alpha, A, lda, B, ldb, beta, Cin, ldcin, C, ldc, status, err,
-                              reserve, ctrans)
-            : launch_terms<1>(p, st, a_layout, M, N, K, alpha, A, lda, B, ldb, beta, Cin, ldcin, C, ldc, status, err,
-                              reserve, ctrans);
+        (terms == 3)   ? launch_terms<3>(p, st, a_layout, M, N, K, alpha, A, lda, B, ldb, beta, Cin, ldcin, C, ldc,
+                                         status, err, reserve, ctrans)
+        : (terms == 2) ? launch_terms<2>(p, st, a_layout, M, N, K, alpha, A, lda, B, ldb, beta, Cin, ldcin, C, ldc,
+                                         status, err, reserve, ctrans)
+                       : launch_terms<1>(p, st, a_layout, M, N, K, alpha, A, lda, B, ldb, beta, Cin, ldcin, C, ldc,
+                                         status, err, reserve, ctrans);
     if (rc == 0) return 0;
     if (ctrans) return rc;
     // the tensor-core launch could not be set up (tensor map or workspace): run the same product on CUDA cores

@@ -6,6 +6,8 @@
 //   B K x N:     element (k, n) at B[k + n ldb]             (K contiguous)
 //
 // terms = 1: single-pass TF32 products (FP32 accumulate).
+// terms = 2: B already exact in TF32 (e.g. the TF32-rounded Gaussian sketch):
+//            A = hi + lo, C accumulates hi*B + lo*B.
 // terms = 3: each operand split x = hi + lo with hi = x truncated to the
 //            11 leading significand bits (exact in TF32) and lo = x - hi;
 //            C accumulates hi*hi + hi*lo + lo*hi, which carries ~22 bits.

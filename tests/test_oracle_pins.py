@@ -66,6 +66,65 @@ def test_gauss_sketch_moments_and_determinism():
     assert np.array_equal(S5, S[:4093])
 
 
+def test_sketch_logf32_matches_libm():
+    # the generator's binary32 ln against the platform's binary64 log, on the
+    # 24-bit uniform grid it is used on (both ends included)
+    xs = np.unique(np.concatenate([np.arange(0, 1 << 24, 977, dtype=np.int64),
+                                   np.arange(0, 64), np.arange((1 << 24) - 64, 1 << 24)]))
+    for x in xs:
+        u = float(np.float32((x + 0.5) / 16777216.0))  # the binary32 uniform the generator uses
+        got = float(orc.logf32(u))
+        ref = math.log(u)
+        ulp = float(np.spacing(np.float32(abs(ref)))) if ref != 0.0 else 0.0
+        # a few roundings (divide, polynomial) on top of the series; a wrong
+        # coefficient would be off by hundreds of ulps
+        assert abs(got - ref) <= 8.0 * ulp, (u, got, ref)
+
+
+def test_sketch_sincospif32_matches_libm():
+    xs = np.concatenate([np.linspace(0.0, 2.0, 20001), [0.25, 0.5, 0.75, 1.0, 1.25, 1.5, 1.75]])
+    for x in xs:
+        x = float(np.float32(x))
+        s, c = orc.sincospif32(x)
+        assert abs(float(s) - math.sin(math.pi * x)) <= 2.0 ** -22, x
+        assert abs(float(c) - math.cos(math.pi * x)) <= 2.0 ** -22, x
+
+
+def test_gauss_sketch_is_tf32_box_muller_of_the_philox_words():
+    # every entry is the TF32 value nearest the binary64 Box-Muller normal of
+    # its Philox words (computed here with numpy from the KAT-pinned Philox),
+    # so a wrong word pairing, index or sign fails
+    seed, stream, k, n, q = 0x1234_5678_9ABC_DEF0, 5, 9, 203, 7
+    S = orc.gauss_sketch(seed, stream, k, n, q)
+    f = S.astype(np.float32)
+    assert np.array_equal(f.astype(np.float64), S)
+    assert np.all((f.view(np.uint32) & 0x1FFF) == 0)  # 11 significant bits
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    for j in range(q):
+        for r in range((n + 3) // 4):
+            w = orc.philox([r, j, k, stream], key)
+            u = [float(np.float32(((int(x) >> 8) + 0.5) / 16777216.0)) for x in w]  # binary32 uniforms
+            z = []
+            for p in range(2):
+                rad = math.sqrt(-2.0 * math.log(u[2 * p])) if u[2 * p] < 1.0 else 0.0
+                z += [rad * math.cos(2 * math.pi * u[2 * p + 1]), rad * math.sin(2 * math.pi * u[2 * p + 1])]
+            for t in range(4):
+                if 4 * r + t < n:
+                    v = S[4 * r + t, j]
+                    assert abs(v - z[t]) <= 2.0 ** -11 * abs(z[t]) + 1e-6, (r, j, t, v, z[t])
+
+
+def test_round_tf32_is_nearest_even():
+    one = 1.0
+    ulp = 2.0 ** -10
+    assert float(orc.round_tf32(one + 0.49 * ulp)) == one
+    assert float(orc.round_tf32(one + 0.51 * ulp)) == one + ulp
+    assert float(orc.round_tf32(one + 0.5 * ulp)) == one                # tie -> even
+    assert float(orc.round_tf32(one + 1.5 * ulp)) == one + 2 * ulp      # tie -> even
+    assert float(orc.round_tf32(-(one + 0.51 * ulp))) == -(one + ulp)
+    assert float(orc.round_tf32(2.0 - 0.4 * ulp)) == 2.0                # carries into the exponent
+
+
 def test_floyd_sample_is_uniform_without_replacement():
     n, m, trials = 20, 5, 20000
     counts = np.zeros(n)
