@@ -34,7 +34,7 @@ CHECK_EVERY, CHECK_COLS, CONFIRM_COLS = 32, 256, 1024
 MAX_ITER = 20000
 # DRAM bytes (read + write) of one k_tc_update launch at n = 8192, q = 128, from one ncu capture
 # (profiles/tc_kernels_n8192_full.md); scaled by (n / 8192)^2 for other n at q = 128.
-UPDATE_TRAFFIC_N8192_Q128 = 279770624 + 208392448
+UPDATE_TRAFFIC_N8192_Q128 = 277638912 + 208375552
 
 
 def parse():
@@ -67,6 +67,21 @@ def load_peaks():
         return float(p["hbm_gbs"]), float(p["bf16_tflops"]), "measured"
     except Exception:
         return 6800.0, 1900.0, "fallback"
+
+
+# Nominal dense tensor rates (PFLOP/s): TF32 1.1 vs BF16 2.25; a TF32 contraction's peak is the
+# measured BF16 peak times this ratio.
+TF32_PER_BF16 = 1.1 / 2.25
+
+
+def load_tf32_sustained_peak():
+    """Measured sustained BF16 TFLOP/s (kernels timed inside a long step) scaled to TF32."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["bf16_tflops_sustained"]) * TF32_PER_BF16, "measured sustained BF16 x 1.1/2.25"
+    except Exception:
+        return 1700.0 * TF32_PER_BF16, "fallback sustained BF16 x 1.1/2.25"
 
 
 class ClockSampler:
@@ -262,6 +277,16 @@ def run_serving(B, wl, args):
     B.rb_srv_destroy(s)
     ok = [r for r in res if r.status == B.RB_OK]
     lat = sorted(r.latency_s for r in res)
+    by_tol = {}
+    for r, req in zip(res, stream):
+        c = by_tol.setdefault(f"{req['tol']:g}", {"requests": 0, "converged": 0, "resid": [], "latency": []})
+        c["requests"] += 1
+        c["converged"] += int(r.status == B.RB_OK)
+        c["resid"].append(r.resid)
+        c["latency"].append(r.latency_s)
+    per_tol = {k: {"requests": v["requests"], "converged": v["converged"],
+                   "median_final_resid": statistics.median(v["resid"]),
+                   "p50_s": statistics.median(v["latency"])} for k, v in sorted(by_tol.items())}
     return {"workload": f"first {len(stream)} requests of the Poisson stream at {args.serve_rate:g} req/s, "
                         "n log-uniform in [512, 8192], A = M^T M/(2n) + 1e-3 I, tol in {1e-3,1e-4,1e-6}, "
                         "q = 32 round(sqrt(n)/32), mixed form, HBM budget 120 GiB, <= 64 live",
@@ -269,7 +294,7 @@ def run_serving(B, wl, args):
             "solves_per_s": len(res) / wall, "p50_s": lat[len(lat) // 2],
             "p99_s": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)],
             "mean_queue_s": statistics.mean(r.queue_s for r in res), "wall_s": wall,
-            "server_p50_s": st.p50_s, "server_p99_s": st.p99_s}
+            "server_p50_s": st.p50_s, "server_p99_s": st.p99_s, "per_tol": per_tol}
 
 
 def run_batched(B, wl, args):
@@ -371,6 +396,18 @@ def main():
                 "traffic": (UPDATE_TRAFFIC_N8192_Q128 * (n / 8192) ** 2) if q == 128 else None,
                 "algorithmic_bytes_per_launch": upd_bytes, "ms_per_launch": upd_ms}
     step_ms = sum(phases.values())
+    # the tcgen05 GEMMs of the step against the TF32 tensor peak: MMA work = terms x 2 n^2 q
+    tf32_peak, tf32_kind = load_tf32_sustained_peak()
+    gemm_rooflines = []
+    for ph, kern, terms in (("S=LS~", "S = L S~ (k_tc_gemm, 2 x TF32)", 2),
+                            ("G=AS | D core", "G = A S (k_tc_gemm, 3 x TF32, 144 SMs)", 3),
+                            ("W=G^TL | C core", "W^T = L^T G (k_tc_gemm, 3 x TF32, 144 SMs)", 3)):
+        if ph in phases:
+            tflops = terms * 2.0 * n * n * q / (phases[ph] * 1e-3) / 1e12
+            gemm_rooflines.append({"kernel": kern, "bound": "tensor", "achieved": tflops, "peak": tf32_peak,
+                                   "unit": "TFLOP/s", "frac": tflops / tf32_peak, "peak_kind": tf32_kind,
+                                   "hbm_gbs": 4.0 * n * n / (phases[ph] * 1e-3) / 1e9,
+                                   "ms_per_launch": phases[ph]})
 
     # ---- plain FP32 form, same tolerance (one solve) ----
     fp32 = None
@@ -437,7 +474,7 @@ def main():
                "data": "synthetic", "config": config(args, args.prec),
                "time_to_tol_s": t_solve, "iters_per_solve": iters, "resid_final": resids,
                "latency_s": {"p50": statistics.median(lat), "p99": p99},
-               "fp32_form": fp32, "roofline": roofline, "phases_ms": phases, "step_ms": step_ms,
+               "fp32_form": fp32, "roofline": roofline, "gemm_rooflines": gemm_rooflines, "phases_ms": phases, "step_ms": step_ms,
                "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
                "serving": serving, "batched": batched,
                "wall_s": wall}
