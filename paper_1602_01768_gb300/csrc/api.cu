@@ -25,7 +25,11 @@ struct rb_ctx {
 
     // n x q panels (ld n) and q x n panels (ld q)
     void *St = nullptr, *S = nullptr, *G = nullptr, *Y = nullptr, *Sh = nullptr;
-    void *W = nullptr, *V = nullptr;  // W shares St's allocation (see alloc_sketch_workspace)
+    void *W = nullptr, *V = nullptr;  // W and Stb share St's allocation (see alloc_sketch_workspace)
+    void *Stb = nullptr;              // second sketch buffer: step k uses St (k even) or Stb (k odd)
+    bool s_valid = false;             // S holds L_k S~_k from the previous fused update
+    float *Spart = nullptr;           // partial S blocks of the fused update
+    size_t spart_cap = 0;
     float *Bv = nullptr, *Bs = nullptr;  // tensor-core V and S^: [D^-T; -C^-T] (2q x q) and C^-T (q x q)
     float *Mf = nullptr, *Nf = nullptr;  // FP32 Gram products S^T A S and S~^T S~ (tensor-core path)
     tc_plan *tc2 = nullptr;              // plan (own workspace) for the side stream's tensor-core GEMMs
@@ -132,12 +136,14 @@ extern "C" const char *rbfgs_status_string(int s)
 static void destroy_ctx(rb_ctx *h)
 {
     if (!h) return;
-    h->W = nullptr;  // part of St's allocation
+    h->W = nullptr;  // parts of St's allocation
+    h->Stb = nullptr;
     void **bufs[] = {&h->A, &h->X, &h->X2, &h->X3, &h->St, &h->S, &h->G, &h->Y, &h->Sh,
                      &h->V, &h->P3, &h->Cinv, &h->Dinv, &h->Lam, &h->B1, &h->R1, &h->R2, &h->R3};
     for (void **b : bufs) rb_free(*b);
     rb_freet(h->Bv);
     rb_freet(h->Bs);
+    rb_freet(h->Spart);
     rb_freet(h->Mf);
     rb_freet(h->Nf);
     if (h->tc2) tc_plan_destroy(h->tc2);
@@ -260,9 +266,11 @@ static rb_status alloc_sketch_workspace(rb_ctx *h)
     const size_t n = h->n, q = h->q, e = h->esz;
     const size_t nq = n * q * e, qq = q * q * e;
     const int nch = ceil_div(h->n, GRAM_CHUNK);
-    // St and W side by side: [S~ | W^T] is the n x 2q M-contiguous operand of V^T
-    RB_TRY(rb_alloc(&h->St, 2 * nq));
+    // [S~_a | W^T | S~_b] side by side: [S~_a | W^T] or [W^T | S~_b] is the n x 2q
+    // M-contiguous operand of V^T, whichever sketch buffer the step uses
+    RB_TRY(rb_alloc(&h->St, 3 * nq));
     h->W = (char *)h->St + nq;
+    h->Stb = (char *)h->St + 2 * nq;
     RB_TRY(rb_alloc(&h->S, nq));
     RB_TRY(rb_alloc(&h->G, nq));
     RB_TRY(rb_alloc(&h->Y, nq));
@@ -272,6 +280,10 @@ static rb_status alloc_sketch_workspace(rb_ctx *h)
         RB_TRY(rb_alloc(&h->Bs, q * q * sizeof(float)));
         RB_TRY(rb_alloc(&h->Mf, q * q * sizeof(float)));
         RB_TRY(rb_alloc(&h->Nf, q * q * sizeof(float)));
+        if (h->method == RB_METHOD_ADARBFGS && q <= 128) {
+            h->spart_cap = tc_update_s_workspace(h->n, (int)q);
+            RB_TRY(rb_alloc(&h->Spart, h->spart_cap * sizeof(float)));
+        }
     }
     RB_TRY(rb_alloc(&h->V, nq));
     RB_TRY(rb_alloc(&h->Cinv, qq));
@@ -427,13 +439,13 @@ extern "C" rb_status rbfgs_step(rbfgs_t h, int nsteps)
 // factors: L+ = L + (S C^-T)(D^-1 S~^T - C^-1 (A S)^T L)).
 // ---------------------------------------------------------------------------
 template <typename T>
-static void ada_draw(rb_ctx *h, T *St)
+static void ada_draw(rb_ctx *h, T *St, uint64_t k)
 {
     if (h->sketch == RB_SKETCH_COORD_UNIFORM) {
-        launch_floyd_draw(h->st, h->n, h->q, h->seed, h->stream_id, h->k, h->idx);
+        launch_floyd_draw(h->st, h->n, h->q, h->seed, h->stream_id, k, h->idx);
         launch_coord_matrix<T>(h->st, h->n, h->q, h->idx, St, h->n);
     } else {
-        launch_gauss_sketch<T>(h->st, h->n, h->q, h->seed, h->stream_id, h->k, St, h->n);
+        launch_gauss_sketch<T>(h->st, h->n, h->q, h->seed, h->stream_id, k, St, h->n);
     }
 }
 
@@ -445,7 +457,7 @@ static void ada_step_simt(rb_ctx *h)
     const int *stp = h->d_status;
     T *A = (T *)h->A, *L = (T *)h->X, *St = (T *)h->St, *S = (T *)h->S, *G = (T *)h->G;
     T *W = (T *)h->W, *V = (T *)h->V, *Sh = (T *)h->Sh, *Ci = (T *)h->Cinv, *Di = (T *)h->Dinv;
-    ada_draw<T>(h, St);
+    ada_draw<T>(h, St, h->k);
     mark(h, "sketch");
     gemm_simt<T>(st, false, false, n, q, n, T(1), L, n, St, n, T(0), S, n, stp);   // S = L S~
     mark(h, "S=LS~");
@@ -492,9 +504,13 @@ constexpr int SIDE_SMS = 8;
 
 // Tensor-core step.  The q x q work runs on a low-priority side stream while
 // the n x n passes run on a high-priority one; the GEMMs that overlap side
-// work leave SIDE_SMS SMs free for it:
-//   main:  sketch -> S = L S~ -> G = A S -> W^T = L^T G -> [join] -> V, S^ -> L += S^ V
-//   side:            [after S]  S~^T S~, D^-1   [after G]  S^T G, C^-1
+// work leave SIDE_SMS SMs free for it.  With the fused update (single-pass
+// correction, q <= 128) the step is
+//   main:  [S = L S~ once, after init / reset / import]  G = A S -> W^T = L^T G
+//          -> [join] -> V, S^ -> draw S~_{k+1} -> L += S^ V and S = L S~_{k+1}
+//   side:  S~^T S~, D^-1 (from the step start)   [after G]  S^T G, C^-1
+// so every step streams A once and L three times (read for W, read + write).
+// Otherwise S = L S~ is its own GEMM at the start of the step.
 static void ada_step_tc(rb_ctx *h)
 {
     const int n = h->n, q = h->q;
@@ -507,7 +523,7 @@ static void ada_step_tc(rb_ctx *h)
     }
     cudaStream_t st = h->st;
     const int *stp = h->d_status;
-    float *A = (float *)h->A, *L = (float *)h->X, *St = (float *)h->St, *S = (float *)h->S, *G = (float *)h->G;
+    float *A = (float *)h->A, *L = (float *)h->X, *S = (float *)h->S, *G = (float *)h->G;
     float *W = (float *)h->W, *V = (float *)h->V, *Sh = (float *)h->Sh, *Ci = (float *)h->Cinv,
           *Di = (float *)h->Dinv;
     const int acc = (h->prec == RB_TF32) ? 1 : 3;  // split terms of the accuracy-critical products
@@ -518,32 +534,47 @@ static void ada_step_tc(rb_ctx *h)
     // straight into the B operands (needs q <= 128 and 16-byte rows)
     bool tcv = fork && q <= 128 && q % 4 == 0 && n % 4 == 0;
     if (tcv && !h->tc2) tcv = (h->tc2 = tc_plan_create(n, q, h->prec)) != nullptr;
+    const bool fuse = tcv && upd == 1 && h->Spart;
     // the side stream's Gram products run stream-K on the SIDE_SMS SMs the main GEMMs leave free
     const int side_rsv = std::max(0, tc_num_sms() - SIDE_SMS);
-    ada_draw<float>(h, St);
-    mark(h, "sketch");
-    // S = L S~ (A = L, M-contiguous); S~ is exact in TF32, so the split needs only L's two parts
-    tc_gemm_nk(h->tc, st, acc == 3 ? 2 : acc, TC_A_MN, n, q, n, L, n, St, n, S, n, stp);
+    // sketch buffers: [S~_a | W^T | S~_b]; step k uses S~_a (k even) or S~_b (k odd) when fused
+    const bool odd = fuse && (h->k & 1);
+    float *St = odd ? (float *)h->Stb : (float *)h->St;
+    float *St_next = odd ? (float *)h->St : (float *)h->Stb;
+    float *SW = odd ? W : St;          // V^T's A operand: [S~ | W^T] or [W^T | S~]
+    const int dofs = odd ? q : 0;      // rows of D^-T in Bv (the -C^-T rows take the other half)
+    const int cofs = odd ? 0 : q;
+    if (!fuse || !h->s_valid) {
+        ada_draw<float>(h, St, h->k);
+        mark(h, "sketch");
+        if (fuse) {  // S = L S~ from the fused kernel without the update, so every S comes from one path
+            const int rc = tc_update_next_s(st, n, q, Sh, V, L, n, St, S, 0, h->Spart, h->spart_cap, stp);
+            if (rc != 0) tc_gemm_nk(h->tc, st, acc == 3 ? 2 : acc, TC_A_MN, n, q, n, L, n, St, n, S, n, stp);
+        } else {
+            // S = L S~ (A = L, M-contiguous); S~ is exact in TF32, so the split needs only L's two parts
+            tc_gemm_nk(h->tc, st, acc == 3 ? 2 : acc, TC_A_MN, n, q, n, L, n, St, n, S, n, stp);
+        }
+        mark(h, "S=LS~");
+    }
     if (fork) {
         cudaEventRecord(h->ev_sk, st);
         cudaStreamWaitEvent(side, h->ev_sk, 0);
-        if (tcv) {  // S~^T S~ (products exact: S~ is TF32) -> D^-T into the top of Bv
+        if (tcv) {  // S~^T S~ (products exact: S~ is TF32) -> D^-T into Bv
             tc_gemm_nk(h->tc2, side, 1, TC_A_K, q, q, n, St, n, St, n, h->Nf, q, stp, side_rsv);
-            launch_core_tr32(side, q, h->Nf, nullptr, h->Bv, 2 * q, 1.f, nullptr, 0, 0.f, h->d_status);
+            launch_core_tr32(side, q, h->Nf, nullptr, h->Bv + dofs, 2 * q, 1.f, nullptr, 0, 0.f, h->d_status);
         } else {
             launch_gram<float>(side, n, q, q, St, n, St, n, h->part, h->N);  // S~^T S~ -> D^-1
             launch_core_ada32(side, q, h->N, nullptr, Di, nullptr, h->d_status);
         }
     }
-    mark(h, "S=LS~");
     tc_gemm_nk(h->tc, st, acc, TC_A_K, n, q, n, A, n, S, n, G, n, stp, rsv);  // G = A S    (A symmetric)
     mark(h, fork ? "G=AS | D core" : "G=AS");
     if (fork) {
         cudaEventRecord(h->ev_g, st);
         cudaStreamWaitEvent(side, h->ev_g, 0);
-        if (tcv) {  // S^T A S = S^T G (3 x TF32) -> -C^-T into the bottom of Bv, C^-T into Bs
+        if (tcv) {  // S^T A S = S^T G (3 x TF32) -> -C^-T into Bv, C^-T into Bs
             tc_gemm_nk(h->tc2, side, 3, TC_A_K, q, q, n, S, n, G, n, h->Mf, q, stp, side_rsv);
-            launch_core_tr32(side, q, h->Mf, nullptr, h->Bv + q, 2 * q, -1.f, h->Bs, q, 1.f, h->d_status);
+            launch_core_tr32(side, q, h->Mf, nullptr, h->Bv + cofs, 2 * q, -1.f, h->Bs, q, 1.f, h->d_status);
         } else {
             launch_gram<float>(side, n, q, q, S, n, G, n, h->part, h->M);    // S^T A S -> C^-1
             launch_core_ada32(side, q, h->M, nullptr, Ci, nullptr, h->d_status);
@@ -563,8 +594,8 @@ static void ada_step_tc(rb_ctx *h)
     if (fork) cudaStreamWaitEvent(st, h->ev_core, 0);                            // join: C^-1, D^-1 ready
     mark(h, fork ? "W=G^TL | C core" : "W=G^TL");
     if (tcv) {
-        // V^T = [S~ | W^T] [D^-T; -C^-T] (n x q), written transposed: V is q x n (ld q)
-        tc_gemm_nk_t(h->tc, st, acc, TC_A_MN, n, q, 2 * q, St, n, h->Bv, 2 * q, V, q, stp);
+        // V^T = [S~ | W^T] [D^-T; -C^-T] (or both halves swapped), written transposed: V is q x n (ld q)
+        tc_gemm_nk_t(h->tc, st, acc, TC_A_MN, n, q, 2 * q, SW, n, h->Bv, 2 * q, V, q, stp);
         // S^ = S C^-T, written transposed (row-major n x q) for the K-major update operand
         tc_gemm_nk_t(h->tc, st, upd, TC_A_MN, n, q, q, S, n, h->Bs, q, Sh, q, stp);
     } else {
@@ -575,10 +606,24 @@ static void ada_step_tc(rb_ctx *h)
         gemm_simt<float>(st, false, true, q, n, q, 1.f, Ci, q, S, n, 0.f, Sh, q, stp);  // S^^T = C^-1 S^T (q x n)
     }
     mark(h, "V, S^");
-    // L += S^ V: persistent HBM-streaming kernel for the single-pass form
-    if (upd != 1 || tc_update_persistent(h->tc, st, n, q, Sh, V, L, n, stp) != 0)
-        tc_update(h->tc, st, upd, n, q, Sh, V, L, n, stp);
-    mark(h, "update L");
+    if (fuse) {
+        // the next step's sketch, then L += S^ V fused with S = L S~_{k+1}
+        ada_draw<float>(h, St_next, h->k + 1);
+        const int rc = tc_update_next_s(st, n, q, Sh, V, L, n, St_next, S, 1, h->Spart, h->spart_cap, stp);
+        if (rc == 0) {
+            h->s_valid = true;
+        } else {
+            h->s_valid = false;
+            if (tc_update_persistent(h->tc, st, n, q, Sh, V, L, n, stp) != 0)
+                tc_update(h->tc, st, upd, n, q, Sh, V, L, n, stp);
+        }
+        mark(h, "update L + next S");
+    } else {
+        // L += S^ V: persistent HBM-streaming kernel for the single-pass form
+        if (upd != 1 || tc_update_persistent(h->tc, st, n, q, Sh, V, L, n, stp) != 0)
+            tc_update(h->tc, st, upd, n, q, Sh, V, L, n, stp);
+        mark(h, "update L");
+    }
     if (fork) {
         cudaEventRecord(h->ev_out, h->st1);
         h->st = user;
@@ -852,6 +897,7 @@ extern "C" rb_status rbfgs_import(rbfgs_t h, int what, const void *in, int64_t l
     else
         launch_copy2d<float, float>(h->st, n, n, (const float *)in, ld, (float *)h->X, n, 1.0);
     RB_CUDA(cudaMemsetAsync(h->d_status, 0, sizeof(int), h->st));
+    h->s_valid = false;
     RB_CUDA(cudaGetLastError());
     return RB_OK;
 }
@@ -860,6 +906,7 @@ extern "C" rb_status rbfgs_set_step(rbfgs_t h, uint64_t k)
 {
     if (!h) return RB_EINVAL;
     h->k = k;
+    h->s_valid = false;
     return RB_OK;
 }
 
@@ -1105,6 +1152,7 @@ extern "C" rb_status rbfgs_reset(rbfgs_t h, uint64_t seed, uint64_t stream_id)
     h->k = 0;
     h->seed = seed;
     h->stream_id = stream_id;
+    h->s_valid = false;
     RB_CUDA(cudaGetLastError());
     return RB_OK;
 }
@@ -1171,6 +1219,7 @@ extern "C" rb_status rbfgs_load_host(rbfgs_t h, const void *A_host, int64_t lda,
         launch_set_identity<double>(h->st, n, (double *)h->X, n, 1.0);
     else
         launch_set_identity<float>(h->st, n, (float *)h->X, n, 1.0f);
+    h->s_valid = false;
     RB_CUDA(cudaMemsetAsync(h->d_status, 0, sizeof(int), h->st));
     h->k = 0;
     if (h->method == RB_METHOD_RBFGS && h->sketch == RB_SKETCH_COORD_TRACE) {

@@ -55,3 +55,14 @@ int tc_num_sms();
 // ran on the tensor cores, 1 when the shape needs the generic kernel.
 int tc_update_persistent(tc_plan *p, cudaStream_t st, int n, int q, const float *ShT, const float *V, float *L,
                          int64_t ldl, const int *status);
+
+// Fused update and next sketch product (see tc_update_s.cu):
+//   L += S^ V (when do_update), then S_out = L S~_next (n x q, ld n)
+// with S~_next exact in TF32.  Spart is a workspace of at least
+// tc_update_s_workspace(n, q) floats.  Returns 0 when it ran on the tensor
+// cores, 1 when the shape is outside the kernel (q > 128, q or n not a
+// multiple of 4, unaligned pointers), < 0 on error.
+size_t tc_update_s_workspace(int n, int q);
+int tc_update_next_s(cudaStream_t st, int n, int q, const float *ShT, const float *V, float *L, int64_t ldl,
+                     const float *St_next, float *S_out, int do_update, float *Spart, size_t spart_elems,
+                     const int *status);

@@ -1,0 +1,483 @@
+// tc_update_s.cu -- AdaRBFGS factor update fused with the next step's sketch
+// product (Eq. (Cholimprov) and the first line of Algorithm 4):
+//
+//   L+ = L + S^ V               (optional: do_update = 0 only forms S)
+//   S_next = L+ S~_next         (S~_next exact in TF32: two products, L+ = hi + lo)
+//
+// Every L tile that the update streams through HBM is also the A operand of
+// its share of S_next = sum over column tiles of L+(rows, cols) S~_next(cols, :),
+// so the next step needs no separate pass over L.  Each CTA owns a contiguous
+// run of 128 x 64 tiles of L, row block by row block (as in tc_update.cu):
+//   warp 0      TMA: V tile (64 x q) and L tile (128 x 64) into a three-deep ring;
+//   warp 2      TMA: the S~_next tile (64 rows x q) into its own slot;
+//   warp 1      tcgen05.mma: L-tile update (A = S^ row block in TMEM, B = V) into
+//               one of two accumulators;
+//   warp 3      tcgen05.mma: the S_next product of each tile as soon as its L+ is
+//               in TMEM (A = L+ hi / lo, B = S~_next), chunked every 8 tiles
+//               (a thread's commits track its own MMAs, so the two streams of
+//               MMAs are ordered independently);
+//   warps 4-7   per tile: drain the update accumulator into the L tile in shared
+//               memory, TMA-store it, write L+ as hi / lo into TMEM for the S_next
+//               MMA; refill S^ in TMEM when the row block changes;
+//   warps 8-11  drain the S_next chunk accumulator, keep running sums (FP32,
+//               round-to-nearest), and write one partial 128 x q block per row
+//               block that the CTA touches; k_snext_reduce adds the partials of
+//               the CTAs that share a row block in CTA order.
+// TMEM: update accumulators [0, 128), S^ [128, 256), L+ hi [256, 320),
+// L+ lo [320, 384), S_next accumulator [384, 512).
+// All mbarrier waits are bounded; a wait that gives up records ST_TIMEOUT and
+// the CTA winds down.
+#include <algorithm>
+
+#include "tc.cuh"
+#include "tc_ptx.cuh"
+
+using namespace tcx;
+
+namespace {
+
+constexpr int UBN = 64;                      // tile columns
+constexpr int L_TILE_BYTES = 128 * UBN * 4;  // 32 KB, column-major
+constexpr int NSTAGES = 2;
+constexpr int TSLOTS = 2;                    // S~_next tiles in flight
+constexpr int SCHUNK = 8;                    // tiles per S_next accumulation chunk (512 of K)
+constexpr uint32_t COL_SH = 128, COL_LHI = 256, COL_LLO = 320, COL_SACC = 384;
+
+template <int KC>  // q padded to NQ = 32 KC
+struct SCfg {
+    static constexpr int NQ = KC * 32;
+    static constexpr int V_BYTES = KC * UBN * 128;  // KC chunks of 64 rows x 128 B
+    static constexpr int STAGE_BYTES = V_BYTES + L_TILE_BYTES;
+    static constexpr int T_BYTES = 2 * NQ * 128;     // two 32-wide K chunks of NQ rows x 128 B
+    static constexpr int SMEM = NSTAGES * STAGE_BYTES + TSLOTS * T_BYTES + 1024 + 256;
+    static_assert(SMEM <= 227 * 1024, "shared memory");
+};
+
+__device__ __forceinline__ void st16(uint32_t taddr, const uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+        "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ float hi_tf32(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+
+template <int KC>
+__global__ void __launch_bounds__(384, 1)
+k_tc_update_s(const float *__restrict__ ShT, int n, int q, const __grid_constant__ CUtensorMap tmV,
+              const __grid_constant__ CUtensorMap tmL, const __grid_constant__ CUtensorMap tmT, int ncb, int ntiles,
+              int do_update, float *Spart, int maxseg, const int *status, int *err)
+{
+    using CF = SCfg<KC>;
+    constexpr int NQ = CF::NQ;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    if (status_bad(status)) return;  // uniform across the CTA
+    unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char *stg = smem;
+    unsigned char *tsl = smem + NSTAGES * CF::STAGE_BYTES;  // S~_next tile
+    uint64_t *bars = (uint64_t *)(tsl + TSLOTS * CF::T_BYTES);
+    uint64_t *full = bars;                   // [3] V + L tile landed
+    uint64_t *sempty = bars + NSTAGES;       // [3] stage released (tile stored / read)
+    uint64_t *afull = bars + 2 * NSTAGES;    // [2] update accumulator written
+    uint64_t *aempty = afull + 2;            // [2] update accumulator drained
+    uint64_t *tfull = aempty + 2;            // [TSLOTS] S~_next tile landed
+    uint64_t *tempty = tfull + TSLOTS;       // [TSLOTS] S~_next tile read (S_next MMA done)
+    uint64_t *lfull = tempty + TSLOTS;       // L+ hi / lo written to TMEM
+    uint64_t *lempty = lfull + 1;            // L+ read (S_next MMA done)
+    uint64_t *shfull = lempty + 1;           // S^ written to TMEM
+    uint64_t *shfree = shfull + 1;           // update MMAs reading S^ done
+    uint64_t *sfull = shfree + 1;            // S_next chunk accumulated
+    uint64_t *sfree = sfull + 1;             // S_next chunk drained
+    uint32_t *tmem_slot = (uint32_t *)(sfree + 1);
+    volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int tb = (int)((long long)ntiles * blockIdx.x / gridDim.x);
+    const int te = (int)((long long)ntiles * (blockIdx.x + 1) / gridDim.x);
+    const int nt = te - tb;
+    const int rb_first = tb / ncb;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NSTAGES; ++s) {
+            mbar_init(smem_u32(&full[s]), 1);
+            mbar_init(smem_u32(&sempty[s]), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(smem_u32(&afull[b]), 1);
+            mbar_init(smem_u32(&aempty[b]), 128);
+        }
+        for (int s = 0; s < TSLOTS; ++s) {
+            mbar_init(smem_u32(&tfull[s]), 1);
+            mbar_init(smem_u32(&tempty[s]), 1);
+        }
+        mbar_init(smem_u32(lfull), 128);
+        mbar_init(smem_u32(lempty), 1);
+        mbar_init(smem_u32(shfull), 128);
+        mbar_init(smem_u32(shfree), 1);
+        mbar_init(smem_u32(sfull), 1);
+        mbar_init(smem_u32(sfree), 128);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(512u)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    // S_next chunking: tile i sits at position p = i - (first tile of its row block in this CTA's run)
+    auto seg_pos = [&](int t) { return t - max(tb, (t / ncb) * ncb); };
+    auto last_of_rb = [&](int t) { return t + 1 == te || (t + 1) / ncb != t / ncb; };
+
+    if (warp == 0) {
+        // ---------------- TMA: V and L tiles ----------------
+        if (lane == 0) {
+            const uint32_t bytes = (do_update ? CF::V_BYTES : 0) + L_TILE_BYTES;
+            for (int i = 0; i < nt; ++i) {
+                const int t = tb + i, rb = t / ncb, cb = t - rb * ncb, s = i % NSTAGES;
+                if (i >= NSTAGES && !mbar_wait(smem_u32(&sempty[s]), ((i / NSTAGES) - 1) & 1, err, abort_flag))
+                    break;
+                unsigned char *st = stg + s * CF::STAGE_BYTES;
+                const uint32_t fb = smem_u32(&full[s]);
+                mbar_expect_tx(fb, bytes);
+                if (do_update)
+                    for (int kc = 0; kc < KC; ++kc)
+                        tma_load_2d(smem_u32(st + kc * 8192), &tmV, 32 * kc, cb * UBN, fb);
+                tma_load_2d(smem_u32(st + CF::V_BYTES), &tmL, rb * 128, cb * UBN, fb);
+            }
+        }
+    } else if (warp == 2) {
+        // ---------------- TMA: S~_next tiles (rows cb * 64 .. + 63) ----------------
+        if (lane == 0) {
+            for (int i = 0; i < nt; ++i) {
+                const int t = tb + i, cb = t % ncb, ts = i % TSLOTS;
+                if (i >= TSLOTS && !mbar_wait(smem_u32(&tempty[ts]), ((i / TSLOTS) - 1) & 1, err, abort_flag)) break;
+                const uint32_t fb = smem_u32(&tfull[ts]);
+                unsigned char *tp = tsl + ts * CF::T_BYTES;
+                mbar_expect_tx(fb, CF::T_BYTES);
+                tma_load_2d(smem_u32(tp), &tmT, cb * UBN, 0, fb);
+                tma_load_2d(smem_u32(tp + NQ * 128), &tmT, cb * UBN + 32, 0, fb);
+            }
+        }
+    } else if (warp == 3) {
+        // ---------------- MMA issuer for the S_next products (own thread, own commits) ----------------
+        if (lane == 0) {
+            const uint32_t idesc_s = idesc_tf32(NQ, 0);
+            int chunk = -1;  // S_next chunk being accumulated
+            bool ok = true;
+            // S_next product of tile j (L+ of tile j in TMEM, S~_next tile j in smem)
+            auto s_mma = [&](int j) {
+                const int t = tb + j, p = seg_pos(t);
+                const bool cstart = (p % SCHUNK) == 0;
+                const bool cend = ((p + 1) % SCHUNK) == 0 || last_of_rb(t);
+                if (cstart) {
+                    ++chunk;
+                    if (chunk >= 1 && !mbar_wait(smem_u32(sfree), (chunk - 1) & 1, err, abort_flag)) {
+                        ok = false;
+                        return;
+                    }
+                }
+                const int ts = j % TSLOTS;
+                if (!mbar_wait(smem_u32(lfull), j & 1, err, abort_flag) ||
+                    !mbar_wait(smem_u32(&tfull[ts]), (j / TSLOTS) & 1, err, abort_flag)) {
+                    ok = false;
+                    return;
+                }
+                tc_fence_after();
+                const uint32_t t_u = smem_u32(tsl + ts * CF::T_BYTES);
+#pragma unroll
+                for (int kk = 0; kk < UBN / 8; ++kk) {
+                    const uint64_t db = umma_desc(t_u + (kk >> 2) * (NQ * 128) + (kk & 3) * 32, 16, 1024);
+                    mma_ts(tmem + COL_SACC, tmem + COL_LLO + 8 * kk, db, idesc_s, (cstart && kk == 0) ? 0u : 1u);
+                    mma_ts(tmem + COL_SACC, tmem + COL_LHI + 8 * kk, db, idesc_s, 1u);
+                }
+                mma_commit(smem_u32(lempty));
+                mma_commit(smem_u32(&tempty[ts]));
+                if (cend) mma_commit(smem_u32(sfull));
+            };
+            for (int j = 0; j < nt && ok; ++j) s_mma(j);
+        }
+    } else if (warp == 1) {
+        // ---------------- MMA issuer for the L-tile update ----------------
+        if (lane == 0 && do_update) {
+            const uint32_t idesc_u = idesc_tf32(UBN, 0);
+            int cur_rb = -1;
+            for (int i = 0; i < nt; ++i) {
+                const int t = tb + i, rb = t / ncb, s = i % NSTAGES, b = i & 1;
+                {
+                    if (rb != cur_rb) {
+                        const int k = rb - rb_first;  // S^ refills of this CTA
+                        if (!mbar_wait(smem_u32(shfull), k & 1, err, abort_flag)) break;
+                        cur_rb = rb;
+                    }
+                    if (!mbar_wait(smem_u32(&full[s]), (i / NSTAGES) & 1, err, abort_flag)) break;
+                    if (i >= 2 && !mbar_wait(smem_u32(&aempty[b]), ((i >> 1) - 1) & 1, err, abort_flag)) break;
+                    tc_fence_after();
+                    const uint32_t v_u = smem_u32(stg + s * CF::STAGE_BYTES);
+#pragma unroll
+                    for (int kc = 0; kc < KC; ++kc)
+#pragma unroll
+                        for (int k8 = 0; k8 < 4; ++k8) {
+                            const uint64_t db = umma_desc(v_u + kc * 8192 + k8 * 32, 16, 1024);
+                            mma_ts(tmem + (uint32_t)(b * UBN), tmem + COL_SH + 32 * kc + 8 * k8, db, idesc_u,
+                                   (kc | k8) ? 1u : 0u);
+                        }
+                    mma_commit(smem_u32(&afull[b]));
+                    if (last_of_rb(t)) mma_commit(smem_u32(shfree));
+                }
+            }
+        }
+    } else if (warp >= 4 && warp < 8) {
+        // ---------------- L tile epilogue, L+ into TMEM, S^ refills ----------------
+        const int r = threadIdx.x - 128;  // tile row = TMEM lane
+        const uint32_t lane_base = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+        bool ok = true;
+        auto load_sh = [&](int rb) {  // S^ rows of row block rb into TMEM (rows past n are zero)
+            const int k = rb - rb_first;
+            if (k >= 1 && !mbar_wait(smem_u32(shfree), (k - 1) & 1, err, abort_flag)) {
+                ok = false;
+                return;
+            }
+            tc_fence_after();
+            const int row = rb * 128 + r;
+            const float4 *src = (const float4 *)(ShT + (size_t)row * q);
+#pragma unroll
+            for (int c0 = 0; c0 < KC * 32; c0 += 16) {
+                uint32_t w[16];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int c = c0 + 4 * j;
+                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (row < n && c < q) v = src[c >> 2];  // q % 4 == 0
+                    w[4 * j] = __float_as_uint(v.x);
+                    w[4 * j + 1] = __float_as_uint(v.y);
+                    w[4 * j + 2] = __float_as_uint(v.z);
+                    w[4 * j + 3] = __float_as_uint(v.w);
+                }
+                st16(lane_base + COL_SH + c0, w);
+            }
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            tc_fence_before();
+            mbar_arrive(smem_u32(shfull));
+        };
+        if (do_update && nt > 0) load_sh(rb_first);
+        for (int i = 0; i < nt && ok; ++i) {
+            const int t = tb + i, rb = t / ncb, cb = t - rb * ncb, s = i % NSTAGES, b = i & 1;
+            // the L row first (shared memory), then the accumulator (TMEM, one wait for all loads)
+            if (!mbar_wait(smem_u32(&full[s]), (i / NSTAGES) & 1, err, abort_flag)) break;
+            float *Ls = (float *)(stg + s * CF::STAGE_BYTES + CF::V_BYTES);  // [64 cols][128 rows]
+            float lp[UBN];
+#pragma unroll
+            for (int c = 0; c < UBN; ++c) lp[c] = Ls[c * 128 + r];
+            if (do_update) {
+                if (!mbar_wait(smem_u32(&afull[b]), (i >> 1) & 1, err, abort_flag)) break;
+                tc_fence_after();
+                uint32_t v[UBN];
+                const uint32_t ta = lane_base + (uint32_t)(b * UBN);
+#pragma unroll
+                for (int c0 = 0; c0 < UBN; c0 += 16)
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+                        "%11, %12, %13, %14, %15}, [%16];"
+                        : "=r"(v[c0]), "=r"(v[c0 + 1]), "=r"(v[c0 + 2]), "=r"(v[c0 + 3]), "=r"(v[c0 + 4]),
+                          "=r"(v[c0 + 5]), "=r"(v[c0 + 6]), "=r"(v[c0 + 7]), "=r"(v[c0 + 8]), "=r"(v[c0 + 9]),
+                          "=r"(v[c0 + 10]), "=r"(v[c0 + 11]), "=r"(v[c0 + 12]), "=r"(v[c0 + 13]), "=r"(v[c0 + 14]),
+                          "=r"(v[c0 + 15])
+                        : "r"(ta + c0));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                tc_fence_before();
+                mbar_arrive(smem_u32(&aempty[b]));
+#pragma unroll
+                for (int c = 0; c < UBN; ++c) {
+                    lp[c] += __uint_as_float(v[c]);
+                    Ls[c * 128 + r] = lp[c];
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            }
+            named_bar(1, 128);
+            if (r == 0 && do_update) {  // the store's completion is awaited after the TMEM writes below
+                tma_store_2d(&tmL, smem_u32(Ls), rb * 128, cb * UBN);
+                bulk_commit();
+            }
+            // L+ of this tile as the A operand of its S_next product (after the previous one is read)
+            if (i >= 1 && !mbar_wait(smem_u32(lempty), (i - 1) & 1, err, abort_flag)) {
+                if (r == 0) bulk_wait0();
+                break;
+            }
+            tc_fence_after();
+#pragma unroll
+            for (int c0 = 0; c0 < UBN; c0 += 16) {
+                uint32_t w[16];
+#pragma unroll
+                for (int j = 0; j < 16; ++j) w[j] = __float_as_uint(lp[c0 + j]);
+                st16(lane_base + COL_LHI + c0, w);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) w[j] = __float_as_uint(lp[c0 + j] - hi_tf32(lp[c0 + j]));
+                st16(lane_base + COL_LLO + c0, w);
+            }
+            asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+            tc_fence_before();
+            mbar_arrive(smem_u32(lfull));
+            if (r == 0) {  // the stage is free once the store has read the tile (or, without update, now)
+                if (do_update) bulk_wait_read0();
+                mbar_arrive(smem_u32(&sempty[s]));
+            }
+            // the update MMAs of this row block are done once its last tile drained: refill S^
+            if (do_update && last_of_rb(t) && i + 1 < nt) load_sh(rb + 1);
+        }
+        if (r == 0) bulk_wait0();
+    } else if (warp >= 8) {
+        // ---------------- S_next chunks: running sums and partial blocks ----------------
+        const int wq = warp & 3;
+        float run[NQ];
+#pragma unroll
+        for (int j = 0; j < NQ; ++j) run[j] = 0.f;
+        int c = 0, i = 0;
+        while (i < nt) {
+            // chunk c covers tiles [i, i + len) of one row block
+            const int t = tb + i, p = seg_pos(t);
+            int len = SCHUNK - (p % SCHUNK);
+            const int rb_end = min(te, (t / ncb + 1) * ncb);
+            len = min(len, rb_end - t);
+            if (!mbar_wait(smem_u32(sfull), c & 1, err, abort_flag)) break;
+            tc_fence_after();
+            const uint32_t keep = (p == 0) ? 0u : 0xFFFFFFFFu;  // a row block starts a fresh sum
+#pragma unroll
+            for (int c0 = 0; c0 < NQ; c0 += 16) {
+                uint32_t v[16];
+                tmem_ld16(tmem + ((uint32_t)(32 * wq) << 16) + COL_SACC + c0, v);
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    run[c0 + j] = __uint_as_float(__float_as_uint(run[c0 + j]) & keep) + __uint_as_float(v[j]);
+            }
+            tc_fence_before();
+            mbar_arrive(smem_u32(sfree));
+            i += len;
+            ++c;
+            if (tb + i == rb_end) {  // row block finished: partial block (rows x NQ, column-major, ld 128)
+                const int seg = t / ncb - rb_first;
+                float *dst = Spart + ((size_t)blockIdx.x * maxseg + seg) * (128 * NQ) + 32 * wq + lane;
+#pragma unroll
+                for (int j = 0; j < NQ; ++j) dst[j * 128] = run[j];
+            }
+        }
+        tc_fence_before();
+    }
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u) : "memory");
+    }
+}
+
+// S_next (n x q, ld lds) = sum of the partial blocks of the CTAs whose tile runs
+// meet each row block, in CTA order.  Block: one row block, thread = row.
+__global__ void k_snext_reduce(int n, int q, int nq, int ncb, int ntiles, int G, int maxseg, const float *Spart,
+                               float *S, int64_t lds, const int *status)
+{
+    if (status_bad(status)) return;
+    const int rb = blockIdx.x, r = threadIdx.x, row = rb * 128 + r;
+    const long long t0 = (long long)rb * ncb, t1 = t0 + ncb;
+    auto tbeg = [&](int b) { return (long long)ntiles * b / G; };
+    int b = (int)(t0 * G / ntiles);
+    while (b + 1 < G && tbeg(b + 1) <= t0) ++b;
+    while (b > 0 && tbeg(b) > t0) --b;
+    for (int c0 = 0; c0 < q; c0 += 32) {
+        float s[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) s[j] = 0.f;
+        for (int bb = b; bb < G && tbeg(bb) < t1; ++bb) {
+            if (tbeg(bb + 1) == tbeg(bb)) continue;
+            const int seg = rb - (int)(tbeg(bb) / ncb);
+            const float *pp = Spart + ((size_t)bb * maxseg + seg) * (128 * nq) + r;
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if (c0 + j < q) s[j] += pp[(size_t)(c0 + j) * 128];
+        }
+        if (row < n)
+#pragma unroll
+            for (int j = 0; j < 32; ++j)
+                if (c0 + j < q) S[row + (int64_t)(c0 + j) * lds] = s[j];
+    }
+}
+
+template <int KC>
+int launch_update_s(cudaStream_t st, const float *ShT, int n, int q, const CUtensorMap &mv, const CUtensorMap &ml,
+                    const CUtensorMap &mt, int do_update, float *Spart, size_t spart_elems, float *S, int64_t lds,
+                    const int *status, int *err)
+{
+    using CF = SCfg<KC>;
+    static bool attr = false;
+    if (!attr) {
+        if (cudaFuncSetAttribute(k_tc_update_s<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, CF::SMEM) !=
+            cudaSuccess)
+            return -1;
+        attr = true;
+    }
+    const int nrb = (n + 127) / 128, ncb = (n + UBN - 1) / UBN;
+    const int ntiles = nrb * ncb;
+    const int grid = std::min(ntiles, tc_num_sms());
+    int maxseg = 1;
+    for (int b = 0; b < grid; ++b) {
+        const long long t0 = (long long)ntiles * b / grid, t1 = (long long)ntiles * (b + 1) / grid;
+        if (t1 > t0) maxseg = std::max(maxseg, (int)((t1 - 1) / ncb - t0 / ncb + 1));
+    }
+    if ((size_t)grid * maxseg * 128 * CF::NQ > spart_elems) return -2;
+    rb_count_launch();
+    k_tc_update_s<KC><<<grid, 384, CF::SMEM, st>>>(ShT, n, q, mv, ml, mt, ncb, ntiles, do_update, Spart, maxseg,
+                                                   status, err);
+    rb_count_launch();
+    k_snext_reduce<<<nrb, 128, 0, st>>>(n, q, CF::NQ, ncb, ntiles, grid, maxseg, Spart, S, lds, status);
+    return cudaGetLastError() == cudaSuccess ? 0 : -3;
+}
+
+}  // namespace
+
+size_t tc_update_s_workspace(int n, int q)
+{
+    // upper bound: every CTA touches at most (its tiles / tiles per row block) + 2 row blocks
+    const int nrb = (n + 127) / 128, ncb = (n + UBN - 1) / UBN, ntiles = nrb * ncb;
+    const int grid = std::min(ntiles, tc_num_sms());
+    const int per = (ntiles + grid - 1) / grid;
+    const int maxseg = per / ncb + 2;
+    return (size_t)grid * maxseg * 128 * (size_t)(((q + 31) / 32) * 32);
+}
+
+int tc_update_next_s(cudaStream_t st, int n, int q, const float *ShT, const float *V, float *L, int64_t ldl,
+                     const float *St_next, float *S_out, int do_update, float *Spart, size_t spart_elems,
+                     const int *status)
+{
+    if (q < 1 || q > 128 || (q % 4) || (ldl % 4) || (n % 4) || ((uintptr_t)ShT % 16) || ((uintptr_t)V % 16) ||
+        ((uintptr_t)L % 16) || ((uintptr_t)St_next % 16))
+        return 1;
+    CUtensorMap mv, ml, mt;
+    const int nq = ((q + 31) / 32) * 32;
+    if (!tc_make_map(&mv, V, q, n, q, 32, UBN, 1) || !tc_make_map(&ml, L, n, n, ldl, 128, UBN, 0) ||
+        !tc_make_map(&mt, St_next, n, q, n, 32, nq, 1))
+        return -4;
+    int *err = const_cast<int *>(status);
+    switch (nq / 32) {
+    case 1: return launch_update_s<1>(st, ShT, n, q, mv, ml, mt, do_update, Spart, spart_elems, S_out, n, status, err);
+    case 2: return launch_update_s<2>(st, ShT, n, q, mv, ml, mt, do_update, Spart, spart_elems, S_out, n, status, err);
+    case 3: return launch_update_s<3>(st, ShT, n, q, mv, ml, mt, do_update, Spart, spart_elems, S_out, n, status, err);
+    default:
+        return launch_update_s<4>(st, ShT, n, q, mv, ml, mt, do_update, Spart, spart_elems, S_out, n, status, err);
+    }
+}
