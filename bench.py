@@ -35,6 +35,8 @@ MAX_ITER = 20000
 # DRAM bytes (read + write) of one k_tc_update launch at n = 8192, q = 128, from one ncu capture
 # (profiles/tc_kernels_n8192_full.md); scaled by (n / 8192)^2 for other n at q = 128.
 UPDATE_TRAFFIC_N8192_Q128 = 277638912 + 208375552
+# the same for one k_tc_update_s launch (fused update + next sketch product); None until captured
+FUSED_TRAFFIC_N8192_Q128 = None
 
 
 def parse():
@@ -387,13 +389,21 @@ def main():
         for name, ms in B.rbfgs_profile_step(h):
             prof.setdefault(name, []).append(ms)
     phases = {k: statistics.median(v) for k, v in prof.items()}
-    upd_ms = phases.get("update L", float("nan"))
-    upd_bytes = 2 * 4 * n * n + 2 * 4 * n * q  # read + write L, read S^ and V
+    fused = "update L + next S" in phases
+    if fused:  # L += S^ V fused with S_next = L S~_next: read + write L; read V, S^, S~_next; write S_next
+        upd_ms = phases["update L + next S"]
+        upd_bytes = 2 * 4 * n * n + 4 * 4 * n * q
+        kern = "fused L += S^ V and S_next = L S~_next (k_tc_update_s: 1xTF32 update, 2xTF32 product)"
+        traffic = (FUSED_TRAFFIC_N8192_Q128 * (n / 8192) ** 2) if (q == 128 and FUSED_TRAFFIC_N8192_Q128) else None
+    else:
+        upd_ms = phases.get("update L", float("nan"))
+        upd_bytes = 2 * 4 * n * n + 2 * 4 * n * q  # read + write L, read S^ and V
+        kern = "rank-q update L += S^ V (k_tc_update, persistent, 1xTF32)"
+        traffic = (UPDATE_TRAFFIC_N8192_Q128 * (n / 8192) ** 2) if q == 128 else None
     achieved = upd_bytes / (upd_ms * 1e-3) / 1e9
-    roofline = {"kernel": "rank-q update L += S^ V (k_tc_update, persistent, 1xTF32)", "bound": "hbm",
+    roofline = {"kernel": kern, "bound": "hbm",
                 "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "peak_kind": f"{peak_kind} HBM copy",
-                "traffic": (UPDATE_TRAFFIC_N8192_Q128 * (n / 8192) ** 2) if q == 128 else None,
+                "peak_kind": f"{peak_kind} HBM copy", "traffic": traffic,
                 "algorithmic_bytes_per_launch": upd_bytes, "ms_per_launch": upd_ms}
     step_ms = sum(phases.values())
     # the tcgen05 GEMMs of the step against the TF32 tensor peak: MMA work = terms x 2 n^2 q
@@ -401,7 +411,8 @@ def main():
     gemm_rooflines = []
     for ph, kern, terms in (("S=LS~", "S = L S~ (k_tc_gemm, 2 x TF32)", 2),
                             ("G=AS | D core", "G = A S (k_tc_gemm, 3 x TF32, 144 SMs)", 3),
-                            ("W=G^TL | C core", "W^T = L^T G (k_tc_gemm, 3 x TF32, 144 SMs)", 3)):
+                            ("W=G^TL | C core", "W^T = L^T G (k_tc_gemm, 3 x TF32, 144 SMs)", 3),
+                            ("update L + next S", "fused update (1 x TF32) + S_next (2 x TF32), k_tc_update_s", 3)):
         if ph in phases:
             tflops = terms * 2.0 * n * n * q / (phases[ph] * 1e-3) / 1e12
             gemm_rooflines.append({"kernel": kern, "bound": "tensor", "achieved": tflops, "peak": tf32_peak,

@@ -499,8 +499,11 @@ static bool ensure_side_stream(rb_ctx *h)
 }
 
 // SMs that the stream-K GEMMs leave to the side stream while it runs the
-// Gram products and the q x q core.
+// Gram products and the q x q core: W = L^T G overlaps S^T G (three passes) and
+// C^-1 and needs 8 (with 4 the chain outlasted W); G = A S overlaps only the
+// one-pass S~^T S~ and D^-1, for which 4 suffice.
 constexpr int SIDE_SMS = 8;
+constexpr int SIDE_SMS_G = 4;
 
 // Tensor-core step.  The q x q work runs on a low-priority side stream while
 // the n x n passes run on a high-priority one; the GEMMs that overlap side
@@ -528,7 +531,7 @@ static void ada_step_tc(rb_ctx *h)
           *Di = (float *)h->Dinv;
     const int acc = (h->prec == RB_TF32) ? 1 : 3;  // split terms of the accuracy-critical products
     const int upd = (h->prec == RB_TF32X3) ? 3 : 1;
-    const int rsv = fork ? SIDE_SMS : 0;
+    const int rsv = fork ? SIDE_SMS : 0, rsv_g = fork ? SIDE_SMS_G : 0;
     cudaStream_t side = fork ? h->st2 : st;
     // V and S^ on the tensor cores: the cores write their inverses transposed
     // straight into the B operands (needs q <= 128 and 16-byte rows)
@@ -536,7 +539,7 @@ static void ada_step_tc(rb_ctx *h)
     if (tcv && !h->tc2) tcv = (h->tc2 = tc_plan_create(n, q, h->prec)) != nullptr;
     const bool fuse = tcv && upd == 1 && h->Spart;
     // the side stream's Gram products run stream-K on the SIDE_SMS SMs the main GEMMs leave free
-    const int side_rsv = std::max(0, tc_num_sms() - SIDE_SMS);
+    const int side_rsv = std::max(0, tc_num_sms() - SIDE_SMS), side_rsv_g = std::max(0, tc_num_sms() - SIDE_SMS_G);
     // sketch buffers: [S~_a | W^T | S~_b]; step k uses S~_a (k even) or S~_b (k odd) when fused
     const bool odd = fuse && (h->k & 1);
     float *St = odd ? (float *)h->Stb : (float *)h->St;
@@ -560,14 +563,14 @@ static void ada_step_tc(rb_ctx *h)
         cudaEventRecord(h->ev_sk, st);
         cudaStreamWaitEvent(side, h->ev_sk, 0);
         if (tcv) {  // S~^T S~ (products exact: S~ is TF32) -> D^-T into Bv
-            tc_gemm_nk(h->tc2, side, 1, TC_A_K, q, q, n, St, n, St, n, h->Nf, q, stp, side_rsv);
+            tc_gemm_nk(h->tc2, side, 1, TC_A_K, q, q, n, St, n, St, n, h->Nf, q, stp, side_rsv_g);
             launch_core_tr32(side, q, h->Nf, nullptr, h->Bv + dofs, 2 * q, 1.f, nullptr, 0, 0.f, h->d_status);
         } else {
             launch_gram<float>(side, n, q, q, St, n, St, n, h->part, h->N);  // S~^T S~ -> D^-1
             launch_core_ada32(side, q, h->N, nullptr, Di, nullptr, h->d_status);
         }
     }
-    tc_gemm_nk(h->tc, st, acc, TC_A_K, n, q, n, A, n, S, n, G, n, stp, rsv);  // G = A S    (A symmetric)
+    tc_gemm_nk(h->tc, st, acc, TC_A_K, n, q, n, A, n, S, n, G, n, stp, rsv_g);  // G = A S  (A symmetric)
     mark(h, fork ? "G=AS | D core" : "G=AS");
     if (fork) {
         cudaEventRecord(h->ev_g, st);
