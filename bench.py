@@ -36,7 +36,7 @@ MAX_ITER = 20000
 # (profiles/tc_kernels_n8192_full.md); scaled by (n / 8192)^2 for other n at q = 128.
 UPDATE_TRAFFIC_N8192_Q128 = 277638912 + 208375552
 # the same for one k_tc_update_s launch (fused update + next sketch product); None until captured
-FUSED_TRAFFIC_N8192_Q128 = None
+FUSED_TRAFFIC_N8192_Q128 = 285880576 + 222835968
 
 
 def parse():
@@ -410,7 +410,7 @@ def main():
     tf32_peak, tf32_kind = load_tf32_sustained_peak()
     gemm_rooflines = []
     for ph, kern, terms in (("S=LS~", "S = L S~ (k_tc_gemm, 2 x TF32)", 2),
-                            ("G=AS | D core", "G = A S (k_tc_gemm, 3 x TF32, 144 SMs)", 3),
+                            ("G=AS | D core", "G = A S (k_tc_gemm, 3 x TF32, 148 SMs)", 3),
                             ("W=G^TL | C core", "W^T = L^T G (k_tc_gemm, 3 x TF32, 144 SMs)", 3),
                             ("update L + next S", "fused update (1 x TF32) + S_next (2 x TF32), k_tc_update_s", 3)):
         if ph in phases:

@@ -388,34 +388,33 @@ k_tc_update_s(const float *__restrict__ ShT, int n, int q, const __grid_constant
 }
 
 // S_next (n x q, ld lds) = sum of the partial blocks of the CTAs whose tile runs
-// meet each row block, in CTA order.  Block: one row block, thread = row.
+// meet each row block, in CTA order.  Block: one row block and 32 columns,
+// thread = row.
 __global__ void k_snext_reduce(int n, int q, int nq, int ncb, int ntiles, int G, int maxseg, const float *Spart,
                                float *S, int64_t lds, const int *status)
 {
     if (status_bad(status)) return;
-    const int rb = blockIdx.x, r = threadIdx.x, row = rb * 128 + r;
+    const int rb = blockIdx.x, c0 = 32 * blockIdx.y, r = threadIdx.x, row = rb * 128 + r;
     const long long t0 = (long long)rb * ncb, t1 = t0 + ncb;
     auto tbeg = [&](int b) { return (long long)ntiles * b / G; };
     int b = (int)(t0 * G / ntiles);
     while (b + 1 < G && tbeg(b + 1) <= t0) ++b;
     while (b > 0 && tbeg(b) > t0) --b;
-    for (int c0 = 0; c0 < q; c0 += 32) {
-        float s[32];
+    float s[32];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) s[j] = 0.f;
-        for (int bb = b; bb < G && tbeg(bb) < t1; ++bb) {
-            if (tbeg(bb + 1) == tbeg(bb)) continue;
-            const int seg = rb - (int)(tbeg(bb) / ncb);
-            const float *pp = Spart + ((size_t)bb * maxseg + seg) * (128 * nq) + r;
+    for (int j = 0; j < 32; ++j) s[j] = 0.f;
+    for (int bb = b; bb < G && tbeg(bb) < t1; ++bb) {
+        if (tbeg(bb + 1) == tbeg(bb)) continue;
+        const int seg = rb - (int)(tbeg(bb) / ncb);
+        const float *pp = Spart + ((size_t)bb * maxseg + seg) * (128 * nq) + (size_t)c0 * 128 + r;
 #pragma unroll
-            for (int j = 0; j < 32; ++j)
-                if (c0 + j < q) s[j] += pp[(size_t)(c0 + j) * 128];
-        }
-        if (row < n)
-#pragma unroll
-            for (int j = 0; j < 32; ++j)
-                if (c0 + j < q) S[row + (int64_t)(c0 + j) * lds] = s[j];
+        for (int j = 0; j < 32; ++j)
+            if (c0 + j < q) s[j] += pp[(size_t)j * 128];
     }
+    if (row < n)
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            if (c0 + j < q) S[row + (int64_t)(c0 + j) * lds] = s[j];
 }
 
 template <int KC>
@@ -444,7 +443,8 @@ int launch_update_s(cudaStream_t st, const float *ShT, int n, int q, const CUten
     k_tc_update_s<KC><<<grid, 384, CF::SMEM, st>>>(ShT, n, q, mv, ml, mt, ncb, ntiles, do_update, Spart, maxseg,
                                                    status, err);
     rb_count_launch();
-    k_snext_reduce<<<nrb, 128, 0, st>>>(n, q, CF::NQ, ncb, ntiles, grid, maxseg, Spart, S, lds, status);
+    k_snext_reduce<<<dim3(nrb, CF::NQ / 32), 128, 0, st>>>(n, q, CF::NQ, ncb, ntiles, grid, maxseg, Spart, S, lds,
+                                                          status);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
