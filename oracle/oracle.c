@@ -615,6 +615,63 @@ int orc_rbfgs_run(int n, const double *A, double *X, int q, int kind, uint64_t s
     return done;
 }
 
+/*
+ * Approximate inverse preconditioning step, Eq. (BFGSas) of Sec. 8 (the
+ * nonsymmetric row variant, Algorithm 1, with W = A^-1 for SPD A):
+ *   X+ = X + S (S^T A S)^-1 S^T (I - A X),
+ * computed as G = A S, Lambda = (S^T G)^-1 (Cholesky), X+ = X + S Lambda (S^T - G^T X)
+ * (S^T A = G^T for symmetric A).  X need not be symmetric.  Returns -1
+ * (X untouched) when S^T A S is not positive definite.
+ */
+int orc_aip_step(int n, const double *A, double *X, const double *S, int q)
+{
+    size_t nq = (size_t)n * q, qq = (size_t)q * q;
+    double *G = (double *)malloc(sizeof(double) * nq);
+    double *M = (double *)malloc(sizeof(double) * qq);
+    double *Lam = (double *)malloc(sizeof(double) * qq);
+    double *R = (double *)malloc(sizeof(double) * nq); /* q x n: S^T - G^T X */
+    double *V = (double *)malloc(sizeof(double) * nq); /* q x n: Lambda R   */
+    int rc = 0;
+    mm_nn(n, q, n, A, S, G); /* G = A S     */
+    mm_tn(q, q, n, S, G, M); /* M = S^T A S */
+    if (orc_cholesky(q, M) != 0) {
+        rc = -1;
+        goto out;
+    }
+    inverse_from_cholesky(q, M, Lam);
+    mm_tn(q, n, n, G, X, R); /* G^T X */
+#pragma omp parallel for schedule(static)
+    for (int j = 0; j < n; ++j)
+        for (int c = 0; c < q; ++c) R[IDX(c, j, q)] = S[IDX(j, c, n)] - R[IDX(c, j, q)];
+    mm_nn(q, n, q, Lam, R, V);
+#pragma omp parallel for schedule(static)
+    for (int j = 0; j < n; ++j)
+        for (int i = 0; i < n; ++i) {
+            double acc = 0.0;
+            for (int c = 0; c < q; ++c) acc += S[IDX(i, c, n)] * V[IDX(c, j, q)];
+            X[IDX(i, j, n)] += acc;
+        }
+out:
+    free(G); free(M); free(Lam); free(R); free(V);
+    return rc;
+}
+
+/* Run steps k0 .. k0+nsteps-1 of the AIP update (kind 0 gauss, 1 coord trace). */
+int orc_aip_run(int n, const double *A, double *X, int q, int kind, uint64_t seed, uint64_t stream,
+                uint64_t k0, int nsteps)
+{
+    double *S = (double *)malloc(sizeof(double) * (size_t)n * q);
+    int done = 0;
+    for (int s = 0; s < nsteps; ++s) {
+        int qk;
+        draw_sketch(kind, A, n, q, seed, stream, k0 + (uint64_t)s, S, &qk);
+        if (orc_aip_step(n, A, X, S, qk) != 0) break;
+        ++done;
+    }
+    free(S);
+    return done;
+}
+
 /* Run steps k0 .. k0+nsteps-1 of AdaRBFGS (kind 0 gauss, kind 2 cols). */
 int orc_adarbfgs_run(int n, const double *A, double *L, int q, int kind, uint64_t seed,
                      uint64_t stream, uint64_t k0, int nsteps)

@@ -38,6 +38,8 @@ def lib():
             "orc_adarbfgs_step": (i, [i, p, p, p, i]),
             "orc_rbfgs_run": (i, [i, p, p, i, i, u64, u64, u64, i, i]),
             "orc_adarbfgs_run": (i, [i, p, p, i, i, u64, u64, u64, i]),
+            "orc_aip_step": (i, [i, p, p, p, i]),
+            "orc_aip_run": (i, [i, p, p, i, i, u64, u64, u64, i]),
             "orc_ns_step": (None, [i, p, p]),
             "orc_power_norm": (d, [i, p, i]),
             "orc_ns_init": (None, [i, p, d, p]),
@@ -152,6 +154,21 @@ def adarbfgs_run(A, L0, q, kind, seed, stream, k0, nsteps):
     L = _f64(L0).copy(order="F")
     done = lib().orc_adarbfgs_run(A.shape[0], _ptr(A), _ptr(L), q, kind, seed, stream, k0, nsteps)
     return done, L
+
+
+def aip_step(A, X, S):
+    """One step of Eq. (BFGSas): X+ = X + S (S^T A S)^-1 S^T (I - A X)."""
+    A, S = _f64(A), _f64(S)
+    X = _f64(X).copy(order="F")
+    rc = lib().orc_aip_step(A.shape[0], _ptr(A), _ptr(X), _ptr(S), S.shape[1])
+    return rc, X
+
+
+def aip_run(A, X0, q, kind, seed, stream, k0, nsteps):
+    A = _f64(A)
+    X = _f64(X0).copy(order="F")
+    done = lib().orc_aip_run(A.shape[0], _ptr(A), _ptr(X), q, kind, seed, stream, k0, nsteps)
+    return done, X
 
 
 def ns_step(A, X):

@@ -289,6 +289,85 @@ def test_rbfgs_coordinate_rate_bound():
 
 
 # --------------------------------------------------------------------------
+# Approximate inverse preconditioning, Eq. (BFGSas) (Sec. 8, Algorithm 1 with W = A^-1)
+# --------------------------------------------------------------------------
+def test_aip_sketch_equation_and_nonsymmetric_iterate():
+    # S^T A X+ = S^T (the row variant's constraint), and X+ is not symmetric in general
+    n, q = 40, 6
+    A, _, _ = _spd(n, 50.0, 31)
+    rng = np.random.default_rng(4)
+    X = rng.standard_normal((n, n)) * 0.05
+    S = orc.gauss_sketch(11, 0, 0, n, q)
+    rc, X1 = orc.aip_step(A, X, S)
+    assert rc == 0
+    assert np.allclose(S.T @ A @ X1, S.T, atol=1e-10)
+    assert np.max(np.abs(X1 - X1.T)) > 1e-3
+
+
+def test_aip_is_the_constrain_and_approximate_minimiser():
+    # Sec. 8: X+ = argmin ||A^{1/2} X A^{1/2} - I||_F over X = X_k + S Y^T.  Brute force: with
+    # B = A^{1/2} S and Z = Y^T A^{1/2} (any q x n), minimise ||E0 + B Z||_F by least squares.
+    n, q = 24, 5
+    A, U, lam = _spd(n, 30.0, 32)
+    Ah = _sqrt_spd(U, lam)
+    Ahinv = (U / np.sqrt(lam)[None, :]) @ U.T
+    rng = np.random.default_rng(5)
+    X = rng.standard_normal((n, n)) * 0.1
+    S = rng.standard_normal((n, q))
+    E0 = Ah @ X @ Ah - np.eye(n)
+    Bm = Ah @ S
+    Z, *_ = np.linalg.lstsq(Bm, -E0, rcond=None)
+    Xstar = X + S @ Z @ Ahinv
+    rc, X1 = orc.aip_step(A, X, S)
+    assert rc == 0
+    assert np.max(np.abs(X1 - Xstar)) <= 1e-9 * max(1.0, np.max(np.abs(Xstar)))
+
+
+def test_aip_error_never_increases_and_one_step_inverse():
+    # E+ = (I - P) E with P = A^{1/2} S (S^T A S)^-1 S^T A^{1/2} an orthogonal projection
+    n, q = 30, 4
+    A, U, lam = _spd(n, 100.0, 33)
+    Ah = _sqrt_spd(U, lam)
+    X = np.eye(n)
+    for k in range(25):
+        S = orc.gauss_sketch(12, 0, k, n, q)
+        before = _fa_err(Ah, X)
+        rc, X = orc.aip_step(A, X, S)
+        assert rc == 0
+        assert _fa_err(Ah, X) <= before * (1 + 1e-12)
+    # q = n with an invertible sketch: X_1 = A^-1 from any X_0 (Gauss-Jordan brute force)
+    Ainv = orc.gauss_jordan(A)
+    rc, X1 = orc.aip_step(A, np.ones((n, n)), orc.gauss_sketch(13, 0, 0, n, n))
+    assert rc == 0 and np.allclose(X1, Ainv, rtol=1e-8, atol=1e-8 * np.abs(Ainv).max())
+    # the inverse is a fixed point
+    rc, X2 = orc.aip_step(A, Ainv, orc.gauss_sketch(14, 0, 0, n, q))
+    assert np.allclose(X2, Ainv, atol=1e-10 * np.abs(Ainv).max())
+
+
+def test_aip_coordinate_rate_bound():
+    # Eq. (BBonv): block coordinates with p_b = block trace / Tr A (the stacked sketch is a
+    # permutation) give E||A^{1/2} X_k A^{1/2} - I||^2_F <= (1 - lambda_min(A)/Tr(A))^k ||..X_0..||^2
+    n, q, k, seeds = 12, 3, 30, 300
+    A, U, lam = _spd(n, 8.0, 34)
+    Ah = _sqrt_spd(U, lam)
+    rho = 1.0 - lam.min() / lam.sum()
+    e0 = _fa_err(Ah, np.eye(n)) ** 2
+    errs = []
+    for s in range(seeds):
+        done, X = orc.aip_run(A, np.eye(n), q, orc.SKETCH_COORD_TRACE, s, 0, 0, k)
+        assert done == k
+        errs.append(_fa_err(Ah, X) ** 2)
+    assert np.mean(errs) <= rho ** k * e0
+    # a coordinate step changes only the rows of the drawn block
+    b, first, size = orc.coord_trace_block(A, q, 99, 0, 0)
+    X0 = np.eye(n) * 2.0
+    _, X1 = orc.aip_run(A, X0, q, orc.SKETCH_COORD_TRACE, 99, 0, 0, 1)
+    mask = np.ones(n, bool)
+    mask[first:first + size] = False
+    assert np.array_equal(X1[mask], X0[mask])
+
+
+# --------------------------------------------------------------------------
 # AdaRBFGS (Eq. (Cholimprov), Algorithm 4)
 # --------------------------------------------------------------------------
 def test_adarbfgs_factor_reproduces_rbfgs_iterate():
