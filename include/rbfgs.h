@@ -75,7 +75,13 @@ typedef enum {
     RB_SKETCH_COORD_UNIFORM = 2   /* AdaRBFGS_cols: q distinct coordinates, uniform (Sec. 10) */
 } rb_sketch;
 
-typedef enum { RB_METHOD_RBFGS = 0, RB_METHOD_ADARBFGS = 1, RB_METHOD_NS = 2, RB_METHOD_MR = 3 } rb_method;
+typedef enum {
+    RB_METHOD_RBFGS = 0,
+    RB_METHOD_ADARBFGS = 1,
+    RB_METHOD_NS = 2,
+    RB_METHOD_MR = 3,
+    RB_METHOD_AIP = 4 /* approximate inverse preconditioning, Eq. (BFGSas) */
+} rb_method;
 
 typedef enum { RB_WHAT_X = 0, RB_WHAT_L = 1 } rb_what;
 
@@ -113,6 +119,21 @@ rb_status rbfgs_init(rbfgs_t *h, int n, const void *A_dev, int64_t lda, int a_is
  * equals Eq. (qunac).  Asynchronous.  The handle must be an RBFGS handle.
  */
 rb_status rbfgs_step(rbfgs_t h, int nsteps);
+
+/*
+ * nsteps steps of the approximate inverse preconditioning update, Eq.
+ * (BFGSas) of Sec. 8 (the nonsymmetric row variant, Algorithm 1, with
+ * W = A^-1 for SPD A):  X+ = X + S (S^T A S)^-1 S^T (I - A X),  computed as
+ * G = A S, Lambda = (S^T G)^-1 (Cholesky in FP64), W = G^T X,
+ * X += S Lambda (S^T - W).  The iterate is not symmetric in general; with a
+ * coordinate block C only the rows C of X change.  Sketches as for RBFGS
+ * (RB_SKETCH_GAUSS or RB_SKETCH_COORD_TRACE, q <= 64); all precisions run
+ * on CUDA cores (FP64 for RB_FP64, FP32 otherwise).  Asynchronous.  The
+ * handle must be created with opts.method = RB_METHOD_AIP (X0 = I).
+ * Errors: RB_EINVAL; a breakdown of S^T A S is reported as RB_ENOTSPD by the
+ * next synchronising call.
+ */
+rb_status aip_step(rbfgs_t h, int nsteps);
 
 /*
  * nsteps AdaRBFGS steps (Algorithm 4, Eq. (Cholimprov)): draw S~_k,

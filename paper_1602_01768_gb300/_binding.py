@@ -15,7 +15,7 @@ RB_EINVAL, RB_ENOMEM, RB_ECUDA, RB_ENOTSPD, RB_ENONFINITE, RB_ETIMEOUT, RB_EUNSU
 
 RB_FP64, RB_FP32, RB_TF32, RB_TF32X3, RB_MIXED = 0, 1, 2, 3, 4
 RB_SKETCH_GAUSS, RB_SKETCH_COORD_TRACE, RB_SKETCH_COORD_UNIFORM = 0, 1, 2
-RB_METHOD_RBFGS, RB_METHOD_ADARBFGS, RB_METHOD_NS, RB_METHOD_MR = 0, 1, 2, 3
+RB_METHOD_RBFGS, RB_METHOD_ADARBFGS, RB_METHOD_NS, RB_METHOD_MR, RB_METHOD_AIP = 0, 1, 2, 3, 4
 RB_WHAT_X, RB_WHAT_L = 0, 1
 
 PREC = {"fp64": RB_FP64, "fp32": RB_FP32, "tf32": RB_TF32, "tf32x3": RB_TF32X3, "mixed": RB_MIXED}
@@ -42,6 +42,7 @@ _SIGS = {
     "rbfgs_status_string": (C.c_char_p, [C.c_int]),
     "rbfgs_init": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64, C.c_int, C.c_void_p, C.c_void_p]),
     "rbfgs_step": (C.c_int, [C.c_void_p, C.c_int]),
+    "aip_step": (C.c_int, [C.c_void_p, C.c_int]),
     "adarbfgs_step": (C.c_int, [C.c_void_p, C.c_int]),
     "rbfgs_residual": (C.c_int, [C.c_void_p, C.c_int, C.c_uint64, C.c_void_p]),
     "rbfgs_solve": (C.c_int, [C.c_void_p, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p,
@@ -151,6 +152,10 @@ def rbfgs_init(n, A_dev, lda, a_is_fp64, opts, stream=0):
 
 def rbfgs_step(h, nsteps):
     return _check(_lib().rbfgs_step(h, nsteps), "rbfgs_step")
+
+
+def aip_step(h, nsteps):
+    return _check(_lib().aip_step(h, nsteps), "aip_step")
 
 
 def adarbfgs_step(h, nsteps):

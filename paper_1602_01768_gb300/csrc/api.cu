@@ -261,6 +261,9 @@ static rb_status alloc_common(rb_ctx *h)
     return RB_OK;
 }
 
+// methods that iterate on X with the RBFGS sketches (Gaussian or trace-weighted blocks)
+static bool x_sketch_method(int m) { return m == RB_METHOD_RBFGS || m == RB_METHOD_AIP; }
+
 static rb_status alloc_sketch_workspace(rb_ctx *h)
 {
     const size_t n = h->n, q = h->q, e = h->esz;
@@ -296,7 +299,7 @@ static rb_status alloc_sketch_workspace(rb_ctx *h)
     RB_TRY(rb_alloc(&h->Tm, sizeof(double) * q * q));
     RB_TRY(rb_alloc(&h->blk, sizeof(int) * 2));
     RB_TRY(rb_alloc(&h->idx, sizeof(int) * q));
-    if (h->method == RB_METHOD_RBFGS) RB_TRY(rb_alloc(&h->P3, 3 * nq));
+    if (x_sketch_method(h->method)) RB_TRY(rb_alloc(&h->P3, 3 * nq));
     return RB_OK;
 }
 
@@ -308,11 +311,11 @@ extern "C" rb_status rbfgs_init(rbfgs_t *out, int n, const void *A_dev, int64_t 
     if (!out || !A_dev || !opts || n < 1 || lda < n) return RB_EINVAL;
     *out = nullptr;
     const int method = opts->method, sketch = opts->sketch, q = opts->q, prec = opts->prec;
-    if (method != RB_METHOD_RBFGS && method != RB_METHOD_ADARBFGS) return RB_EINVAL;
+    if (!x_sketch_method(method) && method != RB_METHOD_ADARBFGS) return RB_EINVAL;
     if (!prec_ok(prec)) return RB_EINVAL;
     if (q < 1 || q > n || q > 128) return RB_EINVAL;
-    if (method == RB_METHOD_RBFGS && q > 64) return RB_EUNSUPPORTED;  // RBFGS core holds 3 q x q in smem
-    if (method == RB_METHOD_RBFGS && sketch != RB_SKETCH_GAUSS && sketch != RB_SKETCH_COORD_TRACE)
+    if (x_sketch_method(method) && q > 64) return RB_EUNSUPPORTED;  // the RBFGS core holds 3 q x q in smem
+    if (x_sketch_method(method) && sketch != RB_SKETCH_GAUSS && sketch != RB_SKETCH_COORD_TRACE)
         return RB_EUNSUPPORTED;
     if (method == RB_METHOD_ADARBFGS && sketch != RB_SKETCH_GAUSS && sketch != RB_SKETCH_COORD_UNIFORM)
         return RB_EUNSUPPORTED;
@@ -338,7 +341,7 @@ extern "C" rb_status rbfgs_init(rbfgs_t *out, int n, const void *A_dev, int64_t 
         else
             launch_set_identity<float>(h->st, n, (float *)h->X, n, 1.0f);
         if ((s = alloc_sketch_workspace(h)) != RB_OK) break;
-        if (method == RB_METHOD_RBFGS && sketch == RB_SKETCH_COORD_TRACE)
+        if (x_sketch_method(method) && sketch == RB_SKETCH_COORD_TRACE)
             if ((s = build_trace_weights(h)) != RB_OK) break;
         if (!h->f64 && prec != RB_FP32) {
             h->tc = tc_plan_create(n, q, prec);
@@ -427,6 +430,72 @@ extern "C" rb_status rbfgs_step(rbfgs_t h, int nsteps)
                 rbfgs_step_gauss<double>(h);
             else
                 rbfgs_step_gauss<float>(h);
+        }
+        ++h->k;
+    }
+    RB_CUDA(cudaGetLastError());
+    return RB_OK;
+}
+
+// Approximate inverse preconditioning, Eq. (BFGSas) (Sec. 8; Algorithm 1 with
+// W = A^-1): X+ = X + S Lambda (S^T - G^T X), G = A S, Lambda = (S^T G)^-1.
+template <typename T>
+static void aip_step_gauss(rb_ctx *h)
+{
+    const int n = h->n, q = h->q;
+    cudaStream_t st = h->st;
+    const int *stp = h->d_status;
+    T *A = (T *)h->A, *X = (T *)h->X, *S = (T *)h->P3, *G = (T *)h->G;
+    T *W = (T *)h->Y, *V = (T *)h->V, *Lam = (T *)h->Lam;  // W, V: q x n (ld q)
+    launch_gauss_sketch<T>(st, n, q, h->seed, h->stream_id, h->k, S, n);
+    mark(h, "sketch");
+    gemm_simt<T>(st, false, false, n, q, n, T(1), A, n, S, n, T(0), G, n, stp);   // G = A S
+    mark(h, "G=AS");
+    launch_gram<T>(st, n, q, q, S, n, G, n, h->part, h->M);                        // M = S^T A S
+    launch_core_rbfgs<T>(st, q, h->M, h->M, Lam, (T *)h->B1, h->d_status);        // Lambda = M^-1
+    mark(h, "gram + core");
+    gemm_simt<T>(st, true, false, q, n, n, T(1), G, n, X, n, T(0), W, q, stp);    // W = G^T X
+    mark(h, "W=G^TX");
+    gemm_simt<T>(st, false, true, q, n, q, T(1), Lam, q, S, n, T(0), V, q, stp);  // V = Lambda S^T
+    gemm_simt<T>(st, false, false, q, n, q, T(-1), Lam, q, W, q, T(1), V, q, stp);  //   - Lambda W
+    mark(h, "V");
+    gemm_simt<T>(st, false, false, n, n, q, T(1), S, n, V, q, T(1), X, n, stp);   // X += S V
+    mark(h, "update X");
+}
+
+template <typename T>
+static void aip_step_coord(rb_ctx *h)
+{
+    const int n = h->n, q = h->q;
+    cudaStream_t st = h->st;
+    const int *stp = h->d_status;
+    T *A = (T *)h->A, *X = (T *)h->X, *G = (T *)h->G;
+    T *W = (T *)h->Y, *V = (T *)h->V, *Lam = (T *)h->Lam;
+    launch_coord_trace_draw(st, n, q, h->nb, h->P, h->seed, h->stream_id, h->k, h->blk);
+    launch_coord_gather<T>(st, n, q, A, n, h->blk, G, n, h->M, stp);               // G = A[:, C], M = A[C, C]
+    launch_core_rbfgs<T>(st, q, h->M, h->M, Lam, (T *)h->B1, h->d_status);        // Lambda = M^-1 (padded)
+    mark(h, "draw + gather + core");
+    gemm_simt<T>(st, true, false, q, n, n, T(1), G, n, X, n, T(0), W, q, stp);    // W = G^T X
+    mark(h, "W=G^TX");
+    gemm_simt<T>(st, false, false, q, n, q, T(-1), Lam, q, W, q, T(0), V, q, stp); // V = -Lambda W
+    launch_aip_coord<T>(st, n, q, h->blk, Lam, V, q, X, n, stp);                  // + Lambda I[C,:]; X[C,:] += V
+    mark(h, "update rows");
+}
+
+extern "C" rb_status aip_step(rbfgs_t h, int nsteps)
+{
+    if (!h || nsteps < 0 || h->method != RB_METHOD_AIP) return RB_EINVAL;
+    for (int s = 0; s < nsteps; ++s) {
+        if (h->sketch == RB_SKETCH_COORD_TRACE) {
+            if (h->f64)
+                aip_step_coord<double>(h);
+            else
+                aip_step_coord<float>(h);
+        } else {
+            if (h->f64)
+                aip_step_gauss<double>(h);
+            else
+                aip_step_gauss<float>(h);
         }
         ++h->k;
     }
@@ -824,7 +893,7 @@ extern "C" rb_status rbfgs_footprint(int n, const rb_opts *opts, size_t *bytes)
     b += 10 * (size_t)n * q * e + 4 * q * q * 8;          // panels and q x q matrices
     b += (size_t)((n + 127) / 128) * q * q * 8;           // Gram chunk partials
     b += 3 * (size_t)n * 1024 * e;                        // residual workspace (<= 1024 columns)
-    if (opts->method == RB_METHOD_RBFGS) b += 3 * (size_t)n * q * e;
+    if (x_sketch_method(opts->method)) b += 3 * (size_t)n * q * e;
     b += 2 * (size_t)n * q * e;                           // tensor-core operand splits
     *bytes = b + (1u << 20);
     return RB_OK;
@@ -842,6 +911,8 @@ extern "C" rb_status rbfgs_solve(rbfgs_t h, double tol, int max_iter, int check_
         rb_status s = RB_OK;
         if (h->method == RB_METHOD_RBFGS)
             s = rbfgs_step(h, chunk);
+        else if (h->method == RB_METHOD_AIP)
+            s = aip_step(h, chunk);
         else if (h->method == RB_METHOD_ADARBFGS)
             s = adarbfgs_step(h, chunk);
         else if (h->method == RB_METHOD_NS)
@@ -927,7 +998,7 @@ extern "C" rb_status rbfgs_draw_sketch(rbfgs_t h, uint64_t k, void *out, int64_t
 {
     if (!h || !out || ld < h->n || h->q < 1) return RB_EINVAL;
     const int n = h->n, q = h->q;
-    if (h->method == RB_METHOD_RBFGS && h->sketch == RB_SKETCH_COORD_TRACE) {
+    if (x_sketch_method(h->method) && h->sketch == RB_SKETCH_COORD_TRACE) {
         if (h->f64)
             coord_block_matrix<double>(h, k, (double *)out, ld);
         else
@@ -1146,7 +1217,7 @@ extern "C" rb_status mr_step(rbfgs_t h, int nsteps)
 
 extern "C" rb_status rbfgs_reset(rbfgs_t h, uint64_t seed, uint64_t stream_id)
 {
-    if (!h || (h->method != RB_METHOD_RBFGS && h->method != RB_METHOD_ADARBFGS)) return RB_EINVAL;
+    if (!h || (!x_sketch_method(h->method) && h->method != RB_METHOD_ADARBFGS)) return RB_EINVAL;
     if (h->f64)
         launch_set_identity<double>(h->st, h->n, (double *)h->X, h->n, 1.0);
     else
@@ -1177,6 +1248,8 @@ extern "C" rb_status rbfgs_profile_step(rbfgs_t h, double *ms, const char **name
     rb_status s;
     if (h->method == RB_METHOD_RBFGS)
         s = rbfgs_step(h, 1);
+    else if (h->method == RB_METHOD_AIP)
+        s = aip_step(h, 1);
     else if (h->method == RB_METHOD_ADARBFGS)
         s = adarbfgs_step(h, 1);
     else if (h->method == RB_METHOD_NS)
@@ -1200,7 +1273,7 @@ extern "C" rb_status rbfgs_profile_step(rbfgs_t h, double *ms, const char **name
 
 extern "C" rb_status rbfgs_load_host(rbfgs_t h, const void *A_host, int64_t lda, int a_is_fp64)
 {
-    if (!h || !A_host || lda < h->n || (h->method != RB_METHOD_RBFGS && h->method != RB_METHOD_ADARBFGS))
+    if (!h || !A_host || lda < h->n || (!x_sketch_method(h->method) && h->method != RB_METHOD_ADARBFGS))
         return RB_EINVAL;
     const int n = h->n;
     const size_t in_esz = a_is_fp64 ? 8 : 4;
@@ -1225,7 +1298,7 @@ extern "C" rb_status rbfgs_load_host(rbfgs_t h, const void *A_host, int64_t lda,
     h->s_valid = false;
     RB_CUDA(cudaMemsetAsync(h->d_status, 0, sizeof(int), h->st));
     h->k = 0;
-    if (h->method == RB_METHOD_RBFGS && h->sketch == RB_SKETCH_COORD_TRACE) {
+    if (x_sketch_method(h->method) && h->sketch == RB_SKETCH_COORD_TRACE) {
         rb_freet(h->P);
         RB_TRY(build_trace_weights(h));
     }

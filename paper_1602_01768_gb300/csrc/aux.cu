@@ -356,3 +356,44 @@ template void launch_power_iteration<float>(cudaStream_t, int, const float *, in
                                             double *);
 template void launch_power_iteration<double>(cudaStream_t, int, const double *, int64_t, int, double *, double *,
                                              double *);
+
+// ---------------------------------------------------------------------------
+// Approximate inverse preconditioning, Eq. (BFGSas), with a coordinate block
+// C = {first, .., first + size - 1}: S^T = I[C, :], so Lambda S^T adds the
+// columns of Lambda into columns C of V, and X += S V changes rows C only.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_aip_add_lam(int q, const int *blk, const T *Lam, T *V, int64_t ldv, const int *status)
+{
+    if (status_bad(status)) return;
+    const int first = blk[0], size = blk[1];
+    const int c = threadIdx.x, j = blockIdx.x;
+    if (c < q && j < size) V[c + (int64_t)(first + j) * ldv] += Lam[c + (int64_t)j * q];
+}
+
+template <typename T>
+__global__ void k_aip_update_rows(int n, const int *blk, const T *V, int64_t ldv, T *X, int64_t ldx,
+                                  const int *status)
+{
+    if (status_bad(status)) return;
+    const int first = blk[0], size = blk[1];
+    const int j = blockIdx.x * blockDim.y + threadIdx.y, i = threadIdx.x;
+    if (j < n && i < size) X[(first + i) + (int64_t)j * ldx] += V[i + (int64_t)j * ldv];
+}
+
+template <typename T>
+void launch_aip_coord(cudaStream_t st, int n, int q, const int *blk, const T *Lam, T *V, int64_t ldv, T *X,
+                      int64_t ldx, const int *status)
+{
+    rb_count_launch();
+    k_aip_add_lam<T><<<q, std::max(32, ((q + 31) / 32) * 32), 0, st>>>(q, blk, Lam, V, ldv, status);
+    const int ty = std::max(1, 256 / std::max(1, ((q + 31) / 32) * 32));
+    dim3 blkdim(((q + 31) / 32) * 32, ty);
+    rb_count_launch();
+    k_aip_update_rows<T><<<(n + ty - 1) / ty, blkdim, 0, st>>>(n, blk, V, ldv, X, ldx, status);
+}
+template void launch_aip_coord<float>(cudaStream_t, int, int, const int *, const float *, float *, int64_t, float *,
+                                      int64_t, const int *);
+template void launch_aip_coord<double>(cudaStream_t, int, int, const int *, const double *, double *, int64_t,
+                                       double *, int64_t, const int *);
+

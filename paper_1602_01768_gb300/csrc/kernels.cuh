@@ -52,6 +52,10 @@ void launch_coord_gather(cudaStream_t, int n, int q, const T *A, int64_t lda, co
                          double *Mpad, const int *status);
 template <typename T>
 void launch_coord_add_b1(cudaStream_t, int q, const int *blk, const T *B1, T *W, int64_t ldw, const int *status);
+// AIP with a coordinate block: V[:, C] += Lambda, then X[C, :] += V (first size rows).
+template <typename T>
+void launch_aip_coord(cudaStream_t, int n, int q, const int *blk, const T *Lam, T *V, int64_t ldv, T *X, int64_t ldx,
+                      const int *status);
 template <typename T>
 void launch_coord_update(cudaStream_t, int n, int q, const int *blk, const T *W, int64_t ldw, T *X, int64_t ldx,
                          const int *status);

@@ -131,6 +131,46 @@ def test_rbfgs_coordinate_fp64_parity():
         B.rbfgs_destroy(h)
 
 
+# --------------------------------------------------------------------------
+# Approximate inverse preconditioning, Eq. (BFGSas)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("sketch,kind,n,q", [(B.RB_SKETCH_GAUSS, orc.SKETCH_GAUSS, 256, 8),
+                                             (B.RB_SKETCH_GAUSS, orc.SKETCH_GAUSS, 203, 7),
+                                             (B.RB_SKETCH_COORD_TRACE, orc.SKETCH_COORD_TRACE, 150, 16)])
+def test_aip_fp64_parity(sketch, kind, n, q):
+    # relative Frobenius error of X against the FP64 oracle <= 1e-10 at every check
+    A, _, _ = wl.spd_spectrum(n, 100.0, 41)
+    h = _handle(A, B.RB_METHOD_AIP, sketch, q, B.RB_FP64, seed=9)
+    X = np.eye(n)
+    done = 0
+    try:
+        for chk in (1, 20, 150):
+            B.aip_step(h, chk - done)
+            _, X = orc.aip_run(A, X, q, kind, 9, 0, done, chk - done)
+            done = chk
+            assert rel(export(h, n, B.RB_FP64, B.RB_WHAT_X), X) <= 1e-10, chk
+    finally:
+        B.rbfgs_destroy(h)
+
+
+def test_aip_fp32_parity_and_residual():
+    # FP32 storage: <= 1e-4 relative along 60 steps (u = 6e-8 accumulated over the steps and
+    # n-length dot products), and the library's exact residual matches the oracle's
+    n, q = 512, 32
+    A, _, _ = wl.spd_spectrum(n, 50.0, 42)
+    h = _handle(A, B.RB_METHOD_AIP, B.RB_SKETCH_GAUSS, q, B.RB_FP32, seed=10)
+    try:
+        B.aip_step(h, 60)
+        _, X = orc.aip_run(A, np.eye(n), q, orc.SKETCH_GAUSS, 10, 0, 0, 60)
+        Xg = export(h, n, B.RB_FP32, B.RB_WHAT_X)
+        assert rel(Xg, X) <= 1e-4
+        r_gpu = B.rbfgs_residual(h, 0, 0)
+        r_orc = orc.residual(A, X)
+        assert abs(r_gpu - r_orc) <= 1e-3 * r_orc + 1e-6
+    finally:
+        B.rbfgs_destroy(h)
+
+
 @pytest.mark.parametrize("sketch,kind", [(B.RB_SKETCH_GAUSS, orc.SKETCH_GAUSS),
                                          (B.RB_SKETCH_COORD_UNIFORM, orc.SKETCH_COORD_UNIFORM)])
 def test_adarbfgs_fp64_parity(sketch, kind):
