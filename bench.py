@@ -32,6 +32,7 @@ METRIC = "time to ‖I−XA‖_F/√n≤1e-4 at n=16384 (mixed vs FP32); solves/
 N_DEFAULT, Q_DEFAULT, TOL_DEFAULT = 16384, 128, 1e-4
 CHECK_EVERY, CHECK_COLS, CONFIRM_COLS = 32, 256, 1024
 MAX_ITER = 20000
+SERVE_MAX_ITER = 2000  # per request; the 1e-6 class stalls at the FP32 floor and runs to this cap
 # DRAM bytes (read + write) of one k_tc_update launch at n = 8192, q = 128, from one ncu capture
 # (profiles/tc_kernels_n8192_full.md); scaled by (n / 8192)^2 for other n at q = 128.
 UPDATE_TRAFFIC_N8192_Q128 = 277638912 + 208375552
@@ -54,9 +55,10 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="budget of the oracle sample")
     ap.add_argument("--no-serve", action="store_true")
-    ap.add_argument("--serve-requests", type=int, default=96)
+    ap.add_argument("--serve-requests", type=int, default=64)
     ap.add_argument("--serve-rate", type=float, default=200.0)
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-compare", action="store_true", help="skip the n = 4096 method comparison")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--batch-steps", type=int, default=2000)
     return ap.parse_args()
@@ -264,7 +266,7 @@ def run_serving(B, wl, args):
         mats[r["seed"]] = wl.c5_matrix(r["n"], r["seed"], device="cuda")
     torch.cuda.synchronize()
     budget = wl.WORKLOADS["c5_serving"]["budget_bytes"]
-    s = B.rb_srv_create(budget, 64, B.RB_MIXED, 32, 128, 4000)
+    s = B.rb_srv_create(budget, 64, B.RB_MIXED, 32, 128, SERVE_MAX_ITER)
     tickets = []
     t0 = time.perf_counter()
     for r in stream:
@@ -292,11 +294,102 @@ def run_serving(B, wl, args):
     return {"workload": f"first {len(stream)} requests of the Poisson stream at {args.serve_rate:g} req/s, "
                         "n log-uniform in [512, 8192], A = M^T M/(2n) + 1e-3 I, tol in {1e-3,1e-4,1e-6}, "
                         "q = 32 round(sqrt(n)/32), mixed form, HBM budget 120 GiB, <= 64 live",
-            "requests": len(res), "converged": len(ok), "not_converged_in_4000_steps": len(res) - len(ok),
+            "requests": len(res), "converged": len(ok), "max_iter": SERVE_MAX_ITER,
+            "not_converged": len(res) - len(ok),
             "solves_per_s": len(res) / wall, "p50_s": lat[len(lat) // 2],
             "p99_s": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)],
             "mean_queue_s": statistics.mean(r.queue_s for r in res), "wall_s": wall,
             "server_p50_s": st.p50_s, "server_p99_s": st.p99_s, "per_tol": per_tol}
+
+
+def run_comparison(B, wl, args):
+    """The n = 4096 ridge-Hessian matrix (A = M^T M/m + 1e-3 I): AdaRBFGS mixed and plain FP32 and
+    Newton-Schulz (3 x TF32) to ||I - XA||_F/sqrt(n) <= 1e-4; RBFGS and the AIP update (FP32,
+    Gaussian q = 64) for the same number of steps, residual against time."""
+    import torch
+
+    n, q, tol = 4096, 64, 1e-4
+    A = wl.c2_matrix(device="cuda")
+    st = torch.cuda.current_stream().cuda_stream
+    torch.cuda.synchronize()
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        r = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return r, e0.elapsed_time(e1) / 1e3
+
+    out = {"workload": "A = M^T M/m + 1e-3 I, M 16384 x 4096 Gaussian with column scales log-uniform in "
+                       "[1e-2, 1] (n = 4096), tol 1e-4"}
+    for name, prec in (("adarbfgs_mixed_q64", B.RB_MIXED), ("adarbfgs_fp32_q64", B.RB_FP32)):
+        h = B.rbfgs_init(n, A.data_ptr(), n, False, B.make_opts(method=B.RB_METHOD_ADARBFGS, q=q, prec=prec,
+                                                                 seed=1), st)
+        B.adarbfgs_step(h, 2)
+        torch.cuda.synchronize()
+        B.rbfgs_reset(h, 1, 0)
+        (rc, it, r), t = timed(lambda: B.rbfgs_solve(h, tol, 20000, 32, 256, 1024))
+        out[name] = {"time_to_tol_s": t, "iters": it, "resid": r, "converged": rc == B.RB_OK}
+        B.rbfgs_destroy(h)
+    (h, t0) = timed(lambda: B.newton_schulz_init(n, A.data_ptr(), n, False, B.RB_TF32X3, stream=st))
+    (rc, it, r), t = timed(lambda: B.rbfgs_solve(h, tol, 200, 1, 256, 1024))
+    out["newton_schulz_tf32x3"] = {"time_to_tol_s": t0 + t, "init_s": t0, "iters": it, "resid": r,
+                                   "converged": rc == B.RB_OK}
+    B.rbfgs_destroy(h)
+    for name, method, step in (("rbfgs_fp32_q64", B.RB_METHOD_RBFGS, B.rbfgs_step),
+                               ("aip_fp32_q64", B.RB_METHOD_AIP, B.aip_step)):
+        h = B.rbfgs_init(n, A.data_ptr(), n, False, B.make_opts(method=method, q=q, prec=B.RB_FP32, seed=1), st)
+        step(h, 2)
+        torch.cuda.synchronize()
+        B.rbfgs_reset(h, 1, 0)
+        traj, elapsed = [], 0.0
+        for _ in range(6):
+            _, t = timed(lambda: step(h, 200))
+            elapsed += t
+            traj.append({"steps": 200 * (len(traj) + 1), "seconds": elapsed,
+                         "resid": B.rbfgs_residual(h, 256, 12345)})
+        out[name] = {"trajectory": traj, "ms_per_step": 1e3 * elapsed / 1200}
+        B.rbfgs_destroy(h)
+    out["exp1"] = run_exp1(B, wl, timed, st)
+    return out
+
+
+def run_exp1(B, wl, timed, st):
+    """Sec. 10, Experiment 1: A = Abar^T Abar with Abar uniform on [0, 1]^{n x n}; each method from
+    the paper's X_0 until ||I - AX_k||_F / ||I - AX_0||_F <= 1e-2 (exact residuals at start and end).
+    kappa(A) is far beyond binary32 (the paper ran these in double), so every method runs in FP64."""
+    import numpy as np
+    import torch
+
+    res = {}
+    for n in (1000, 2000):
+        A = torch.from_numpy(np.ascontiguousarray(wl.spd_uniform_gram(n, 10 + n).T)).cuda()
+        q = 32 * max(1, round(n ** 0.5 / 32))
+        row = {}
+        runs = (("adarbfgs_gauss", lambda: B.rbfgs_init(n, A.data_ptr(), n, True, B.make_opts(
+                    method=B.RB_METHOD_ADARBFGS, sketch=B.RB_SKETCH_GAUSS, q=q, prec=B.RB_FP64, seed=1), st), 32),
+                ("adarbfgs_cols", lambda: B.rbfgs_init(n, A.data_ptr(), n, True, B.make_opts(
+                    method=B.RB_METHOD_ADARBFGS, sketch=B.RB_SKETCH_COORD_UNIFORM, q=q, prec=B.RB_FP64, seed=1),
+                    st), 32),
+                ("newton_schulz", lambda: B.newton_schulz_init(n, A.data_ptr(), n, True, B.RB_FP64, stream=st), 1),
+                ("mr", lambda: B.mr_init(n, A.data_ptr(), n, True, B.RB_FP64, stream=st), 1))
+        for name, make, every in runs:
+            h = None
+            try:
+                h, t_init = timed(make)
+                r0 = B.rbfgs_residual(h, 0, 0)
+                cap = 3000 if name.startswith("adarbfgs") else 300  # NS and MR stall (see DESIGN)
+                (rc, it, r), t = timed(lambda: B.rbfgs_solve(h, 1e-2 * r0, cap, every, 256, 0))
+                row[name] = {"seconds": t_init + t, "iters": it, "relative_error": r / r0,
+                             "converged": rc == B.RB_OK}
+            except B.RbfgsError as e:
+                row[name] = {"failed": str(e)}
+            finally:
+                if h is not None:
+                    B.rbfgs_destroy(h)
+        res[f"n{n}"] = dict(q=q, prec="fp64", **row)
+    return res
 
 
 def run_batched(B, wl, args):
@@ -467,6 +560,11 @@ def main():
     if not args.no_batch:
         batched = run_batched(B, wl, args)
 
+    # ---- the n = 4096 comparison of methods ----
+    comparison = None
+    if not args.no_compare and rank == 0:
+        comparison = run_comparison(B, wl, args)
+
     # ---- CPU oracle on a bounded sample (rank 0, N = 1 only) ----
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -487,7 +585,7 @@ def main():
                "latency_s": {"p50": statistics.median(lat), "p99": p99},
                "fp32_form": fp32, "roofline": roofline, "gemm_rooflines": gemm_rooflines, "phases_ms": phases, "step_ms": step_ms,
                "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
-               "serving": serving, "batched": batched,
+               "serving": serving, "batched": batched, "comparison": comparison,
                "wall_s": wall}
         print(json.dumps(out), flush=True)
     if world > 1:
