@@ -165,15 +165,21 @@ def barrier(world):
     torch.cuda.synchronize()
 
 
-def max_over_ranks(world, x):
+def max_over_ranks(world, x, device="cuda"):
+    """The slowest rank's time: every replica's clock is reduced with MAX (the job ends with it)."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
 
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_value(world, steps, slowest_seconds):
+    """Whole-job throughput of N independent replicas: all ranks' solves over the slowest rank's time."""
+    return world * steps / slowest_seconds
 
 
 # --------------------------------------------------------------------------
@@ -470,7 +476,7 @@ def main():
     clocks = clk.stop() if clk else None
     dev_s = ev0.elapsed_time(ev1) / 1e3
     dev_s = max_over_ranks(world, dev_s)
-    solves_per_s = world * args.steps / dev_s
+    solves_per_s = job_value(world, args.steps, dev_s)
     t_solve = dev_s / args.steps
 
     # ---- roofline of the dominant kernel, live CUDA events on the library's stream ----
