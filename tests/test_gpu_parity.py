@@ -353,8 +353,10 @@ def test_invalid_arguments_are_rejected():
         B.rbfgs_init(8, A.data_ptr(), 8, 1, B.make_opts(q=9), 0)
 
 
-@pytest.mark.parametrize("prec", [B.RB_FP64, B.RB_TF32X3])
+@pytest.mark.parametrize("prec", [B.RB_FP64, B.RB_TF32X3, B.RB_MIXED])
 def test_checkpoint_resume_is_bit_exact(prec):
+    # (mixed: the resumed handle forms S with the fused kernel's update-free pass, the uninterrupted
+    # one takes S from the previous fused update -- the same arithmetic path, so the same bits)
     n, q, K = 256, 16, 12
     A = wl.c2_matrix(n=n)
     tdt = torch_dtype(prec)
