@@ -8,7 +8,7 @@
 // its share of S_next = sum over column tiles of L+(rows, cols) S~_next(cols, :),
 // so the next step needs no separate pass over L.  Each CTA owns a contiguous
 // run of 128 x 64 tiles of L, row block by row block (as in tc_update.cu):
-//   warp 0      TMA: V tile (64 x q) and L tile (128 x 64) into a three-deep ring;
+//   warp 0      TMA: V tile (64 x q) and L tile (128 x 64) into a two-deep ring;
 //   warp 2      TMA: the S~_next tile (64 rows x q) into its own slot;
 //   warp 1      tcgen05.mma: L-tile update (A = S^ row block in TMEM, B = V) into
 //               one of two accumulators;
@@ -16,13 +16,16 @@
 //               in TMEM (A = L+ hi / lo, B = S~_next), chunked every 8 tiles
 //               (a thread's commits track its own MMAs, so the two streams of
 //               MMAs are ordered independently);
-//   warps 4-7   per tile: drain the update accumulator into the L tile in shared
-//               memory, TMA-store it, write L+ as hi / lo into TMEM for the S_next
-//               MMA; refill S^ in TMEM when the row block changes;
-//   warps 8-11  drain the S_next chunk accumulator, keep running sums (FP32,
-//               round-to-nearest), and write one partial 128 x q block per row
-//               block that the CTA touches; k_snext_reduce adds the partials of
-//               the CTAs that share a row block in CTA order.
+//   warps 4-7   per tile: read the L rows, release the stage as soon as the update
+//               MMAs are done with it, add the accumulator and write L+ into TMEM,
+//               as hi (the FP32 value, which the MMA truncates) and lo = L+ - hi,
+//               for the S_next MMA; refill S^ in TMEM when the row block changes;
+//   warps 8-11  per tile: read L+ back from TMEM, stage it in the warp's own
+//               32-row output buffer and TMA-store it from there; per chunk: drain
+//               the S_next accumulator, keep running sums (FP32, round-to-nearest),
+//               and write one partial 128 x q block per row block that the CTA
+//               touches; k_snext_reduce adds the partials of the CTAs that share a
+//               row block in CTA order.
 // TMEM: update accumulators [0, 128), S^ [128, 256), L+ hi [256, 320),
 // L+ lo [320, 384), S_next accumulator [384, 512).
 // All mbarrier waits are bounded; a wait that gives up records ST_TIMEOUT and
@@ -49,7 +52,8 @@ struct SCfg {
     static constexpr int V_BYTES = KC * UBN * 128;  // KC chunks of 64 rows x 128 B
     static constexpr int STAGE_BYTES = V_BYTES + L_TILE_BYTES;
     static constexpr int T_BYTES = 2 * NQ * 128;     // two 32-wide K chunks of NQ rows x 128 B
-    static constexpr int SMEM = NSTAGES * STAGE_BYTES + TSLOTS * T_BYTES + 1024 + 256;
+    static constexpr int OUT_BYTES = 4 * 32 * UBN * 4;  // one 32-row L+ block per epilogue warp
+    static constexpr int SMEM = NSTAGES * STAGE_BYTES + TSLOTS * T_BYTES + OUT_BYTES + 1024 + 256;
     static_assert(SMEM <= 227 * 1024, "shared memory");
 };
 
@@ -78,7 +82,8 @@ __device__ __forceinline__ float hi_tf32(float x) { return __uint_as_float(__flo
 template <int KC>
 __global__ void __launch_bounds__(384, 1)
 k_tc_update_s(const float *__restrict__ ShT, int n, int q, const __grid_constant__ CUtensorMap tmV,
-              const __grid_constant__ CUtensorMap tmL, const __grid_constant__ CUtensorMap tmT, int ncb, int ntiles,
+              const __grid_constant__ CUtensorMap tmL, const __grid_constant__ CUtensorMap tmLo,
+              const __grid_constant__ CUtensorMap tmT, int ncb, int ntiles,
               int do_update, float *Spart, int maxseg, const int *status, int *err)
 {
     using CF = SCfg<KC>;
@@ -88,15 +93,16 @@ k_tc_update_s(const float *__restrict__ ShT, int n, int q, const __grid_constant
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     unsigned char *stg = smem;
     unsigned char *tsl = smem + NSTAGES * CF::STAGE_BYTES;  // S~_next tile
-    uint64_t *bars = (uint64_t *)(tsl + TSLOTS * CF::T_BYTES);
-    uint64_t *full = bars;                   // [3] V + L tile landed
-    uint64_t *sempty = bars + NSTAGES;       // [3] stage released (tile stored / read)
+    float *outb = (float *)(tsl + TSLOTS * CF::T_BYTES);  // [4 warps][64 cols][32 rows]
+    uint64_t *bars = (uint64_t *)((unsigned char *)outb + CF::OUT_BYTES);
+    uint64_t *full = bars;                   // [2] V + L tile landed
+    uint64_t *sempty = bars + NSTAGES;       // [2] stage released (L rows read, V read by the MMAs)
     uint64_t *afull = bars + 2 * NSTAGES;    // [2] update accumulator written
     uint64_t *aempty = afull + 2;            // [2] update accumulator drained
     uint64_t *tfull = aempty + 2;            // [TSLOTS] S~_next tile landed
     uint64_t *tempty = tfull + TSLOTS;       // [TSLOTS] S~_next tile read (S_next MMA done)
     uint64_t *lfull = tempty + TSLOTS;       // L+ hi / lo written to TMEM
-    uint64_t *lempty = lfull + 1;            // L+ read (S_next MMA done)
+    uint64_t *lempty = lfull + 1;            // L+ read (S_next MMA done, L+ staged for the store)
     uint64_t *shfull = lempty + 1;           // S^ written to TMEM
     uint64_t *shfree = shfull + 1;           // update MMAs reading S^ done
     uint64_t *sfull = shfree + 1;            // S_next chunk accumulated
@@ -113,7 +119,7 @@ k_tc_update_s(const float *__restrict__ ShT, int n, int q, const __grid_constant
     if (threadIdx.x == 0) {
         for (int s = 0; s < NSTAGES; ++s) {
             mbar_init(smem_u32(&full[s]), 1);
-            mbar_init(smem_u32(&sempty[s]), 1);
+            mbar_init(smem_u32(&sempty[s]), 4);  // one arrival per epilogue warp
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(smem_u32(&afull[b]), 1);
@@ -124,7 +130,7 @@ k_tc_update_s(const float *__restrict__ ShT, int n, int q, const __grid_constant
             mbar_init(smem_u32(&tempty[s]), 1);
         }
         mbar_init(smem_u32(lfull), 128);
-        mbar_init(smem_u32(lempty), 1);
+        mbar_init(smem_u32(lempty), 1 + 4);  // the S_next MMA commit and one arrival per store warp
         mbar_init(smem_u32(shfull), 128);
         mbar_init(smem_u32(shfree), 1);
         mbar_init(smem_u32(sfull), 1);
@@ -249,29 +255,43 @@ k_tc_update_s(const float *__restrict__ ShT, int n, int q, const __grid_constant
         const int r = threadIdx.x - 128;  // tile row = TMEM lane
         const uint32_t lane_base = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
         bool ok = true;
+        // waits agree across the warp (the TMEM accesses and the stage release are warp-wide)
+        auto wwait = [&](uint64_t *bar, uint32_t par) {
+            return __all_sync(0xffffffffu, mbar_wait(smem_u32(bar), par, err, abort_flag));
+        };
         auto load_sh = [&](int rb) {  // S^ rows of row block rb into TMEM (rows past n are zero)
             const int k = rb - rb_first;
-            if (k >= 1 && !mbar_wait(smem_u32(shfree), (k - 1) & 1, err, abort_flag)) {
+            if (k >= 1 && !wwait(shfree, (k - 1) & 1)) {
                 ok = false;
                 return;
             }
             tc_fence_after();
             const int row = rb * 128 + r;
             const float4 *src = (const float4 *)(ShT + (size_t)row * q);
+            // 64 columns per batch: all loads of a batch are in flight together
 #pragma unroll
-            for (int c0 = 0; c0 < KC * 32; c0 += 16) {
-                uint32_t w[16];
+            for (int b0 = 0; b0 < KC * 32; b0 += 64) {
+                float4 v[16];
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const int c = c0 + 4 * j;
-                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (row < n && c < q) v = src[c >> 2];  // q % 4 == 0
-                    w[4 * j] = __float_as_uint(v.x);
-                    w[4 * j + 1] = __float_as_uint(v.y);
-                    w[4 * j + 2] = __float_as_uint(v.z);
-                    w[4 * j + 3] = __float_as_uint(v.w);
+                for (int j = 0; j < 16; ++j) {
+                    const int c = b0 + 4 * j;
+                    v[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (c < KC * 32 && row < n && c < q) v[j] = src[c >> 2];  // q % 4 == 0
                 }
-                st16(lane_base + COL_SH + c0, w);
+#pragma unroll
+                for (int c0 = 0; c0 < 64; c0 += 16) {
+                    if (b0 + c0 >= KC * 32) break;
+                    uint32_t w[16];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const float4 x = v[(c0 >> 2) + j];
+                        w[4 * j] = __float_as_uint(x.x);
+                        w[4 * j + 1] = __float_as_uint(x.y);
+                        w[4 * j + 2] = __float_as_uint(x.z);
+                        w[4 * j + 3] = __float_as_uint(x.w);
+                    }
+                    st16(lane_base + COL_SH + b0 + c0, w);
+                }
             }
             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
             tc_fence_before();
@@ -279,15 +299,15 @@ k_tc_update_s(const float *__restrict__ ShT, int n, int q, const __grid_constant
         };
         if (do_update && nt > 0) load_sh(rb_first);
         for (int i = 0; i < nt && ok; ++i) {
-            const int t = tb + i, rb = t / ncb, cb = t - rb * ncb, s = i % NSTAGES, b = i & 1;
+            const int t = tb + i, rb = t / ncb, s = i % NSTAGES, b = i & 1;
             // the L row first (shared memory), then the accumulator (TMEM, one wait for all loads)
-            if (!mbar_wait(smem_u32(&full[s]), (i / NSTAGES) & 1, err, abort_flag)) break;
-            float *Ls = (float *)(stg + s * CF::STAGE_BYTES + CF::V_BYTES);  // [64 cols][128 rows]
+            if (!wwait(&full[s], (i / NSTAGES) & 1)) break;
+            const float *Ls = (const float *)(stg + s * CF::STAGE_BYTES + CF::V_BYTES);  // [64 cols][128 rows]
             float lp[UBN];
 #pragma unroll
             for (int c = 0; c < UBN; ++c) lp[c] = Ls[c * 128 + r];
             if (do_update) {
-                if (!mbar_wait(smem_u32(&afull[b]), (i >> 1) & 1, err, abort_flag)) break;
+                if (!wwait(&afull[b], (i >> 1) & 1)) break;
                 tc_fence_after();
                 uint32_t v[UBN];
                 const uint32_t ta = lane_base + (uint32_t)(b * UBN);
@@ -305,22 +325,13 @@ k_tc_update_s(const float *__restrict__ ShT, int n, int q, const __grid_constant
                 tc_fence_before();
                 mbar_arrive(smem_u32(&aempty[b]));
 #pragma unroll
-                for (int c = 0; c < UBN; ++c) {
-                    lp[c] += __uint_as_float(v[c]);
-                    Ls[c * 128 + r] = lp[c];
-                }
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                for (int c = 0; c < UBN; ++c) lp[c] += __uint_as_float(v[c]);
             }
-            named_bar(1, 128);
-            if (r == 0 && do_update) {  // the store's completion is awaited after the TMEM writes below
-                tma_store_2d(&tmL, smem_u32(Ls), rb * 128, cb * UBN);
-                bulk_commit();
-            }
+            // the L rows are in registers and the update MMAs have read V: the stage is free
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&sempty[s]));
             // L+ of this tile as the A operand of its S_next product (after the previous one is read)
-            if (i >= 1 && !mbar_wait(smem_u32(lempty), (i - 1) & 1, err, abort_flag)) {
-                if (r == 0) bulk_wait0();
-                break;
-            }
+            if (i >= 1 && !wwait(lempty, (i - 1) & 1)) break;
             tc_fence_after();
 #pragma unroll
             for (int c0 = 0; c0 < UBN; c0 += 16) {
@@ -335,49 +346,77 @@ k_tc_update_s(const float *__restrict__ ShT, int n, int q, const __grid_constant
             asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
             tc_fence_before();
             mbar_arrive(smem_u32(lfull));
-            if (r == 0) {  // the stage is free once the store has read the tile (or, without update, now)
-                if (do_update) bulk_wait_read0();
-                mbar_arrive(smem_u32(&sempty[s]));
-            }
             // the update MMAs of this row block are done once its last tile drained: refill S^
             if (do_update && last_of_rb(t) && i + 1 < nt) load_sh(rb + 1);
         }
-        if (r == 0) bulk_wait0();
     } else if (warp >= 8) {
-        // ---------------- S_next chunks: running sums and partial blocks ----------------
+        // ---------------- L+ stores and S_next chunks ----------------
         const int wq = warp & 3;
+        const uint32_t lane_base = tmem + ((uint32_t)(32 * wq) << 16);
+        float *ow = outb + wq * (32 * UBN);  // [64 cols][32 rows]
+        auto wwait = [&](uint64_t *bar, uint32_t par) {
+            return __all_sync(0xffffffffu, mbar_wait(smem_u32(bar), par, err, abort_flag));
+        };
         float run[NQ];
 #pragma unroll
         for (int j = 0; j < NQ; ++j) run[j] = 0.f;
-        int c = 0, i = 0;
-        while (i < nt) {
-            // chunk c covers tiles [i, i + len) of one row block
-            const int t = tb + i, p = seg_pos(t);
-            int len = SCHUNK - (p % SCHUNK);
-            const int rb_end = min(te, (t / ncb + 1) * ncb);
-            len = min(len, rb_end - t);
-            if (!mbar_wait(smem_u32(sfull), c & 1, err, abort_flag)) break;
+        int c = 0;
+        for (int i = 0; i < nt; ++i) {
+            const int t = tb + i, rb = t / ncb, cb = t - rb * ncb, p = seg_pos(t);
+            // L+ of tile i (the hi slot holds the FP32 value) to the output buffer, then one TMA store
+            if (!wwait(lfull, i & 1)) break;
             tc_fence_after();
-            const uint32_t keep = (p == 0) ? 0u : 0xFFFFFFFFu;  // a row block starts a fresh sum
+            if (do_update) {
+                if (lane == 0) bulk_wait_read0();  // the previous store has read the buffer
+                __syncwarp();
 #pragma unroll
-            for (int c0 = 0; c0 < NQ; c0 += 16) {
-                uint32_t v[16];
-                tmem_ld16(tmem + ((uint32_t)(32 * wq) << 16) + COL_SACC + c0, v);
+                for (int c0 = 0; c0 < UBN; c0 += 32) {
+                    uint32_t v0[16], v1[16];
+                    tmem_ld16(lane_base + COL_LHI + c0, v0);
+                    tmem_ld16(lane_base + COL_LHI + c0 + 16, v1);
 #pragma unroll
-                for (int j = 0; j < 16; ++j)
-                    run[c0 + j] = __uint_as_float(__float_as_uint(run[c0 + j]) & keep) + __uint_as_float(v[j]);
+                    for (int j = 0; j < 16; ++j) {
+                        ow[(c0 + j) * 32 + lane] = __uint_as_float(v0[j]);
+                        ow[(c0 + 16 + j) * 32 + lane] = __uint_as_float(v1[j]);
+                    }
+                }
             }
             tc_fence_before();
-            mbar_arrive(smem_u32(sfree));
-            i += len;
-            ++c;
-            if (tb + i == rb_end) {  // row block finished: partial block (rows x NQ, column-major, ld 128)
-                const int seg = t / ncb - rb_first;
-                float *dst = Spart + ((size_t)blockIdx.x * maxseg + seg) * (128 * NQ) + 32 * wq + lane;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(lempty));
+            if (do_update) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0 && rb * 128 + 32 * wq < n) {  // a block wholly past row n stores nothing
+                    tma_store_2d(&tmLo, smem_u32(ow), rb * 128 + 32 * wq, cb * UBN);
+                    bulk_commit();
+                }
+            }
+            // S_next chunk ends with tile i: running sums; a row block's last chunk writes its partial block
+            if (((p + 1) % SCHUNK) == 0 || last_of_rb(t)) {
+                if (!wwait(sfull, c & 1)) break;
+                tc_fence_after();
+                const uint32_t keep = (p < SCHUNK) ? 0u : 0xFFFFFFFFu;  // a row block starts a fresh sum
 #pragma unroll
-                for (int j = 0; j < NQ; ++j) dst[j * 128] = run[j];
+                for (int c0 = 0; c0 < NQ; c0 += 16) {
+                    uint32_t v[16];
+                    tmem_ld16(lane_base + COL_SACC + c0, v);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j)
+                        run[c0 + j] = __uint_as_float(__float_as_uint(run[c0 + j]) & keep) + __uint_as_float(v[j]);
+                }
+                tc_fence_before();
+                mbar_arrive(smem_u32(sfree));
+                ++c;
+                if (last_of_rb(t)) {  // partial block (rows x NQ, column-major, ld 128)
+                    const int seg = rb - rb_first;
+                    float *dst = Spart + ((size_t)blockIdx.x * maxseg + seg) * (128 * NQ) + 32 * wq + lane;
+#pragma unroll
+                    for (int j = 0; j < NQ; ++j) dst[j * 128] = run[j];
+                }
             }
         }
+        if (lane == 0) bulk_wait0();
         tc_fence_before();
     }
     __syncthreads();
@@ -419,6 +458,7 @@ __global__ void k_snext_reduce(int n, int q, int nq, int ncb, int ntiles, int G,
 
 template <int KC>
 int launch_update_s(cudaStream_t st, const float *ShT, int n, int q, const CUtensorMap &mv, const CUtensorMap &ml,
+                    const CUtensorMap &mlo,
                     const CUtensorMap &mt, int do_update, float *Spart, size_t spart_elems, float *S, int64_t lds,
                     const int *status, int *err)
 {
@@ -440,8 +480,8 @@ int launch_update_s(cudaStream_t st, const float *ShT, int n, int q, const CUten
     }
     if ((size_t)grid * maxseg * 128 * CF::NQ > spart_elems) return -2;
     rb_count_launch();
-    k_tc_update_s<KC><<<grid, 384, CF::SMEM, st>>>(ShT, n, q, mv, ml, mt, ncb, ntiles, do_update, Spart, maxseg,
-                                                   status, err);
+    k_tc_update_s<KC><<<grid, 384, CF::SMEM, st>>>(ShT, n, q, mv, ml, mlo, mt, ncb, ntiles, do_update, Spart,
+                                                   maxseg, status, err);
     rb_count_launch();
     k_snext_reduce<<<dim3(nrb, CF::NQ / 32), 128, 0, st>>>(n, q, CF::NQ, ncb, ntiles, grid, maxseg, Spart, S, lds,
                                                           status);
@@ -467,17 +507,18 @@ int tc_update_next_s(cudaStream_t st, int n, int q, const float *ShT, const floa
     if (q < 1 || q > 128 || (q % 4) || (ldl % 4) || (n % 4) || ((uintptr_t)ShT % 16) || ((uintptr_t)V % 16) ||
         ((uintptr_t)L % 16) || ((uintptr_t)St_next % 16))
         return 1;
-    CUtensorMap mv, ml, mt;
+    CUtensorMap mv, ml, mlo, mt;
     const int nq = ((q + 31) / 32) * 32;
     if (!tc_make_map(&mv, V, q, n, q, 32, UBN, 1) || !tc_make_map(&ml, L, n, n, ldl, 128, UBN, 0) ||
+        !tc_make_map(&mlo, L, n, n, ldl, 32, UBN, 0) ||
         !tc_make_map(&mt, St_next, n, q, n, 32, nq, 1))
         return -4;
     int *err = const_cast<int *>(status);
     switch (nq / 32) {
-    case 1: return launch_update_s<1>(st, ShT, n, q, mv, ml, mt, do_update, Spart, spart_elems, S_out, n, status, err);
-    case 2: return launch_update_s<2>(st, ShT, n, q, mv, ml, mt, do_update, Spart, spart_elems, S_out, n, status, err);
-    case 3: return launch_update_s<3>(st, ShT, n, q, mv, ml, mt, do_update, Spart, spart_elems, S_out, n, status, err);
+    case 1: return launch_update_s<1>(st, ShT, n, q, mv, ml, mlo, mt, do_update, Spart, spart_elems, S_out, n, status, err);
+    case 2: return launch_update_s<2>(st, ShT, n, q, mv, ml, mlo, mt, do_update, Spart, spart_elems, S_out, n, status, err);
+    case 3: return launch_update_s<3>(st, ShT, n, q, mv, ml, mlo, mt, do_update, Spart, spart_elems, S_out, n, status, err);
     default:
-        return launch_update_s<4>(st, ShT, n, q, mv, ml, mt, do_update, Spart, spart_elems, S_out, n, status, err);
+        return launch_update_s<4>(st, ShT, n, q, mv, ml, mlo, mt, do_update, Spart, spart_elems, S_out, n, status, err);
     }
 }
