@@ -8,8 +8,10 @@
 // its share of S_next = sum over column tiles of L+(rows, cols) S~_next(cols, :),
 // so the next step needs no separate pass over L.  Each CTA owns a contiguous
 // run of 128 x 64 tiles of L, row block by row block (as in tc_update.cu):
-//   warp 0      TMA: V tile (64 x q) and L tile (128 x 64) into a two-deep ring;
-//   warp 2      TMA: the S~_next tile (64 rows x q) into its own slot;
+//   warp 0      TMA: L tile (128 x 64) into the L half of a two-deep ring (released
+//               as soon as the epilogue has read it);
+//   warp 2      TMA: V tile (64 x q) into the V half of the ring (released by the
+//               update MMAs) and the S~_next tile (64 rows x q) into its own slot;
 //   warp 1      tcgen05.mma: L-tile update (A = S^ row block in TMEM, B = V) into
 //               one of two accumulators;
 //   warp 3      tcgen05.mma: the S_next product of each tile as soon as its L+ is
@@ -95,9 +97,11 @@ k_tc_update_s(const float *__restrict__ ShT, int n, int q, const __grid_constant
     unsigned char *tsl = smem + NSTAGES * CF::STAGE_BYTES;  // S~_next tile
     float *outb = (float *)(tsl + TSLOTS * CF::T_BYTES);  // [4 warps][64 cols][32 rows]
     uint64_t *bars = (uint64_t *)((unsigned char *)outb + CF::OUT_BYTES);
-    uint64_t *full = bars;                   // [2] V + L tile landed
-    uint64_t *sempty = bars + NSTAGES;       // [2] stage released (L rows read, V read by the MMAs)
-    uint64_t *afull = bars + 2 * NSTAGES;    // [2] update accumulator written
+    uint64_t *lfull_s = bars;                // [2] L tile landed
+    uint64_t *lempty_s = bars + NSTAGES;     // [2] L tile read by the epilogue
+    uint64_t *vfull = bars + 2 * NSTAGES;    // [2] V tile landed
+    uint64_t *vempty = bars + 3 * NSTAGES;   // [2] V tile read by the update MMAs
+    uint64_t *afull = bars + 4 * NSTAGES;    // [2] update accumulator written
     uint64_t *aempty = afull + 2;            // [2] update accumulator drained
     uint64_t *tfull = aempty + 2;            // [TSLOTS] S~_next tile landed
     uint64_t *tempty = tfull + TSLOTS;       // [TSLOTS] S~_next tile read (S_next MMA done)
@@ -118,8 +122,10 @@ k_tc_update_s(const float *__restrict__ ShT, int n, int q, const __grid_constant
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NSTAGES; ++s) {
-            mbar_init(smem_u32(&full[s]), 1);
-            mbar_init(smem_u32(&sempty[s]), 4);  // one arrival per epilogue warp
+            mbar_init(smem_u32(&lfull_s[s]), 1);
+            mbar_init(smem_u32(&lempty_s[s]), 4);  // one arrival per epilogue warp
+            mbar_init(smem_u32(&vfull[s]), 1);
+            mbar_init(smem_u32(&vempty[s]), 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(smem_u32(&afull[b]), 1);
@@ -153,27 +159,30 @@ k_tc_update_s(const float *__restrict__ ShT, int n, int q, const __grid_constant
     auto last_of_rb = [&](int t) { return t + 1 == te || (t + 1) / ncb != t / ncb; };
 
     if (warp == 0) {
-        // ---------------- TMA: V and L tiles ----------------
+        // ---------------- TMA: L tiles ----------------
         if (lane == 0) {
-            const uint32_t bytes = (do_update ? CF::V_BYTES : 0) + L_TILE_BYTES;
             for (int i = 0; i < nt; ++i) {
                 const int t = tb + i, rb = t / ncb, cb = t - rb * ncb, s = i % NSTAGES;
-                if (i >= NSTAGES && !mbar_wait(smem_u32(&sempty[s]), ((i / NSTAGES) - 1) & 1, err, abort_flag))
+                if (i >= NSTAGES && !mbar_wait(smem_u32(&lempty_s[s]), ((i / NSTAGES) - 1) & 1, err, abort_flag))
                     break;
-                unsigned char *st = stg + s * CF::STAGE_BYTES;
-                const uint32_t fb = smem_u32(&full[s]);
-                mbar_expect_tx(fb, bytes);
-                if (do_update)
-                    for (int kc = 0; kc < KC; ++kc)
-                        tma_load_2d(smem_u32(st + kc * 8192), &tmV, 32 * kc, cb * UBN, fb);
-                tma_load_2d(smem_u32(st + CF::V_BYTES), &tmL, rb * 128, cb * UBN, fb);
+                const uint32_t fb = smem_u32(&lfull_s[s]);
+                mbar_expect_tx(fb, L_TILE_BYTES);
+                tma_load_2d(smem_u32(stg + s * CF::STAGE_BYTES + CF::V_BYTES), &tmL, rb * 128, cb * UBN, fb);
             }
         }
     } else if (warp == 2) {
-        // ---------------- TMA: S~_next tiles (rows cb * 64 .. + 63) ----------------
+        // ---------------- TMA: V tiles and S~_next tiles (rows cb * 64 .. + 63) ----------------
         if (lane == 0) {
             for (int i = 0; i < nt; ++i) {
-                const int t = tb + i, cb = t % ncb, ts = i % TSLOTS;
+                const int t = tb + i, cb = t % ncb, ts = i % TSLOTS, s = i % NSTAGES;
+                if (do_update) {
+                    if (i >= NSTAGES && !mbar_wait(smem_u32(&vempty[s]), ((i / NSTAGES) - 1) & 1, err, abort_flag))
+                        break;
+                    const uint32_t vb = smem_u32(&vfull[s]);
+                    mbar_expect_tx(vb, CF::V_BYTES);
+                    for (int kc = 0; kc < KC; ++kc)
+                        tma_load_2d(smem_u32(stg + s * CF::STAGE_BYTES + kc * 8192), &tmV, 32 * kc, cb * UBN, vb);
+                }
                 if (i >= TSLOTS && !mbar_wait(smem_u32(&tempty[ts]), ((i / TSLOTS) - 1) & 1, err, abort_flag)) break;
                 const uint32_t fb = smem_u32(&tfull[ts]);
                 unsigned char *tp = tsl + ts * CF::T_BYTES;
@@ -233,7 +242,7 @@ k_tc_update_s(const float *__restrict__ ShT, int n, int q, const __grid_constant
                         if (!mbar_wait(smem_u32(shfull), k & 1, err, abort_flag)) break;
                         cur_rb = rb;
                     }
-                    if (!mbar_wait(smem_u32(&full[s]), (i / NSTAGES) & 1, err, abort_flag)) break;
+                    if (!mbar_wait(smem_u32(&vfull[s]), (i / NSTAGES) & 1, err, abort_flag)) break;
                     if (i >= 2 && !mbar_wait(smem_u32(&aempty[b]), ((i >> 1) - 1) & 1, err, abort_flag)) break;
                     tc_fence_after();
                     const uint32_t v_u = smem_u32(stg + s * CF::STAGE_BYTES);
@@ -246,6 +255,7 @@ k_tc_update_s(const float *__restrict__ ShT, int n, int q, const __grid_constant
                                    (kc | k8) ? 1u : 0u);
                         }
                     mma_commit(smem_u32(&afull[b]));
+                    mma_commit(smem_u32(&vempty[s]));
                     if (last_of_rb(t)) mma_commit(smem_u32(shfree));
                 }
             }
@@ -301,11 +311,13 @@ k_tc_update_s(const float *__restrict__ ShT, int n, int q, const __grid_constant
         for (int i = 0; i < nt && ok; ++i) {
             const int t = tb + i, rb = t / ncb, s = i % NSTAGES, b = i & 1;
             // the L row first (shared memory), then the accumulator (TMEM, one wait for all loads)
-            if (!wwait(&full[s], (i / NSTAGES) & 1)) break;
+            if (!wwait(&lfull_s[s], (i / NSTAGES) & 1)) break;
             const float *Ls = (const float *)(stg + s * CF::STAGE_BYTES + CF::V_BYTES);  // [64 cols][128 rows]
             float lp[UBN];
 #pragma unroll
             for (int c = 0; c < UBN; ++c) lp[c] = Ls[c * 128 + r];
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&lempty_s[s]));  // the L tile is in registers
             if (do_update) {
                 if (!wwait(&afull[b], (i >> 1) & 1)) break;
                 tc_fence_after();
@@ -327,9 +339,6 @@ k_tc_update_s(const float *__restrict__ ShT, int n, int q, const __grid_constant
 #pragma unroll
                 for (int c = 0; c < UBN; ++c) lp[c] += __uint_as_float(v[c]);
             }
-            // the L rows are in registers and the update MMAs have read V: the stage is free
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&sempty[s]));
             // L+ of this tile as the A operand of its S_next product (after the previous one is read)
             if (i >= 1 && !wwait(lempty, (i - 1) & 1)) break;
             tc_fence_after();
