@@ -47,6 +47,10 @@ constexpr int NSTAGES = 2;
 constexpr int TSLOTS = 2;                    // S~_next tiles in flight
 constexpr int SCHUNK = 8;                    // tiles per S_next accumulation chunk (512 of K)
 constexpr uint32_t COL_SH = 128, COL_LHI = 256, COL_LLO = 320, COL_SACC = 384;
+// Registers per thread: 168 at launch (384 threads); warps 0-3 drop to REG_ISSUE and warps 8-11
+// (running sums of S_next, NQ per thread) rise to REG_DRAIN: 128 x (112 + 168 + 208) <= 384 x 168.
+constexpr int REG_ISSUE = 112, REG_DRAIN = 208;
+static_assert(128 * (REG_ISSUE + 168 + REG_DRAIN) <= 384 * 168, "register split");
 
 template <int KC>  // q padded to NQ = 32 KC
 struct SCfg {
@@ -158,109 +162,113 @@ k_tc_update_s(const float *__restrict__ ShT, int n, int q, const __grid_constant
     auto seg_pos = [&](int t) { return t - max(tb, (t / ncb) * ncb); };
     auto last_of_rb = [&](int t) { return t + 1 == te || (t + 1) / ncb != t / ncb; };
 
-    if (warp == 0) {
-        // ---------------- TMA: L tiles ----------------
-        if (lane == 0) {
-            for (int i = 0; i < nt; ++i) {
-                const int t = tb + i, rb = t / ncb, cb = t - rb * ncb, s = i % NSTAGES;
-                if (i >= NSTAGES && !mbar_wait(smem_u32(&lempty_s[s]), ((i / NSTAGES) - 1) & 1, err, abort_flag))
-                    break;
-                const uint32_t fb = smem_u32(&lfull_s[s]);
-                mbar_expect_tx(fb, L_TILE_BYTES);
-                tma_load_2d(smem_u32(stg + s * CF::STAGE_BYTES + CF::V_BYTES), &tmL, rb * 128, cb * UBN, fb);
-            }
-        }
-    } else if (warp == 2) {
-        // ---------------- TMA: V tiles and S~_next tiles (rows cb * 64 .. + 63) ----------------
-        if (lane == 0) {
-            for (int i = 0; i < nt; ++i) {
-                const int t = tb + i, cb = t % ncb, ts = i % TSLOTS, s = i % NSTAGES;
-                if (do_update) {
-                    if (i >= NSTAGES && !mbar_wait(smem_u32(&vempty[s]), ((i / NSTAGES) - 1) & 1, err, abort_flag))
+    if (warp < 4) {
+        // single-thread roles: give registers to the S_next drain warps
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(REG_ISSUE));
+        if (warp == 0) {
+            // ---------------- TMA: L tiles ----------------
+            if (lane == 0) {
+                for (int i = 0; i < nt; ++i) {
+                    const int t = tb + i, rb = t / ncb, cb = t - rb * ncb, s = i % NSTAGES;
+                    if (i >= NSTAGES && !mbar_wait(smem_u32(&lempty_s[s]), ((i / NSTAGES) - 1) & 1, err, abort_flag))
                         break;
-                    const uint32_t vb = smem_u32(&vfull[s]);
-                    mbar_expect_tx(vb, CF::V_BYTES);
-                    for (int kc = 0; kc < KC; ++kc)
-                        tma_load_2d(smem_u32(stg + s * CF::STAGE_BYTES + kc * 8192), &tmV, 32 * kc, cb * UBN, vb);
+                    const uint32_t fb = smem_u32(&lfull_s[s]);
+                    mbar_expect_tx(fb, L_TILE_BYTES);
+                    tma_load_2d(smem_u32(stg + s * CF::STAGE_BYTES + CF::V_BYTES), &tmL, rb * 128, cb * UBN, fb);
                 }
-                if (i >= TSLOTS && !mbar_wait(smem_u32(&tempty[ts]), ((i / TSLOTS) - 1) & 1, err, abort_flag)) break;
-                const uint32_t fb = smem_u32(&tfull[ts]);
-                unsigned char *tp = tsl + ts * CF::T_BYTES;
-                mbar_expect_tx(fb, CF::T_BYTES);
-                tma_load_2d(smem_u32(tp), &tmT, cb * UBN, 0, fb);
-                tma_load_2d(smem_u32(tp + NQ * 128), &tmT, cb * UBN + 32, 0, fb);
             }
-        }
-    } else if (warp == 3) {
-        // ---------------- MMA issuer for the S_next products (own thread, own commits) ----------------
-        if (lane == 0) {
-            const uint32_t idesc_s = idesc_tf32(NQ, 0);
-            int chunk = -1;  // S_next chunk being accumulated
-            bool ok = true;
-            // S_next product of tile j (L+ of tile j in TMEM, S~_next tile j in smem)
-            auto s_mma = [&](int j) {
-                const int t = tb + j, p = seg_pos(t);
-                const bool cstart = (p % SCHUNK) == 0;
-                const bool cend = ((p + 1) % SCHUNK) == 0 || last_of_rb(t);
-                if (cstart) {
-                    ++chunk;
-                    if (chunk >= 1 && !mbar_wait(smem_u32(sfree), (chunk - 1) & 1, err, abort_flag)) {
+        } else if (warp == 2) {
+            // ---------------- TMA: V tiles and S~_next tiles (rows cb * 64 .. + 63) ----------------
+            if (lane == 0) {
+                for (int i = 0; i < nt; ++i) {
+                    const int t = tb + i, cb = t % ncb, ts = i % TSLOTS, s = i % NSTAGES;
+                    if (do_update) {
+                        if (i >= NSTAGES && !mbar_wait(smem_u32(&vempty[s]), ((i / NSTAGES) - 1) & 1, err, abort_flag))
+                            break;
+                        const uint32_t vb = smem_u32(&vfull[s]);
+                        mbar_expect_tx(vb, CF::V_BYTES);
+                        for (int kc = 0; kc < KC; ++kc)
+                            tma_load_2d(smem_u32(stg + s * CF::STAGE_BYTES + kc * 8192), &tmV, 32 * kc, cb * UBN, vb);
+                    }
+                    if (i >= TSLOTS && !mbar_wait(smem_u32(&tempty[ts]), ((i / TSLOTS) - 1) & 1, err, abort_flag)) break;
+                    const uint32_t fb = smem_u32(&tfull[ts]);
+                    unsigned char *tp = tsl + ts * CF::T_BYTES;
+                    mbar_expect_tx(fb, CF::T_BYTES);
+                    tma_load_2d(smem_u32(tp), &tmT, cb * UBN, 0, fb);
+                    tma_load_2d(smem_u32(tp + NQ * 128), &tmT, cb * UBN + 32, 0, fb);
+                }
+            }
+        } else if (warp == 3) {
+            // ---------------- MMA issuer for the S_next products (own thread, own commits) ----------------
+            if (lane == 0) {
+                const uint32_t idesc_s = idesc_tf32(NQ, 0);
+                int chunk = -1;  // S_next chunk being accumulated
+                bool ok = true;
+                // S_next product of tile j (L+ of tile j in TMEM, S~_next tile j in smem)
+                auto s_mma = [&](int j) {
+                    const int t = tb + j, p = seg_pos(t);
+                    const bool cstart = (p % SCHUNK) == 0;
+                    const bool cend = ((p + 1) % SCHUNK) == 0 || last_of_rb(t);
+                    if (cstart) {
+                        ++chunk;
+                        if (chunk >= 1 && !mbar_wait(smem_u32(sfree), (chunk - 1) & 1, err, abort_flag)) {
+                            ok = false;
+                            return;
+                        }
+                    }
+                    const int ts = j % TSLOTS;
+                    if (!mbar_wait(smem_u32(lfull), j & 1, err, abort_flag) ||
+                        !mbar_wait(smem_u32(&tfull[ts]), (j / TSLOTS) & 1, err, abort_flag)) {
                         ok = false;
                         return;
                     }
-                }
-                const int ts = j % TSLOTS;
-                if (!mbar_wait(smem_u32(lfull), j & 1, err, abort_flag) ||
-                    !mbar_wait(smem_u32(&tfull[ts]), (j / TSLOTS) & 1, err, abort_flag)) {
-                    ok = false;
-                    return;
-                }
-                tc_fence_after();
-                const uint32_t t_u = smem_u32(tsl + ts * CF::T_BYTES);
-#pragma unroll
-                for (int kk = 0; kk < UBN / 8; ++kk) {
-                    const uint64_t db = umma_desc(t_u + (kk >> 2) * (NQ * 128) + (kk & 3) * 32, 16, 1024);
-                    mma_ts(tmem + COL_SACC, tmem + COL_LLO + 8 * kk, db, idesc_s, (cstart && kk == 0) ? 0u : 1u);
-                    mma_ts(tmem + COL_SACC, tmem + COL_LHI + 8 * kk, db, idesc_s, 1u);
-                }
-                mma_commit(smem_u32(lempty));
-                mma_commit(smem_u32(&tempty[ts]));
-                if (cend) mma_commit(smem_u32(sfull));
-            };
-            for (int j = 0; j < nt && ok; ++j) s_mma(j);
-        }
-    } else if (warp == 1) {
-        // ---------------- MMA issuer for the L-tile update ----------------
-        if (lane == 0 && do_update) {
-            const uint32_t idesc_u = idesc_tf32(UBN, 0);
-            int cur_rb = -1;
-            for (int i = 0; i < nt; ++i) {
-                const int t = tb + i, rb = t / ncb, s = i % NSTAGES, b = i & 1;
-                {
-                    if (rb != cur_rb) {
-                        const int k = rb - rb_first;  // S^ refills of this CTA
-                        if (!mbar_wait(smem_u32(shfull), k & 1, err, abort_flag)) break;
-                        cur_rb = rb;
-                    }
-                    if (!mbar_wait(smem_u32(&vfull[s]), (i / NSTAGES) & 1, err, abort_flag)) break;
-                    if (i >= 2 && !mbar_wait(smem_u32(&aempty[b]), ((i >> 1) - 1) & 1, err, abort_flag)) break;
                     tc_fence_after();
-                    const uint32_t v_u = smem_u32(stg + s * CF::STAGE_BYTES);
-#pragma unroll
-                    for (int kc = 0; kc < KC; ++kc)
-#pragma unroll
-                        for (int k8 = 0; k8 < 4; ++k8) {
-                            const uint64_t db = umma_desc(v_u + kc * 8192 + k8 * 32, 16, 1024);
-                            mma_ts(tmem + (uint32_t)(b * UBN), tmem + COL_SH + 32 * kc + 8 * k8, db, idesc_u,
-                                   (kc | k8) ? 1u : 0u);
+                    const uint32_t t_u = smem_u32(tsl + ts * CF::T_BYTES);
+    #pragma unroll
+                    for (int kk = 0; kk < UBN / 8; ++kk) {
+                        const uint64_t db = umma_desc(t_u + (kk >> 2) * (NQ * 128) + (kk & 3) * 32, 16, 1024);
+                        mma_ts(tmem + COL_SACC, tmem + COL_LLO + 8 * kk, db, idesc_s, (cstart && kk == 0) ? 0u : 1u);
+                        mma_ts(tmem + COL_SACC, tmem + COL_LHI + 8 * kk, db, idesc_s, 1u);
+                    }
+                    mma_commit(smem_u32(lempty));
+                    mma_commit(smem_u32(&tempty[ts]));
+                    if (cend) mma_commit(smem_u32(sfull));
+                };
+                for (int j = 0; j < nt && ok; ++j) s_mma(j);
+            }
+        } else if (warp == 1) {
+            // ---------------- MMA issuer for the L-tile update ----------------
+            if (lane == 0 && do_update) {
+                const uint32_t idesc_u = idesc_tf32(UBN, 0);
+                int cur_rb = -1;
+                for (int i = 0; i < nt; ++i) {
+                    const int t = tb + i, rb = t / ncb, s = i % NSTAGES, b = i & 1;
+                    {
+                        if (rb != cur_rb) {
+                            const int k = rb - rb_first;  // S^ refills of this CTA
+                            if (!mbar_wait(smem_u32(shfull), k & 1, err, abort_flag)) break;
+                            cur_rb = rb;
                         }
-                    mma_commit(smem_u32(&afull[b]));
-                    mma_commit(smem_u32(&vempty[s]));
-                    if (last_of_rb(t)) mma_commit(smem_u32(shfree));
+                        if (!mbar_wait(smem_u32(&vfull[s]), (i / NSTAGES) & 1, err, abort_flag)) break;
+                        if (i >= 2 && !mbar_wait(smem_u32(&aempty[b]), ((i >> 1) - 1) & 1, err, abort_flag)) break;
+                        tc_fence_after();
+                        const uint32_t v_u = smem_u32(stg + s * CF::STAGE_BYTES);
+    #pragma unroll
+                        for (int kc = 0; kc < KC; ++kc)
+    #pragma unroll
+                            for (int k8 = 0; k8 < 4; ++k8) {
+                                const uint64_t db = umma_desc(v_u + kc * 8192 + k8 * 32, 16, 1024);
+                                mma_ts(tmem + (uint32_t)(b * UBN), tmem + COL_SH + 32 * kc + 8 * k8, db, idesc_u,
+                                       (kc | k8) ? 1u : 0u);
+                            }
+                        mma_commit(smem_u32(&afull[b]));
+                        mma_commit(smem_u32(&vempty[s]));
+                        if (last_of_rb(t)) mma_commit(smem_u32(shfree));
+                    }
                 }
             }
         }
-    } else if (warp >= 4 && warp < 8) {
+    } else if (warp < 8) {
         // ---------------- L tile epilogue, L+ into TMEM, S^ refills ----------------
         const int r = threadIdx.x - 128;  // tile row = TMEM lane
         const uint32_t lane_base = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
@@ -278,19 +286,18 @@ k_tc_update_s(const float *__restrict__ ShT, int n, int q, const __grid_constant
             tc_fence_after();
             const int row = rb * 128 + r;
             const float4 *src = (const float4 *)(ShT + (size_t)row * q);
-            // 64 columns per batch: all loads of a batch are in flight together
+            // 32 columns per batch: all loads of a batch are in flight together
 #pragma unroll
-            for (int b0 = 0; b0 < KC * 32; b0 += 64) {
-                float4 v[16];
+            for (int b0 = 0; b0 < KC * 32; b0 += 32) {
+                float4 v[8];
 #pragma unroll
-                for (int j = 0; j < 16; ++j) {
+                for (int j = 0; j < 8; ++j) {
                     const int c = b0 + 4 * j;
                     v[j] = make_float4(0.f, 0.f, 0.f, 0.f);
-                    if (c < KC * 32 && row < n && c < q) v[j] = src[c >> 2];  // q % 4 == 0
+                    if (row < n && c < q) v[j] = src[c >> 2];  // q % 4 == 0
                 }
 #pragma unroll
-                for (int c0 = 0; c0 < 64; c0 += 16) {
-                    if (b0 + c0 >= KC * 32) break;
+                for (int c0 = 0; c0 < 32; c0 += 16) {
                     uint32_t w[16];
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
@@ -321,23 +328,27 @@ k_tc_update_s(const float *__restrict__ ShT, int n, int q, const __grid_constant
             if (do_update) {
                 if (!wwait(&afull[b], (i >> 1) & 1)) break;
                 tc_fence_after();
-                uint32_t v[UBN];
                 const uint32_t ta = lane_base + (uint32_t)(b * UBN);
+                // the accumulator in two 32-column halves (one wait each)
 #pragma unroll
-                for (int c0 = 0; c0 < UBN; c0 += 16)
-                    asm volatile(
-                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
-                        "%11, %12, %13, %14, %15}, [%16];"
-                        : "=r"(v[c0]), "=r"(v[c0 + 1]), "=r"(v[c0 + 2]), "=r"(v[c0 + 3]), "=r"(v[c0 + 4]),
-                          "=r"(v[c0 + 5]), "=r"(v[c0 + 6]), "=r"(v[c0 + 7]), "=r"(v[c0 + 8]), "=r"(v[c0 + 9]),
-                          "=r"(v[c0 + 10]), "=r"(v[c0 + 11]), "=r"(v[c0 + 12]), "=r"(v[c0 + 13]), "=r"(v[c0 + 14]),
-                          "=r"(v[c0 + 15])
-                        : "r"(ta + c0));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                for (int hc = 0; hc < UBN; hc += 32) {
+                    uint32_t v[32];
+#pragma unroll
+                    for (int c0 = 0; c0 < 32; c0 += 16)
+                        asm volatile(
+                            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+                            "%11, %12, %13, %14, %15}, [%16];"
+                            : "=r"(v[c0]), "=r"(v[c0 + 1]), "=r"(v[c0 + 2]), "=r"(v[c0 + 3]), "=r"(v[c0 + 4]),
+                              "=r"(v[c0 + 5]), "=r"(v[c0 + 6]), "=r"(v[c0 + 7]), "=r"(v[c0 + 8]), "=r"(v[c0 + 9]),
+                              "=r"(v[c0 + 10]), "=r"(v[c0 + 11]), "=r"(v[c0 + 12]), "=r"(v[c0 + 13]),
+                              "=r"(v[c0 + 14]), "=r"(v[c0 + 15])
+                            : "r"(ta + hc + c0));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                    for (int c = 0; c < 32; ++c) lp[hc + c] += __uint_as_float(v[c]);
+                }
                 tc_fence_before();
                 mbar_arrive(smem_u32(&aempty[b]));
-#pragma unroll
-                for (int c = 0; c < UBN; ++c) lp[c] += __uint_as_float(v[c]);
             }
             // L+ of this tile as the A operand of its S_next product (after the previous one is read)
             if (i >= 1 && !wwait(lempty, (i - 1) & 1)) break;
@@ -358,7 +369,8 @@ k_tc_update_s(const float *__restrict__ ShT, int n, int q, const __grid_constant
             // the update MMAs of this row block are done once its last tile drained: refill S^
             if (do_update && last_of_rb(t) && i + 1 < nt) load_sh(rb + 1);
         }
-    } else if (warp >= 8) {
+    } else {
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(REG_DRAIN));
         // ---------------- L+ stores and S_next chunks ----------------
         const int wq = warp & 3;
         const uint32_t lane_base = tmem + ((uint32_t)(32 * wq) << 16);
@@ -380,13 +392,12 @@ k_tc_update_s(const float *__restrict__ ShT, int n, int q, const __grid_constant
                 __syncwarp();
 #pragma unroll
                 for (int c0 = 0; c0 < UBN; c0 += 32) {
-                    uint32_t v0[16], v1[16];
-                    tmem_ld16(lane_base + COL_LHI + c0, v0);
-                    tmem_ld16(lane_base + COL_LHI + c0 + 16, v1);
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        ow[(c0 + j) * 32 + lane] = __uint_as_float(v0[j]);
-                        ow[(c0 + 16 + j) * 32 + lane] = __uint_as_float(v1[j]);
+                    for (int c1 = c0; c1 < c0 + 32; c1 += 16) {
+                        uint32_t v0[16];
+                        tmem_ld16(lane_base + COL_LHI + c1, v0);
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) ow[(c1 + j) * 32 + lane] = __uint_as_float(v0[j]);
                     }
                 }
             }
