@@ -46,6 +46,16 @@ struct Cfg {
     // which is what held the two shared-memory-operand MMAs back (measured on
     // GB300: 0.31 against 0.36 ms for a 16384 x 16384 x 128 product).
     static constexpr bool HI_TMEM = AMN != 0 || TERMS == 3;
+    // A k-step of a 3-term product issues two MMAs instead of three: hi x [B | B lo]
+    // is one MMA of width 2 BN (B lo follows B in the stage, so the two form one
+    // K-major operand of 2 BN rows) and lo x B the other.  The MMA issue rate, not
+    // the arithmetic, bounds these products on GB300 (halving N leaves the time of
+    // a 16384 x 16384 x 128 product unchanged), so fewer, wider MMAs are faster.
+    // The accumulator is then 2 BN columns wide ([hi B + lo B | hi B lo], summed by
+    // the drain) and single-buffered.
+    static constexpr bool PACK = TERMS == 3 && 2 * BN <= 256;
+    static constexpr int ACC_COLS = PACK ? 2 * BN : BN;  // one accumulator
+    static constexpr int NACC = PACK ? 1 : 2;            // accumulators (chunks alternate when 2)
     static constexpr bool LO_TMEM = TERMS >= 2;
     static constexpr bool CONVERT = HI_TMEM || LO_TMEM;
     static constexpr int LO_OFF = HI_TMEM ? 32 : 0;  // TMEM column of lo within a stage
@@ -55,7 +65,7 @@ struct Cfg {
     static constexpr int A_TMEM_COLS = 32 * ((HI_TMEM ? 1 : 0) + (LO_TMEM ? 1 : 0));
     // TMEM: two chunk accumulators (2 BN columns), then the A stages
     static constexpr int STAGES_SMEM = (200 * 1024) / STAGE_BYTES;
-    static constexpr int STAGES_TMEM = CONVERT ? (512 - 2 * BN) / A_TMEM_COLS : 8;
+    static constexpr int STAGES_TMEM = CONVERT ? (512 - NACC * ACC_COLS) / A_TMEM_COLS : 8;
     static constexpr int STAGES_A = STAGES_SMEM < STAGES_TMEM ? STAGES_SMEM : STAGES_TMEM;
     static constexpr int STAGES = STAGES_A > 8 ? 8 : STAGES_A;
     static constexpr int TMEM_COLS = CONVERT ? 512 : (2 * BN < 32 ? 32 : 2 * BN);
@@ -188,7 +198,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     auto stage_a = [&](int s) { return smem + s * CF::STAGE_BYTES; };
     auto stage_b = [&](int s) { return smem + s * CF::STAGE_BYTES + CF::A_BYTES; };
     auto stage_blo = [&](int s) { return smem + s * CF::STAGE_BYTES + CF::A_BYTES + CF::B_BYTES; };
-    auto a_col = [&](int s) { return (uint32_t)(2 * BN + s * CF::A_TMEM_COLS); };
+    auto a_col = [&](int s) { return (uint32_t)(CF::NACC * CF::ACC_COLS + s * CF::A_TMEM_COLS); };
 
     if (warp == 0) {
         // ---------------- TMA producer (warp 0) ----------------
@@ -221,6 +231,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         // ---------------- MMA issuer (warp 1) ----------------
         if (lane == 0) {
             const uint32_t idesc = idesc_tf32(BN, 0);
+            const uint32_t idesc2 = idesc_tf32(CF::PACK ? 2 * BN : BN, 0);  // hi x [B | B lo]
             int c = -1;           // chunk being accumulated
             int kb = kb_b, p = 0;  // k-block in the tile, position in the segment
             for (int i = 0; i < nk; ++i) {
@@ -228,13 +239,17 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                 const bool cstart = (p % CHUNK_KB) == 0;
                 const bool cend = ((p + 1) % CHUNK_KB) == 0 || kb + 1 == nkb || i + 1 == nk;
                 if (cstart) ++c;
-                const int b = c & 1;
-                if (cstart && c >= 2 && !mbar_wait(smem_u32(&chunk_free[b]), ((c >> 1) - 1) & 1, err, abort_flag))
-                    break;
+                const int b = CF::NACC == 2 ? (c & 1) : 0;
+                if (CF::NACC == 2) {
+                    if (cstart && c >= 2 && !mbar_wait(smem_u32(&chunk_free[b]), ((c >> 1) - 1) & 1, err, abort_flag))
+                        break;
+                } else {
+                    if (cstart && c >= 1 && !mbar_wait(smem_u32(&chunk_free[0]), (c - 1) & 1, err, abort_flag)) break;
+                }
                 const uint32_t wb = CF::CONVERT ? smem_u32(&conv[s]) : smem_u32(&full[s]);
                 if (!mbar_wait(wb, (i / STAGES) & 1, err, abort_flag)) break;
                 tc_fence_after();
-                const uint32_t dacc = tmem + (uint32_t)(b * BN);
+                const uint32_t dacc = tmem + (uint32_t)(b * CF::ACC_COLS);
                 const uint32_t a_s = smem_u32(stage_a(s)), b_hi = smem_u32(stage_b(s)), b_lo = smem_u32(stage_blo(s));
                 const uint32_t ta = tmem + a_col(s);
 #pragma unroll
@@ -242,21 +257,24 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                     // K = 8 TF32 per MMA: 32 bytes along a 128-byte swizzle row, 8 TMEM columns
                     const uint64_t db_hi = umma_desc(b_hi + kk * 32, 16, 1024);
                     const uint32_t first = (cstart && kk == 0) ? 0u : 1u;  // each chunk starts a fresh sum
-                    auto mma_hi = [&](uint64_t db, uint32_t accum) {       // A hi x db
+                    auto mma_hi = [&](uint64_t db, uint32_t accum, uint32_t id) {  // A hi x db
                         if (CF::HI_TMEM)
-                            mma_tf32_ts(dacc, ta + 8 * kk, db, idesc, accum);
+                            mma_tf32_ts(dacc, ta + 8 * kk, db, id, accum);
                         else
-                            mma_tf32(dacc, umma_desc(a_s + kk * 32, 16, 1024), db, idesc, accum);
+                            mma_tf32(dacc, umma_desc(a_s + kk * 32, 16, 1024), db, id, accum);
                     };
-                    if (TERMS == 3) {
+                    if (CF::PACK) {
+                        mma_hi(db_hi, first, idesc2);                                      // hi x [hi | lo]
+                        mma_tf32_ts(dacc, ta + CF::LO_OFF + 8 * kk, db_hi, idesc, 1u);     // lo x hi
+                    } else if (TERMS == 3) {
                         mma_tf32_ts(dacc, ta + CF::LO_OFF + 8 * kk, db_hi, idesc, first);  // lo x hi
-                        mma_hi(umma_desc(b_lo + kk * 32, 16, 1024), 1u);                  // hi x lo
-                        mma_hi(db_hi, 1u);                                                 // hi x hi
+                        mma_hi(umma_desc(b_lo + kk * 32, 16, 1024), 1u, idesc);           // hi x lo
+                        mma_hi(db_hi, 1u, idesc);                                          // hi x hi
                     } else if (TERMS == 2) {  // B exact in TF32
                         mma_tf32_ts(dacc, ta + CF::LO_OFF + 8 * kk, db_hi, idesc, first);  // lo x B
-                        mma_hi(db_hi, 1u);                                                 // hi x B
+                        mma_hi(db_hi, 1u, idesc);                                          // hi x B
                     } else {
-                        mma_hi(db_hi, first);
+                        mma_hi(db_hi, first, idesc);
                     }
                 }
                 mma_commit(smem_u32(&empty[s]));
@@ -312,15 +330,23 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         bool fresh = true;  // next chunk starts a segment
         while (u < u_e) {
             const int len = min(CHUNK_KB, min(nkb - kb, u_e - u));
-            const int b = c & 1;
-            if (!mbar_wait(smem_u32(&chunk_full[b]), (c >> 1) & 1, err, abort_flag)) break;
+            const int b = CF::NACC == 2 ? (c & 1) : 0;
+            const uint32_t ph = CF::NACC == 2 ? ((c >> 1) & 1) : (c & 1);
+            if (!mbar_wait(smem_u32(&chunk_full[b]), ph, err, abort_flag)) break;
             tc_fence_after();
             // the first chunk of a segment starts the sum: clear the running value by mask
             const uint32_t keep = fresh ? 0u : 0xFFFFFFFFu;
 #pragma unroll
             for (int c0 = 0; c0 < BN; c0 += 16) {
                 uint32_t rr[16];
-                tmem_ld16(tmem + ((uint32_t)(32 * wq) << 16) + (uint32_t)(b * BN + c0), rr);
+                const uint32_t ta = tmem + ((uint32_t)(32 * wq) << 16) + (uint32_t)(b * CF::ACC_COLS + c0);
+                tmem_ld16(ta, rr);
+                if (CF::PACK) {  // the hi x B lo half of the accumulator
+                    uint32_t r2[16];
+                    tmem_ld16(ta + BN, r2);
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) rr[j] = __float_as_uint(__uint_as_float(rr[j]) + __uint_as_float(r2[j]));
+                }
 #pragma unroll
                 for (int j = 0; j < 16; ++j)
                     run[c0 + j] = __uint_as_float(__float_as_uint(run[c0 + j]) & keep) + __uint_as_float(rr[j]);
