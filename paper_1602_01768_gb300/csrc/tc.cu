@@ -4,8 +4,10 @@
 // When the output has fewer tiles than the GPU has SMs the launch is
 // stream-K: one CTA per SM, each taking an equal contiguous run of units in
 // (tile, k-block) order; every piece of a tile that a CTA covers (a segment)
-// is written as a partial tile and the pieces are summed afterwards in CTA
-// order, so results are deterministic.  Otherwise each CTA owns one tile.
+// is written as a partial tile, and the CTA that finishes a tile's last piece
+// (an atomic count per tile and 32-row quarter tells it so) sums the pieces in
+// CTA order and writes the output, so results are deterministic and no second
+// kernel runs.  Otherwise each CTA owns one tile.
 // Warp roles, 384 threads:
 //   warp 0      TMA producer: streams 128 x 32 tiles of op(A) and BN x 32
 //               tiles of B (and of B's lo part) with 128-byte swizzle into a
@@ -74,6 +76,11 @@ struct Cfg {
 };
 
 __device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+
+// Register split of the GEMM CTA (setmaxnreg): warps 0-7 drop to GEMM_REG_LOW,
+// the drain warps 8-11 rise to GEMM_REG_DRAIN.
+constexpr int GEMM_REG_LOW = 120, GEMM_REG_DRAIN = 208;
+static_assert(128 * (2 * GEMM_REG_LOW + GEMM_REG_DRAIN) <= 384 * 168, "register split");
 
 // lo = x - hi(x), elementwise over a column-major rows x cols panel (ld).  The
 // tensor core reads an FP32 operand of kind::tf32 as its top 19 bits (the low
@@ -144,7 +151,7 @@ __global__ void __launch_bounds__(384, 1)
 k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
           const __grid_constant__ CUtensorMap tmBlo, int M, int N, int mt, int nkb, long long U, int maxseg,
           float alpha, float beta, const float *Cin, int64_t ldcin, float *C, int64_t ldc, int ctrans, float *part,
-          const int *status, int *err)
+          int *tile_cnt, const int *status, int *err)
 {
     using CF = Cfg<BN, TERMS, AMN>;
     constexpr int STAGES = CF::STAGES;
@@ -200,93 +207,101 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     auto stage_blo = [&](int s) { return smem + s * CF::STAGE_BYTES + CF::A_BYTES + CF::B_BYTES; };
     auto a_col = [&](int s) { return (uint32_t)(CF::NACC * CF::ACC_COLS + s * CF::A_TMEM_COLS); };
 
-    if (warp == 0) {
-        // ---------------- TMA producer (warp 0) ----------------
-        if (lane == 0) {
-            int t = t_b, kb = kb_b, m0 = (t % mt) * BM, n0 = (t / mt) * BN;
-            for (int i = 0; i < nk; ++i) {
-                const int s = i % STAGES;
-                if (i >= STAGES && !mbar_wait(smem_u32(&empty[s]), ((i / STAGES) - 1) & 1, err, abort_flag)) break;
-                const uint32_t fb = smem_u32(&full[s]);
-                mbar_expect_tx(fb, CF::STAGE_BYTES);
-                const int k = kb * BK;
-                if (AMN) {
-#pragma unroll
-                    for (int c = 0; c < BM / 32; ++c)
-                        tma_load_2d(smem_u32(stage_a(s) + c * 4096), &tmA, m0 + 32 * c, k, fb);
-                } else {
-                    tma_load_2d(smem_u32(stage_a(s)), &tmA, k, m0, fb);
-                }
-                tma_load_2d(smem_u32(stage_b(s)), &tmB, k, n0, fb);
-                if (TERMS == 3) tma_load_2d(smem_u32(stage_blo(s)), &tmBlo, k, n0, fb);  // B lo, split once per call
-                if (++kb == nkb) {
-                    kb = 0;
-                    ++t;
-                    m0 = (t % mt) * BM;
-                    n0 = (t / mt) * BN;
-                }
-            }
-        }
-    } else if (warp == 1) {
-        // ---------------- MMA issuer (warp 1) ----------------
-        if (lane == 0) {
-            const uint32_t idesc = idesc_tf32(BN, 0);
-            const uint32_t idesc2 = idesc_tf32(CF::PACK ? 2 * BN : BN, 0);  // hi x [B | B lo]
-            int c = -1;           // chunk being accumulated
-            int kb = kb_b, p = 0;  // k-block in the tile, position in the segment
-            for (int i = 0; i < nk; ++i) {
-                const int s = i % STAGES;
-                const bool cstart = (p % CHUNK_KB) == 0;
-                const bool cend = ((p + 1) % CHUNK_KB) == 0 || kb + 1 == nkb || i + 1 == nk;
-                if (cstart) ++c;
-                const int b = CF::NACC == 2 ? (c & 1) : 0;
-                if (CF::NACC == 2) {
-                    if (cstart && c >= 2 && !mbar_wait(smem_u32(&chunk_free[b]), ((c >> 1) - 1) & 1, err, abort_flag))
-                        break;
-                } else {
-                    if (cstart && c >= 1 && !mbar_wait(smem_u32(&chunk_free[0]), (c - 1) & 1, err, abort_flag)) break;
-                }
-                const uint32_t wb = CF::CONVERT ? smem_u32(&conv[s]) : smem_u32(&full[s]);
-                if (!mbar_wait(wb, (i / STAGES) & 1, err, abort_flag)) break;
-                tc_fence_after();
-                const uint32_t dacc = tmem + (uint32_t)(b * CF::ACC_COLS);
-                const uint32_t a_s = smem_u32(stage_a(s)), b_hi = smem_u32(stage_b(s)), b_lo = smem_u32(stage_blo(s));
-                const uint32_t ta = tmem + a_col(s);
-#pragma unroll
-                for (int kk = 0; kk < BK / 8; ++kk) {
-                    // K = 8 TF32 per MMA: 32 bytes along a 128-byte swizzle row, 8 TMEM columns
-                    const uint64_t db_hi = umma_desc(b_hi + kk * 32, 16, 1024);
-                    const uint32_t first = (cstart && kk == 0) ? 0u : 1u;  // each chunk starts a fresh sum
-                    auto mma_hi = [&](uint64_t db, uint32_t accum, uint32_t id) {  // A hi x db
-                        if (CF::HI_TMEM)
-                            mma_tf32_ts(dacc, ta + 8 * kk, db, id, accum);
-                        else
-                            mma_tf32(dacc, umma_desc(a_s + kk * 32, 16, 1024), db, id, accum);
-                    };
-                    if (CF::PACK) {
-                        mma_hi(db_hi, first, idesc2);                                      // hi x [hi | lo]
-                        mma_tf32_ts(dacc, ta + CF::LO_OFF + 8 * kk, db_hi, idesc, 1u);     // lo x hi
-                    } else if (TERMS == 3) {
-                        mma_tf32_ts(dacc, ta + CF::LO_OFF + 8 * kk, db_hi, idesc, first);  // lo x hi
-                        mma_hi(umma_desc(b_lo + kk * 32, 16, 1024), 1u, idesc);           // hi x lo
-                        mma_hi(db_hi, 1u, idesc);                                          // hi x hi
-                    } else if (TERMS == 2) {  // B exact in TF32
-                        mma_tf32_ts(dacc, ta + CF::LO_OFF + 8 * kk, db_hi, idesc, first);  // lo x B
-                        mma_hi(db_hi, 1u, idesc);                                          // hi x B
+    // registers: the drain warps keep BN running sums per thread; the single-thread
+    // roles and the converter need far fewer.  The split must fit in what the CTA
+    // was launched with (384 x 168; launch_bn checks the compiled count).
+    constexpr int REG_LOW = GEMM_REG_LOW, REG_DRAIN = GEMM_REG_DRAIN;
+    if (warp < 4) {
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(REG_LOW));
+        if (warp == 0) {
+            // ---------------- TMA producer (warp 0) ----------------
+            if (lane == 0) {
+                int t = t_b, kb = kb_b, m0 = (t % mt) * BM, n0 = (t / mt) * BN;
+                for (int i = 0; i < nk; ++i) {
+                    const int s = i % STAGES;
+                    if (i >= STAGES && !mbar_wait(smem_u32(&empty[s]), ((i / STAGES) - 1) & 1, err, abort_flag)) break;
+                    const uint32_t fb = smem_u32(&full[s]);
+                    mbar_expect_tx(fb, CF::STAGE_BYTES);
+                    const int k = kb * BK;
+                    if (AMN) {
+    #pragma unroll
+                        for (int c = 0; c < BM / 32; ++c)
+                            tma_load_2d(smem_u32(stage_a(s) + c * 4096), &tmA, m0 + 32 * c, k, fb);
                     } else {
-                        mma_hi(db_hi, first, idesc);
+                        tma_load_2d(smem_u32(stage_a(s)), &tmA, k, m0, fb);
+                    }
+                    tma_load_2d(smem_u32(stage_b(s)), &tmB, k, n0, fb);
+                    if (TERMS == 3) tma_load_2d(smem_u32(stage_blo(s)), &tmBlo, k, n0, fb);  // B lo, split once per call
+                    if (++kb == nkb) {
+                        kb = 0;
+                        ++t;
+                        m0 = (t % mt) * BM;
+                        n0 = (t / mt) * BN;
                     }
                 }
-                mma_commit(smem_u32(&empty[s]));
-                if (cend) mma_commit(smem_u32(&chunk_full[b]));
-                ++p;
-                if (++kb == nkb) {
-                    kb = 0;
-                    p = 0;
+            }
+        } else if (warp == 1) {
+            // ---------------- MMA issuer (warp 1) ----------------
+            if (lane == 0) {
+                const uint32_t idesc = idesc_tf32(BN, 0);
+                const uint32_t idesc2 = idesc_tf32(CF::PACK ? 2 * BN : BN, 0);  // hi x [B | B lo]
+                int c = -1;           // chunk being accumulated
+                int kb = kb_b, p = 0;  // k-block in the tile, position in the segment
+                for (int i = 0; i < nk; ++i) {
+                    const int s = i % STAGES;
+                    const bool cstart = (p % CHUNK_KB) == 0;
+                    const bool cend = ((p + 1) % CHUNK_KB) == 0 || kb + 1 == nkb || i + 1 == nk;
+                    if (cstart) ++c;
+                    const int b = CF::NACC == 2 ? (c & 1) : 0;
+                    if (CF::NACC == 2) {
+                        if (cstart && c >= 2 && !mbar_wait(smem_u32(&chunk_free[b]), ((c >> 1) - 1) & 1, err, abort_flag))
+                            break;
+                    } else {
+                        if (cstart && c >= 1 && !mbar_wait(smem_u32(&chunk_free[0]), (c - 1) & 1, err, abort_flag)) break;
+                    }
+                    const uint32_t wb = CF::CONVERT ? smem_u32(&conv[s]) : smem_u32(&full[s]);
+                    if (!mbar_wait(wb, (i / STAGES) & 1, err, abort_flag)) break;
+                    tc_fence_after();
+                    const uint32_t dacc = tmem + (uint32_t)(b * CF::ACC_COLS);
+                    const uint32_t a_s = smem_u32(stage_a(s)), b_hi = smem_u32(stage_b(s)), b_lo = smem_u32(stage_blo(s));
+                    const uint32_t ta = tmem + a_col(s);
+    #pragma unroll
+                    for (int kk = 0; kk < BK / 8; ++kk) {
+                        // K = 8 TF32 per MMA: 32 bytes along a 128-byte swizzle row, 8 TMEM columns
+                        const uint64_t db_hi = umma_desc(b_hi + kk * 32, 16, 1024);
+                        const uint32_t first = (cstart && kk == 0) ? 0u : 1u;  // each chunk starts a fresh sum
+                        auto mma_hi = [&](uint64_t db, uint32_t accum, uint32_t id) {  // A hi x db
+                            if (CF::HI_TMEM)
+                                mma_tf32_ts(dacc, ta + 8 * kk, db, id, accum);
+                            else
+                                mma_tf32(dacc, umma_desc(a_s + kk * 32, 16, 1024), db, id, accum);
+                        };
+                        if (CF::PACK) {
+                            mma_hi(db_hi, first, idesc2);                                      // hi x [hi | lo]
+                            mma_tf32_ts(dacc, ta + CF::LO_OFF + 8 * kk, db_hi, idesc, 1u);     // lo x hi
+                        } else if (TERMS == 3) {
+                            mma_tf32_ts(dacc, ta + CF::LO_OFF + 8 * kk, db_hi, idesc, first);  // lo x hi
+                            mma_hi(umma_desc(b_lo + kk * 32, 16, 1024), 1u, idesc);           // hi x lo
+                            mma_hi(db_hi, 1u, idesc);                                          // hi x hi
+                        } else if (TERMS == 2) {  // B exact in TF32
+                            mma_tf32_ts(dacc, ta + CF::LO_OFF + 8 * kk, db_hi, idesc, first);  // lo x B
+                            mma_hi(db_hi, 1u, idesc);                                          // hi x B
+                        } else {
+                            mma_hi(db_hi, first, idesc);
+                        }
+                    }
+                    mma_commit(smem_u32(&empty[s]));
+                    if (cend) mma_commit(smem_u32(&chunk_full[b]));
+                    ++p;
+                    if (++kb == nkb) {
+                        kb = 0;
+                        p = 0;
+                    }
                 }
             }
         }
-    } else if (warp >= 4 && warp < 8) {
+    } else if (warp < 8) {
+        asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(REG_LOW));
         // ---------------- converter (warps 4-7): A lo [and hi] into TMEM ----------------
         if (CF::CONVERT) {
             const int r = threadIdx.x - 128;  // tile row = TMEM lane
@@ -316,7 +331,8 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                 mbar_arrive(smem_u32(&conv[s]));
             }
         }
-    } else if (warp >= 8) {
+    } else {
+        asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(REG_DRAIN));
         // ---------------- drain and epilogue (warps 8-11) ----------------
         // Running sum of the finished K chunks, one tile row per thread, added on
         // the CUDA cores with round-to-nearest.  The tensor core's FP32 accumulation
@@ -332,7 +348,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
             const int len = min(CHUNK_KB, min(nkb - kb, u_e - u));
             const int b = CF::NACC == 2 ? (c & 1) : 0;
             const uint32_t ph = CF::NACC == 2 ? ((c >> 1) & 1) : (c & 1);
-            if (!mbar_wait(smem_u32(&chunk_full[b]), ph, err, abort_flag)) break;
+            if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&chunk_full[b]), ph, err, abort_flag))) break;
             tc_fence_after();
             // the first chunk of a segment starts the sum: clear the running value by mask
             const uint32_t keep = fresh ? 0u : 0xFFFFFFFFu;
@@ -340,12 +356,15 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
             for (int c0 = 0; c0 < BN; c0 += 16) {
                 uint32_t rr[16];
                 const uint32_t ta = tmem + ((uint32_t)(32 * wq) << 16) + (uint32_t)(b * CF::ACC_COLS + c0);
-                tmem_ld16(ta, rr);
-                if (CF::PACK) {  // the hi x B lo half of the accumulator
+                if (CF::PACK) {  // both halves of the accumulator ([.. | hi x B lo]), one wait
                     uint32_t r2[16];
-                    tmem_ld16(ta + BN, r2);
+                    tmem_ld16_async(ta, rr);
+                    tmem_ld16_async(ta + BN, r2);
+                    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
                     for (int j = 0; j < 16; ++j) rr[j] = __float_as_uint(__uint_as_float(rr[j]) + __uint_as_float(r2[j]));
+                } else {
+                    tmem_ld16(ta, rr);
                 }
 #pragma unroll
                 for (int j = 0; j < 16; ++j)
@@ -358,9 +377,43 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
             ++c;
             fresh = (kb == nkb || u == u_e);
             if (fresh) {
-                // segment finished: the whole tile (write C) or a partial tile in
-                // slot (CTA, segment index) of the workspace
-                if (part == nullptr) {
+                // segment finished.  Stream-K: write the partial tile into slot (CTA,
+                // segment index) of the workspace; the warp whose quarter of the tile
+                // is the last to arrive sums all pieces in CTA order and writes C.
+                bool write_c = (part == nullptr);
+                if (part != nullptr) {
+                    float *dst = part + ((size_t)blockIdx.x * maxseg + (t - t_b)) * (BM * BN) + 32 * wq + lane;
+#pragma unroll
+                    for (int j = 0; j < BN; ++j) dst[j * BM] = run[j];
+                    // CTAs whose units meet the tile: b0 (holds its first unit) .. b1 (its last)
+                    const long long t0 = (long long)t * nkb, t1 = t0 + nkb;
+                    auto cta_of = [&](long long unit) {
+                        int cb = (int)(unit * gridDim.x / U);
+                        while (cb + 1 < (int)gridDim.x && U * (cb + 1) / gridDim.x <= unit) ++cb;
+                        while (cb > 0 && U * cb / gridDim.x > unit) --cb;
+                        return cb;
+                    };
+                    const int b0 = cta_of(t0), b1 = cta_of(t1 - 1);
+                    __threadfence();
+                    __syncwarp();
+                    int old = 0;
+                    if (lane == 0) old = atomicAdd(&tile_cnt[4 * t + wq], 1);
+                    old = __shfl_sync(0xffffffffu, old, 0);
+                    if (old == b1 - b0) {  // every other piece is written
+                        if (lane == 0) tile_cnt[4 * t + wq] = 0;  // ready for the next launch
+                        __threadfence();
+#pragma unroll
+                        for (int j = 0; j < BN; ++j) run[j] = 0.f;
+                        for (int bb = b0; bb <= b1; ++bb) {
+                            const float *pp = part + ((size_t)bb * maxseg + (size_t)(t - (U * bb / gridDim.x) / nkb)) *
+                                                         (BM * BN) + 32 * wq + lane;
+#pragma unroll
+                            for (int j = 0; j < BN; ++j) run[j] += __ldcg(pp + j * BM);
+                        }
+                        write_c = true;
+                    }
+                }
+                if (write_c) {
                     const int m = (t % mt) * BM + 32 * wq + lane, n0 = (t / mt) * BN;
                     if (m < M) {
                         // element (m, n) at C[m + n ldc], or at C[n + m ldc] when ctrans
@@ -379,10 +432,6 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                             ci += sj;
                         }
                     }
-                } else {
-                    float *dst = part + ((size_t)blockIdx.x * maxseg + (t - t_b)) * (BM * BN) + 32 * wq + lane;
-#pragma unroll
-                    for (int j = 0; j < BN; ++j) dst[j * BM] = run[j];
                 }
                 if (kb == nkb) {
                     kb = 0;
@@ -398,43 +447,6 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                      "r"((uint32_t)CF::TMEM_COLS)
                      : "memory");
-    }
-}
-
-// Stream-K fix-up: C = alpha (sum of the partial tiles of every CTA whose
-// units overlap the tile, in CTA order) + beta Cin.  Block (tile, 32-column
-// group), thread = tile row.
-__global__ void k_streamk_reduce(int M, int N, int mt, int bn, int nkb, long long U, int G, int maxseg,
-                                 const float *part, float alpha, float beta, const float *Cin, int64_t ldcin,
-                                 float *C, int64_t ldc, int ctrans, const int *status)
-{
-    if (status_bad(status)) return;
-    const int t = blockIdx.x, r = threadIdx.x, j0 = blockIdx.y * 32;
-    const int m = (t % mt) * BM + r, n0 = (t / mt) * bn + j0;
-    const long long t0 = (long long)t * nkb, t1 = t0 + nkb;
-    int b = (int)(t0 * G / U);  // first CTA whose units reach into the tile
-    while (b + 1 < G && U * (b + 1) / G <= t0) ++b;
-    float s[32];
-#pragma unroll
-    for (int jj = 0; jj < 32; ++jj) s[jj] = 0.f;
-    for (; b < G; ++b) {
-        const long long u0 = U * b / G, u1 = U * (b + 1) / G;
-        if (u0 >= t1) break;
-        if (u1 == u0) continue;  // a CTA without units
-        const float *pp = part + ((size_t)b * maxseg + (size_t)(t - u0 / nkb)) * (BM * bn) + r + (size_t)j0 * BM;
-#pragma unroll
-        for (int jj = 0; jj < 32; ++jj) s[jj] += pp[(size_t)jj * BM];
-    }
-    if (m >= M) return;
-    const int64_t sm = ctrans ? ldc : 1, sn = ctrans ? 1 : ldc, si = ctrans ? ldcin : 1, sj = ctrans ? 1 : ldcin;
-#pragma unroll
-    for (int jj = 0; jj < 32; ++jj) {
-        const int nn = n0 + jj;
-        if (nn < N) {
-            float o = alpha * s[jj];
-            if (beta != 0.f) o = fmaf(beta, Cin[m * si + (int64_t)nn * sj], o);
-            C[m * sm + (int64_t)nn * sn] = o;
-        }
     }
 }
 
@@ -505,6 +517,8 @@ struct tc_plan {
     size_t part_cap = 0;
     float *blo = nullptr;  // lo part of the B operand (3-term products)
     size_t blo_cap = 0;
+    int *cnt = nullptr;  // stream-K arrival counts, 4 per tile, zero between launches
+    size_t cnt_cap = 0;
     int *err = nullptr;
 };
 
@@ -534,6 +548,7 @@ void tc_plan_destroy(tc_plan *p)
     if (!p) return;
     if (p->part) cudaFree(p->part);
     if (p->blo) cudaFree(p->blo);
+    if (p->cnt) cudaFree(p->cnt);
     if (p->err) cudaFree(p->err);
     delete p;
 }
@@ -558,6 +573,12 @@ static int launch_bn(tc_plan *p, cudaStream_t st, const CUtensorMap &ma, const C
     if (!attr) {
         if (cudaFuncSetAttribute(k_tc_gemm<BN, TERMS, AMN>, cudaFuncAttributeMaxDynamicSharedMemorySize, CF::SMEM) !=
             cudaSuccess)
+            return -1;
+        // the register split raises warps 8-11 out of what the CTA holds: refuse a
+        // build whose launch count leaves too few (setmaxnreg.inc would never return)
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, k_tc_gemm<BN, TERMS, AMN>) != cudaSuccess ||
+            384 * fa.numRegs < 128 * (2 * GEMM_REG_LOW + GEMM_REG_DRAIN))
             return -1;
         attr = true;
     }
@@ -586,15 +607,18 @@ static int launch_bn(tc_plan *p, cudaStream_t st, const CUtensorMap &ma, const C
             p->part_cap = need;
         }
         part = p->part;
+        if ((size_t)4 * tiles > p->cnt_cap) {
+            if (p->cnt) cudaFree(p->cnt);
+            p->cnt = nullptr;
+            p->cnt_cap = 0;
+            if (cudaMalloc(&p->cnt, sizeof(int) * 4 * tiles) != cudaSuccess) return -2;
+            if (cudaMemsetAsync(p->cnt, 0, sizeof(int) * 4 * tiles, st) != cudaSuccess) return -2;
+            p->cnt_cap = (size_t)4 * tiles;
+        }
     }
     rb_count_launch();
     k_tc_gemm<BN, TERMS, AMN><<<G, 384, CF::SMEM, st>>>(ma, mb, mblo, M, N, mt, nkb, U, maxseg, alpha, beta, Cin,
-                                                        ldcin, C, ldc, ctrans, part, status, err);
-    if (streamk) {
-        rb_count_launch();
-        k_streamk_reduce<<<dim3(tiles, BN / 32), BM, 0, st>>>(M, N, mt, BN, nkb, U, G, maxseg, part, alpha, beta, Cin,
-                                                              ldcin, C, ldc, ctrans, status);
-    }
+                                                        ldcin, C, ldc, ctrans, part, p->cnt, status, err);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 

@@ -488,6 +488,12 @@ int launch_update_s(cudaStream_t st, const float *ShT, int n, int q, const CUten
         if (cudaFuncSetAttribute(k_tc_update_s<KC>, cudaFuncAttributeMaxDynamicSharedMemorySize, CF::SMEM) !=
             cudaSuccess)
             return -1;
+        // the register split raises warps 8-11 out of what the CTA holds: refuse a
+        // build whose launch count leaves too few (setmaxnreg.inc would never return)
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, k_tc_update_s<KC>) != cudaSuccess ||
+            384 * fa.numRegs < 128 * (REG_ISSUE + 168 + REG_DRAIN))
+            return -1;
         attr = true;
     }
     const int nrb = (n + 127) / 128, ncb = (n + UBN - 1) / UBN;
