@@ -30,6 +30,8 @@ struct rb_ctx {
     bool s_valid = false;             // S holds L_k S~_k from the previous fused update
     float *Spart = nullptr;           // partial S blocks of the fused update
     size_t spart_cap = 0;
+    float *Slo = nullptr, *Glo = nullptr;  // lo parts (x - hi(x)) of S and G for the 3-term products
+    bool slo_valid = false;                // Slo belongs to the S in place
     float *Bv = nullptr, *Bs = nullptr;  // tensor-core V and S^: [D^-T; -C^-T] (2q x q) and C^-T (q x q)
     float *Mf = nullptr, *Nf = nullptr;  // FP32 Gram products S^T A S and S~^T S~ (tensor-core path)
     tc_plan *tc2 = nullptr;              // plan (own workspace) for the side stream's tensor-core GEMMs
@@ -144,6 +146,8 @@ static void destroy_ctx(rb_ctx *h)
     rb_freet(h->Bv);
     rb_freet(h->Bs);
     rb_freet(h->Spart);
+    rb_freet(h->Slo);
+    rb_freet(h->Glo);
     rb_freet(h->Mf);
     rb_freet(h->Nf);
     if (h->tc2) tc_plan_destroy(h->tc2);
@@ -286,6 +290,8 @@ static rb_status alloc_sketch_workspace(rb_ctx *h)
         if (h->method == RB_METHOD_ADARBFGS && q <= 128) {
             h->spart_cap = tc_update_s_workspace(h->n, (int)q);
             RB_TRY(rb_alloc(&h->Spart, h->spart_cap * sizeof(float)));
+            RB_TRY(rb_alloc(&h->Slo, nq));
+            RB_TRY(rb_alloc(&h->Glo, nq));
         }
     }
     RB_TRY(rb_alloc(&h->V, nq));
@@ -619,9 +625,13 @@ static void ada_step_tc(rb_ctx *h)
     if (!fuse || !h->s_valid) {
         ada_draw<float>(h, St, h->k);
         mark(h, "sketch");
+        h->slo_valid = false;
         if (fuse) {  // S = L S~ from the fused kernel without the update, so every S comes from one path
-            const int rc = tc_update_next_s(st, n, q, Sh, V, L, n, St, S, 0, h->Spart, h->spart_cap, stp);
-            if (rc != 0) tc_gemm_nk(h->tc, st, acc == 3 ? 2 : acc, TC_A_MN, n, q, n, L, n, St, n, S, n, stp);
+            const int rc = tc_update_next_s(st, n, q, Sh, V, L, n, St, S, 0, h->Spart, h->spart_cap, stp, h->Slo);
+            if (rc != 0)
+                tc_gemm_nk(h->tc, st, acc == 3 ? 2 : acc, TC_A_MN, n, q, n, L, n, St, n, S, n, stp);
+            else
+                h->slo_valid = h->Slo != nullptr;
         } else {
             // S = L S~ (A = L, M-contiguous); S~ is exact in TF32, so the split needs only L's two parts
             tc_gemm_nk(h->tc, st, acc == 3 ? 2 : acc, TC_A_MN, n, q, n, L, n, St, n, S, n, stp);
@@ -639,13 +649,18 @@ static void ada_step_tc(rb_ctx *h)
             launch_core_ada32(side, q, h->N, nullptr, Di, nullptr, h->d_status);
         }
     }
-    tc_gemm_nk(h->tc, st, acc, TC_A_K, n, q, n, A, n, S, n, G, n, stp, rsv_g);  // G = A S  (A symmetric)
+    // G = A S (A symmetric); S's lo part comes from the kernel that formed S, and G's is
+    // written beside G for the two products that take G as their B (W and S^T G)
+    const bool glo = acc == 3 && h->Glo != nullptr;
+    tc_gemm_nk_lo(h->tc, st, acc, TC_A_K, n, q, n, A, n, S, (acc == 3 && h->slo_valid) ? h->Slo : nullptr, n, G,
+                  glo ? h->Glo : nullptr, n, stp, rsv_g);
     mark(h, fork ? "G=AS | D core" : "G=AS");
     if (fork) {
         cudaEventRecord(h->ev_g, st);
         cudaStreamWaitEvent(side, h->ev_g, 0);
         if (tcv) {  // S^T A S = S^T G (3 x TF32) -> -C^-T into Bv, C^-T into Bs
-            tc_gemm_nk(h->tc2, side, 3, TC_A_K, q, q, n, S, n, G, n, h->Mf, q, stp, side_rsv);
+            tc_gemm_nk_lo(h->tc2, side, 3, TC_A_K, q, q, n, S, n, G, glo ? h->Glo : nullptr, n, h->Mf, nullptr, q,
+                          stp, side_rsv);
             launch_core_tr32(side, q, h->Mf, nullptr, h->Bv + cofs, 2 * q, -1.f, h->Bs, q, 1.f, h->d_status);
         } else {
             launch_gram<float>(side, n, q, q, S, n, G, n, h->part, h->M);    // S^T A S -> C^-1
@@ -662,7 +677,8 @@ static void ada_step_tc(rb_ctx *h)
             launch_core_ada<float>(st, q, h->M, h->N, Ci, Di, h->d_status);
         mark(h, "q x q core");
     }
-    tc_gemm_nk(h->tc, st, acc, TC_A_K, n, q, n, L, n, G, n, W, n, stp, rsv);  // W^T = L^T G (n x q)
+    tc_gemm_nk_lo(h->tc, st, acc, TC_A_K, n, q, n, L, n, G, glo ? h->Glo : nullptr, n, W, nullptr, n, stp,
+                  rsv);  // W^T = L^T G (n x q)
     if (fork) cudaStreamWaitEvent(st, h->ev_core, 0);                            // join: C^-1, D^-1 ready
     mark(h, fork ? "W=G^TL | C core" : "W=G^TL");
     if (tcv) {
@@ -681,11 +697,13 @@ static void ada_step_tc(rb_ctx *h)
     if (fuse) {
         // the next step's sketch, then L += S^ V fused with S = L S~_{k+1}
         ada_draw<float>(h, St_next, h->k + 1);
-        const int rc = tc_update_next_s(st, n, q, Sh, V, L, n, St_next, S, 1, h->Spart, h->spart_cap, stp);
+        const int rc = tc_update_next_s(st, n, q, Sh, V, L, n, St_next, S, 1, h->Spart, h->spart_cap, stp, h->Slo);
         if (rc == 0) {
             h->s_valid = true;
+            h->slo_valid = h->Slo != nullptr;
         } else {
             h->s_valid = false;
+            h->slo_valid = false;
             if (tc_update_persistent(h->tc, st, n, q, Sh, V, L, n, stp) != 0)
                 tc_update(h->tc, st, upd, n, q, Sh, V, L, n, stp);
         }

@@ -150,8 +150,8 @@ template <int BN, int TERMS, int AMN>
 __global__ void __launch_bounds__(384, 1)
 k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
           const __grid_constant__ CUtensorMap tmBlo, int M, int N, int mt, int nkb, long long U, int maxseg,
-          float alpha, float beta, const float *Cin, int64_t ldcin, float *C, int64_t ldc, int ctrans, float *part,
-          int *tile_cnt, const int *status, int *err)
+          float alpha, float beta, const float *Cin, int64_t ldcin, float *C, float *Clo, int64_t ldc, int ctrans,
+          float *part, int *tile_cnt, const int *status, int *err)
 {
     using CF = Cfg<BN, TERMS, AMN>;
     constexpr int STAGES = CF::STAGES;
@@ -421,12 +421,15 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                         const int64_t si = ctrans ? ldcin : 1, sj = ctrans ? 1 : ldcin;
                         float *cp = C + m * sm + (int64_t)n0 * sn;
                         const float *ci = Cin + m * si + (int64_t)n0 * sj;
+                        // C's lo part (x - hi(x)) beside C when a later product takes C as its B
+                        float *cl = Clo ? Clo + m * sm + (int64_t)n0 * sn : nullptr;
 #pragma unroll
                         for (int j = 0; j < BN; ++j) {
                             if (n0 + j < N) {
                                 float o = alpha * run[j];
                                 if (beta != 0.f) o = fmaf(beta, *ci, o);
                                 *cp = o;
+                                if (cl) cl[j * sn] = o - tf32_hi(o);
                             }
                             cp += sn;
                             ci += sj;
@@ -565,7 +568,7 @@ int tc_plan_error(tc_plan *p, cudaStream_t st)
 template <int BN, int TERMS, int AMN>
 static int launch_bn(tc_plan *p, cudaStream_t st, const CUtensorMap &ma, const CUtensorMap &mb,
                      const CUtensorMap &mblo, int M, int N, int K,
-                     float alpha, float beta, const float *Cin, int64_t ldcin, float *C, int64_t ldc,
+                     float alpha, float beta, const float *Cin, int64_t ldcin, float *C, float *Clo, int64_t ldc,
                      const int *status, int *err, int reserve, int ctrans)
 {
     using CF = Cfg<BN, TERMS, AMN>;
@@ -618,14 +621,15 @@ static int launch_bn(tc_plan *p, cudaStream_t st, const CUtensorMap &ma, const C
     }
     rb_count_launch();
     k_tc_gemm<BN, TERMS, AMN><<<G, 384, CF::SMEM, st>>>(ma, mb, mblo, M, N, mt, nkb, U, maxseg, alpha, beta, Cin,
-                                                        ldcin, C, ldc, ctrans, part, p->cnt, status, err);
+                                                        ldcin, C, Clo, ldc, ctrans, part, p->cnt, status, err);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
 template <int TERMS>
 static int launch_terms(tc_plan *p, cudaStream_t st, int a_layout, int M, int N, int K, float alpha, const float *A,
-                        int64_t lda, const float *B, int64_t ldb, float beta, const float *Cin, int64_t ldcin,
-                        float *C, int64_t ldc, const int *status, int *err, int reserve, int ctrans)
+                        int64_t lda, const float *B, const float *Blo, int64_t ldb, float beta, const float *Cin,
+                        int64_t ldcin, float *C, float *Clo, int64_t ldc, const int *status, int *err, int reserve,
+                        int ctrans)
 {
     const int a_mn = (a_layout == TC_A_MN);
     const int bn = N <= 32 ? 32 : N <= 64 ? 64 : 128;
@@ -633,7 +637,9 @@ static int launch_terms(tc_plan *p, cudaStream_t st, int a_layout, int M, int N,
     bool ok = a_mn ? make_map(&ma, A, M, K, lda, 32) : make_map(&ma, A, K, M, lda, BM);
     ok = ok && make_map(&mb, B, K, N, ldb, bn);
     CUtensorMap mblo = mb;
-    if (TERMS == 3) {
+    if (TERMS == 3 && Blo) {
+        ok = ok && make_map(&mblo, Blo, K, N, ldb, bn);  // lo part of B supplied by the caller
+    } else if (TERMS == 3) {
         // lo part of B, split once here rather than in every CTA (B is shared by all M tiles)
         const int ldlo = (K + 3) & ~3;  // 16-byte rows for TMA
         const size_t need = (size_t)ldlo * N;
@@ -652,10 +658,10 @@ static int launch_terms(tc_plan *p, cudaStream_t st, int a_layout, int M, int N,
     if (!ok) return -4;
 #define RB_TC_CASE(BNV)                                                                                     \
     case BNV:                                                                                                  \
-        return a_mn ? launch_bn<BNV, TERMS, 1>(p, st, ma, mb, mblo, M, N, K, alpha, beta, Cin, ldcin, C, ldc, status, \
-                                               err, reserve, ctrans)                                            \
-                    : launch_bn<BNV, TERMS, 0>(p, st, ma, mb, mblo, M, N, K, alpha, beta, Cin, ldcin, C, ldc, status, \
-                                               err, reserve, ctrans);
+        return a_mn ? launch_bn<BNV, TERMS, 1>(p, st, ma, mb, mblo, M, N, K, alpha, beta, Cin, ldcin, C, Clo, ldc, \
+                                               status, err, reserve, ctrans)                                    \
+                    : launch_bn<BNV, TERMS, 0>(p, st, ma, mb, mblo, M, N, K, alpha, beta, Cin, ldcin, C, Clo, ldc, \
+                                               status, err, reserve, ctrans);
     switch (bn) {
         RB_TC_CASE(32)
         RB_TC_CASE(64)
@@ -667,32 +673,44 @@ static int launch_terms(tc_plan *p, cudaStream_t st, int a_layout, int M, int N,
 
 static bool tma_ok(const void *ptr, int64_t ld) { return ((uintptr_t)ptr % 16 == 0) && (ld % 4 == 0); }
 
+// C's lo part after a CUDA-core product (the tensor-core epilogue writes it itself)
+static void split_after_simt(cudaStream_t st, int M, int N, const float *C, float *Clo, int64_t ldc)
+{
+    if (!Clo) return;
+    rb_count_launch();
+    k_split_lo<<<dim3((M + 255) / 256, N), 256, 0, st>>>(M, N, C, ldc, Clo, ldc);
+}
+
 static int tc_run(tc_plan *p, cudaStream_t st, int terms, int a_layout, int M, int N, int K, float alpha,
                   const float *A, int64_t lda, const float *B, int64_t ldb, float beta, const float *Cin,
-                  int64_t ldcin, float *C, int64_t ldc, const int *status, int reserve = 0, int ctrans = 0)
+                  int64_t ldcin, float *C, int64_t ldc, const int *status, int reserve = 0, int ctrans = 0,
+                  const float *Blo = nullptr, float *Clo = nullptr)
 {
     if (M <= 0 || N <= 0) return 0;
-    const bool ok = p && K > 0 && tma_ok(A, lda) && tma_ok(B, ldb);
+    if (Clo && (ctrans || terms == 1)) return -7;  // C's lo part: plain output of a split product only
+    const bool ok = p && K > 0 && tma_ok(A, lda) && tma_ok(B, ldb) && (!Blo || tma_ok(Blo, ldb));
     if (!ok && ctrans) return -6;  // the SIMT kernels have no transposed output
     if (!ok) {
         // SIMT fallback: alpha op(A) B + beta Cin (Cin copied to C first when distinct)
         if (beta != 0.f && Cin != C) launch_copy2d<float, float>(st, M, N, Cin, ldcin, C, ldc, 1.0);
         gemm_simt<float>(st, a_layout == TC_A_K, false, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, status);
+        split_after_simt(st, M, N, C, Clo, ldc);
         return 1;
     }
     int *err = status ? const_cast<int *>(status) : p->err;
     const int rc =
-        (terms == 3)   ? launch_terms<3>(p, st, a_layout, M, N, K, alpha, A, lda, B, ldb, beta, Cin, ldcin, C, ldc,
-                                         status, err, reserve, ctrans)
-        : (terms == 2) ? launch_terms<2>(p, st, a_layout, M, N, K, alpha, A, lda, B, ldb, beta, Cin, ldcin, C, ldc,
-                                         status, err, reserve, ctrans)
-                       : launch_terms<1>(p, st, a_layout, M, N, K, alpha, A, lda, B, ldb, beta, Cin, ldcin, C, ldc,
-                                         status, err, reserve, ctrans);
+        (terms == 3)   ? launch_terms<3>(p, st, a_layout, M, N, K, alpha, A, lda, B, Blo, ldb, beta, Cin, ldcin, C,
+                                         Clo, ldc, status, err, reserve, ctrans)
+        : (terms == 2) ? launch_terms<2>(p, st, a_layout, M, N, K, alpha, A, lda, B, nullptr, ldb, beta, Cin, ldcin,
+                                         C, Clo, ldc, status, err, reserve, ctrans)
+                       : launch_terms<1>(p, st, a_layout, M, N, K, alpha, A, lda, B, nullptr, ldb, beta, Cin, ldcin,
+                                         C, nullptr, ldc, status, err, reserve, ctrans);
     if (rc == 0) return 0;
     if (ctrans) return rc;
     // the tensor-core launch could not be set up (tensor map or workspace): run the same product on CUDA cores
     if (beta != 0.f && Cin != C) launch_copy2d<float, float>(st, M, N, Cin, ldcin, C, ldc, 1.0);
     gemm_simt<float>(st, a_layout == TC_A_K, false, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, status);
+    split_after_simt(st, M, N, C, Clo, ldc);
     return 1;
 }
 
@@ -721,4 +739,12 @@ int tc_update(tc_plan *p, cudaStream_t st, int terms, int n, int q, const float 
 {
     // L (n x n) += op(A) B with op(A)(i, c) = ShT[c + i q] (K-major, K = q), B(c, j) = V[c + j q]
     return tc_run(p, st, terms, TC_A_K, n, n, q, 1.f, ShT, q, V, q, 1.f, L, ldl, L, ldl, status);
+}
+
+int tc_gemm_nk_lo(tc_plan *p, cudaStream_t st, int terms, int a_layout, int M, int N, int K, const float *A,
+                  int64_t lda, const float *B, const float *Blo, int64_t ldb, float *C, float *Clo, int64_t ldc,
+                  const int *status, int reserve_sms)
+{
+    return tc_run(p, st, terms, a_layout, M, N, K, 1.f, A, lda, B, ldb, 0.f, nullptr, 0, C, ldc, status, reserve_sms,
+                  0, Blo, Clo);
 }

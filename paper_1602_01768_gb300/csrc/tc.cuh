@@ -34,6 +34,14 @@ int tc_gemm_nk(tc_plan *p, cudaStream_t st, int terms, int a_layout, int M, int 
 int tc_gemm_nk_t(tc_plan *p, cudaStream_t st, int terms, int a_layout, int M, int N, int K, const float *A,
                  int64_t lda, const float *B, int64_t ldb, float *C, int64_t ldc, const int *status,
                  int reserve_sms = 0);
+// As tc_gemm_nk, with two hand-offs between products.  Blo (may be null): the
+// lo part of B (element-wise x - hi(x), K x N, ld ldb, 16-byte aligned), already
+// formed by the kernel that wrote B, so this call does not split B itself.  Clo
+// (may be null; terms >= 2): C's lo part, written beside C (same layout and ld)
+// for a later product that takes C as its B.
+int tc_gemm_nk_lo(tc_plan *p, cudaStream_t st, int terms, int a_layout, int M, int N, int K, const float *A,
+                  int64_t lda, const float *B, const float *Blo, int64_t ldb, float *C, float *Clo, int64_t ldc,
+                  const int *status, int reserve_sms = 0);
 int tc_gemm_nk_axpby(tc_plan *p, cudaStream_t st, int terms, int a_layout, int M, int N, int K, float alpha,
                      const float *A, int64_t lda, const float *B, int64_t ldb, float beta, const float *Cin,
                      int64_t ldcin, float *C, int64_t ldc);
@@ -59,10 +67,12 @@ int tc_update_persistent(tc_plan *p, cudaStream_t st, int n, int q, const float 
 // Fused update and next sketch product (see tc_update_s.cu):
 //   L += S^ V (when do_update), then S_out = L S~_next (n x q, ld n)
 // with S~_next exact in TF32.  Spart is a workspace of at least
-// tc_update_s_workspace(n, q) floats.  Returns 0 when it ran on the tensor
-// cores, 1 when the shape is outside the kernel (q > 128, q or n not a
-// multiple of 4, unaligned pointers), < 0 on error.
+// tc_update_s_workspace(n, q) floats.  S_lo (may be null, 16-byte aligned):
+// S_out's lo part x - hi(x), same layout, for the 3-term product that takes S
+// as its B.  Returns 0 when it ran on the tensor cores, 1 when the shape is
+// outside the kernel (q > 128, q or n not a multiple of 4, unaligned
+// pointers), < 0 on error.
 size_t tc_update_s_workspace(int n, int q);
 int tc_update_next_s(cudaStream_t st, int n, int q, const float *ShT, const float *V, float *L, int64_t ldl,
                      const float *St_next, float *S_out, int do_update, float *Spart, size_t spart_elems,
-                     const int *status);
+                     const int *status, float *S_lo = nullptr);

@@ -450,7 +450,7 @@ k_tc_update_s(const float *__restrict__ ShT, int n, int q, const __grid_constant
 // meet each row block, in CTA order.  Block: one row block and 32 columns,
 // thread = row.
 __global__ void k_snext_reduce(int n, int q, int nq, int ncb, int ntiles, int G, int maxseg, const float *Spart,
-                               float *S, int64_t lds, const int *status)
+                               float *S, float *Slo, int64_t lds, const int *status)
 {
     if (status_bad(status)) return;
     const int rb = blockIdx.x, c0 = 32 * blockIdx.y, r = threadIdx.x, row = rb * 128 + r;
@@ -473,14 +473,17 @@ __global__ void k_snext_reduce(int n, int q, int nq, int ncb, int ntiles, int G,
     if (row < n)
 #pragma unroll
         for (int j = 0; j < 32; ++j)
-            if (c0 + j < q) S[row + (int64_t)(c0 + j) * lds] = s[j];
+            if (c0 + j < q) {
+                S[row + (int64_t)(c0 + j) * lds] = s[j];
+                if (Slo) Slo[row + (int64_t)(c0 + j) * lds] = s[j] - hi_tf32(s[j]);  // lo part for a 3-term product
+            }
 }
 
 template <int KC>
 int launch_update_s(cudaStream_t st, const float *ShT, int n, int q, const CUtensorMap &mv, const CUtensorMap &ml,
                     const CUtensorMap &mlo,
-                    const CUtensorMap &mt, int do_update, float *Spart, size_t spart_elems, float *S, int64_t lds,
-                    const int *status, int *err)
+                    const CUtensorMap &mt, int do_update, float *Spart, size_t spart_elems, float *S, float *Slo,
+                    int64_t lds, const int *status, int *err)
 {
     using CF = SCfg<KC>;
     static bool attr = false;
@@ -509,8 +512,8 @@ int launch_update_s(cudaStream_t st, const float *ShT, int n, int q, const CUten
     k_tc_update_s<KC><<<grid, 384, CF::SMEM, st>>>(ShT, n, q, mv, ml, mlo, mt, ncb, ntiles, do_update, Spart,
                                                    maxseg, status, err);
     rb_count_launch();
-    k_snext_reduce<<<dim3(nrb, CF::NQ / 32), 128, 0, st>>>(n, q, CF::NQ, ncb, ntiles, grid, maxseg, Spart, S, lds,
-                                                          status);
+    k_snext_reduce<<<dim3(nrb, CF::NQ / 32), 128, 0, st>>>(n, q, CF::NQ, ncb, ntiles, grid, maxseg, Spart, S, Slo,
+                                                          lds, status);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
@@ -528,10 +531,10 @@ size_t tc_update_s_workspace(int n, int q)
 
 int tc_update_next_s(cudaStream_t st, int n, int q, const float *ShT, const float *V, float *L, int64_t ldl,
                      const float *St_next, float *S_out, int do_update, float *Spart, size_t spart_elems,
-                     const int *status)
+                     const int *status, float *S_lo)
 {
     if (q < 1 || q > 128 || (q % 4) || (ldl % 4) || (n % 4) || ((uintptr_t)ShT % 16) || ((uintptr_t)V % 16) ||
-        ((uintptr_t)L % 16) || ((uintptr_t)St_next % 16))
+        ((uintptr_t)L % 16) || ((uintptr_t)St_next % 16) || ((uintptr_t)S_lo % 16))
         return 1;
     CUtensorMap mv, ml, mlo, mt;
     const int nq = ((q + 31) / 32) * 32;
@@ -541,10 +544,10 @@ int tc_update_next_s(cudaStream_t st, int n, int q, const float *ShT, const floa
         return -4;
     int *err = const_cast<int *>(status);
     switch (nq / 32) {
-    case 1: return launch_update_s<1>(st, ShT, n, q, mv, ml, mlo, mt, do_update, Spart, spart_elems, S_out, n, status, err);
-    case 2: return launch_update_s<2>(st, ShT, n, q, mv, ml, mlo, mt, do_update, Spart, spart_elems, S_out, n, status, err);
-    case 3: return launch_update_s<3>(st, ShT, n, q, mv, ml, mlo, mt, do_update, Spart, spart_elems, S_out, n, status, err);
+    case 1: return launch_update_s<1>(st, ShT, n, q, mv, ml, mlo, mt, do_update, Spart, spart_elems, S_out, S_lo, n, status, err);
+    case 2: return launch_update_s<2>(st, ShT, n, q, mv, ml, mlo, mt, do_update, Spart, spart_elems, S_out, S_lo, n, status, err);
+    case 3: return launch_update_s<3>(st, ShT, n, q, mv, ml, mlo, mt, do_update, Spart, spart_elems, S_out, S_lo, n, status, err);
     default:
-        return launch_update_s<4>(st, ShT, n, q, mv, ml, mlo, mt, do_update, Spart, spart_elems, S_out, n, status, err);
+        return launch_update_s<4>(st, ShT, n, q, mv, ml, mlo, mt, do_update, Spart, spart_elems, S_out, S_lo, n, status, err);
     }
 }
