@@ -290,6 +290,8 @@ static rb_status alloc_sketch_workspace(rb_ctx *h)
         if (h->method == RB_METHOD_ADARBFGS && q <= 128) {
             h->spart_cap = tc_update_s_workspace(h->n, (int)q);
             RB_TRY(rb_alloc(&h->Spart, h->spart_cap * sizeof(float)));
+            // the fused kernel's arrival counts live at the head of this workspace and must start at zero
+            RB_CUDA(cudaMemsetAsync(h->Spart, 0, h->spart_cap * sizeof(float), h->st));
             RB_TRY(rb_alloc(&h->Slo, nq));
             RB_TRY(rb_alloc(&h->Glo, nq));
         }
@@ -514,13 +516,14 @@ extern "C" rb_status aip_step(rbfgs_t h, int nsteps)
 // factors: L+ = L + (S C^-T)(D^-1 S~^T - C^-1 (A S)^T L)).
 // ---------------------------------------------------------------------------
 template <typename T>
-static void ada_draw(rb_ctx *h, T *St, uint64_t k)
+static void ada_draw(rb_ctx *h, T *St, uint64_t k, cudaStream_t s = nullptr)
 {
+    cudaStream_t st = s ? s : h->st;
     if (h->sketch == RB_SKETCH_COORD_UNIFORM) {
-        launch_floyd_draw(h->st, h->n, h->q, h->seed, h->stream_id, k, h->idx);
-        launch_coord_matrix<T>(h->st, h->n, h->q, h->idx, St, h->n);
+        launch_floyd_draw(st, h->n, h->q, h->seed, h->stream_id, k, h->idx);
+        launch_coord_matrix<T>(st, h->n, h->q, h->idx, St, h->n);
     } else {
-        launch_gauss_sketch<T>(h->st, h->n, h->q, h->seed, h->stream_id, k, St, h->n);
+        launch_gauss_sketch<T>(st, h->n, h->q, h->seed, h->stream_id, k, St, h->n);
     }
 }
 
@@ -667,6 +670,12 @@ static void ada_step_tc(rb_ctx *h)
             launch_core_ada32(side, q, h->M, nullptr, Ci, nullptr, h->d_status);
         }
         cudaEventRecord(h->ev_core, side);
+        // the next step's sketch, off the main stream while it runs W's tail, V and S^ (its buffer is
+        // free: nothing of this step reads it); only the fused update waits for it
+        if (fuse) {
+            ada_draw<float>(h, St_next, h->k + 1, side);
+            cudaEventRecord(h->ev_g, side);
+        }
     } else {
         launch_gram<float>(st, n, q, q, S, n, G, n, h->part, h->M);
         launch_gram<float>(st, n, q, q, St, n, St, n, h->part, h->N);
@@ -695,8 +704,11 @@ static void ada_step_tc(rb_ctx *h)
     }
     mark(h, "V, S^");
     if (fuse) {
-        // the next step's sketch, then L += S^ V fused with S = L S~_{k+1}
-        ada_draw<float>(h, St_next, h->k + 1);
+        // L += S^ V fused with S = L S~_{k+1} (the sketch was drawn on the side stream)
+        if (fork)
+            cudaStreamWaitEvent(st, h->ev_g, 0);
+        else
+            ada_draw<float>(h, St_next, h->k + 1);
         const int rc = tc_update_next_s(st, n, q, Sh, V, L, n, St_next, S, 1, h->Spart, h->spart_cap, stp, h->Slo);
         if (rc == 0) {
             h->s_valid = true;

@@ -67,7 +67,8 @@ int tc_update_persistent(tc_plan *p, cudaStream_t st, int n, int q, const float 
 // Fused update and next sketch product (see tc_update_s.cu):
 //   L += S^ V (when do_update), then S_out = L S~_next (n x q, ld n)
 // with S~_next exact in TF32.  Spart is a workspace of at least
-// tc_update_s_workspace(n, q) floats.  S_lo (may be null, 16-byte aligned):
+// tc_update_s_workspace(n, q) floats, zeroed once before its first use (its
+// head holds arrival counts that every complete launch leaves at zero).  S_lo (may be null, 16-byte aligned):
 // S_out's lo part x - hi(x), same layout, for the 3-term product that takes S
 // as its B.  Returns 0 when it ran on the tensor cores, 1 when the shape is
 // outside the kernel (q > 128, q or n not a multiple of 4, unaligned

@@ -26,8 +26,9 @@
 //               32-row output buffer and TMA-store it from there; per chunk: drain
 //               the S_next accumulator, keep running sums (FP32, round-to-nearest),
 //               and write one partial 128 x q block per row block that the CTA
-//               touches; k_snext_reduce adds the partials of the CTAs that share a
-//               row block in CTA order.
+//               touches; the warp that is last to finish its quarter of a row block
+//               (an atomic count per row block and quarter) adds the partials of the
+//               CTAs that share the row block in CTA order and writes S_next.
 // TMEM: update accumulators [0, 128), S^ [128, 256), L+ hi [256, 320),
 // L+ lo [320, 384), S_next accumulator [384, 512).
 // All mbarrier waits are bounded; a wait that gives up records ST_TIMEOUT and
@@ -90,7 +91,8 @@ __global__ void __launch_bounds__(384, 1)
 k_tc_update_s(const float *__restrict__ ShT, int n, int q, const __grid_constant__ CUtensorMap tmV,
               const __grid_constant__ CUtensorMap tmL, const __grid_constant__ CUtensorMap tmLo,
               const __grid_constant__ CUtensorMap tmT, int ncb, int ntiles,
-              int do_update, float *Spart, int maxseg, const int *status, int *err)
+              int do_update, float *Spart, int *rb_cnt, int maxseg, float *S, float *Slo, int64_t lds,
+              const int *status, int *err)
 {
     using CF = SCfg<KC>;
     constexpr int NQ = CF::NQ;
@@ -433,6 +435,39 @@ k_tc_update_s(const float *__restrict__ ShT, int n, int q, const __grid_constant
                     float *dst = Spart + ((size_t)blockIdx.x * maxseg + seg) * (128 * NQ) + 32 * wq + lane;
 #pragma unroll
                     for (int j = 0; j < NQ; ++j) dst[j * 128] = run[j];
+                    // CTAs whose tile runs meet the row block: b0 .. b1
+                    auto cta_of = [&](int tile) {
+                        int cb = (int)((long long)tile * gridDim.x / ntiles);
+                        while (cb + 1 < (int)gridDim.x && (long long)ntiles * (cb + 1) / gridDim.x <= tile) ++cb;
+                        while (cb > 0 && (long long)ntiles * cb / gridDim.x > tile) --cb;
+                        return cb;
+                    };
+                    const int b0 = cta_of(rb * ncb), b1 = cta_of(min(rb * ncb + ncb, ntiles) - 1);
+                    __threadfence();
+                    __syncwarp();
+                    int old = 0;
+                    if (lane == 0) old = atomicAdd(&rb_cnt[4 * rb + wq], 1);
+                    old = __shfl_sync(0xffffffffu, old, 0);
+                    if (old == b1 - b0) {  // every other partial of this quarter is written: S_next rows
+                        if (lane == 0) rb_cnt[4 * rb + wq] = 0;  // ready for the next launch
+                        __threadfence();
+#pragma unroll
+                        for (int j = 0; j < NQ; ++j) run[j] = 0.f;
+                        for (int bb = b0; bb <= b1; ++bb) {
+                            const int sg = rb - (int)((long long)ntiles * bb / gridDim.x) / ncb;
+                            const float *pp = Spart + ((size_t)bb * maxseg + sg) * (128 * NQ) + 32 * wq + lane;
+#pragma unroll
+                            for (int j = 0; j < NQ; ++j) run[j] += __ldcg(pp + j * 128);
+                        }
+                        const int row = rb * 128 + 32 * wq + lane;
+                        if (row < n)
+#pragma unroll
+                            for (int j = 0; j < NQ; ++j)
+                                if (j < q) {
+                                    S[row + (int64_t)j * lds] = run[j];
+                                    if (Slo) Slo[row + (int64_t)j * lds] = run[j] - hi_tf32(run[j]);  // for a 3-term product
+                                }
+                    }
                 }
             }
         }
@@ -444,39 +479,6 @@ k_tc_update_s(const float *__restrict__ ShT, int n, int q, const __grid_constant
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512u) : "memory");
     }
-}
-
-// S_next (n x q, ld lds) = sum of the partial blocks of the CTAs whose tile runs
-// meet each row block, in CTA order.  Block: one row block and 32 columns,
-// thread = row.
-__global__ void k_snext_reduce(int n, int q, int nq, int ncb, int ntiles, int G, int maxseg, const float *Spart,
-                               float *S, float *Slo, int64_t lds, const int *status)
-{
-    if (status_bad(status)) return;
-    const int rb = blockIdx.x, c0 = 32 * blockIdx.y, r = threadIdx.x, row = rb * 128 + r;
-    const long long t0 = (long long)rb * ncb, t1 = t0 + ncb;
-    auto tbeg = [&](int b) { return (long long)ntiles * b / G; };
-    int b = (int)(t0 * G / ntiles);
-    while (b + 1 < G && tbeg(b + 1) <= t0) ++b;
-    while (b > 0 && tbeg(b) > t0) --b;
-    float s[32];
-#pragma unroll
-    for (int j = 0; j < 32; ++j) s[j] = 0.f;
-    for (int bb = b; bb < G && tbeg(bb) < t1; ++bb) {
-        if (tbeg(bb + 1) == tbeg(bb)) continue;
-        const int seg = rb - (int)(tbeg(bb) / ncb);
-        const float *pp = Spart + ((size_t)bb * maxseg + seg) * (128 * nq) + (size_t)c0 * 128 + r;
-#pragma unroll
-        for (int j = 0; j < 32; ++j)
-            if (c0 + j < q) s[j] += pp[(size_t)j * 128];
-    }
-    if (row < n)
-#pragma unroll
-        for (int j = 0; j < 32; ++j)
-            if (c0 + j < q) {
-                S[row + (int64_t)(c0 + j) * lds] = s[j];
-                if (Slo) Slo[row + (int64_t)(c0 + j) * lds] = s[j] - hi_tf32(s[j]);  // lo part for a 3-term product
-            }
 }
 
 template <int KC>
@@ -507,13 +509,13 @@ int launch_update_s(cudaStream_t st, const float *ShT, int n, int q, const CUten
         const long long t0 = (long long)ntiles * b / grid, t1 = (long long)ntiles * (b + 1) / grid;
         if (t1 > t0) maxseg = std::max(maxseg, (int)((t1 - 1) / ncb - t0 / ncb + 1));
     }
-    if ((size_t)grid * maxseg * 128 * CF::NQ > spart_elems) return -2;
+    // workspace: arrival counts (4 per row block, zero between launches) then the partial blocks
+    const size_t cnt_floats = ((size_t)4 * nrb + 31) / 32 * 32;
+    if (cnt_floats + (size_t)grid * maxseg * 128 * CF::NQ > spart_elems) return -2;
     rb_count_launch();
-    k_tc_update_s<KC><<<grid, 384, CF::SMEM, st>>>(ShT, n, q, mv, ml, mlo, mt, ncb, ntiles, do_update, Spart,
-                                                   maxseg, status, err);
-    rb_count_launch();
-    k_snext_reduce<<<dim3(nrb, CF::NQ / 32), 128, 0, st>>>(n, q, CF::NQ, ncb, ntiles, grid, maxseg, Spart, S, Slo,
-                                                          lds, status);
+    k_tc_update_s<KC><<<grid, 384, CF::SMEM, st>>>(ShT, n, q, mv, ml, mlo, mt, ncb, ntiles, do_update,
+                                                   Spart + cnt_floats, (int *)Spart, maxseg, S, Slo, lds, status,
+                                                   err);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
@@ -526,7 +528,8 @@ size_t tc_update_s_workspace(int n, int q)
     const int grid = std::min(ntiles, tc_num_sms());
     const int per = (ntiles + grid - 1) / grid;
     const int maxseg = per / ncb + 2;
-    return (size_t)grid * maxseg * 128 * (size_t)(((q + 31) / 32) * 32);
+    const size_t cnt_floats = ((size_t)4 * nrb + 31) / 32 * 32;  // arrival counts (as int)
+    return cnt_floats + (size_t)grid * maxseg * 128 * (size_t)(((q + 31) / 32) * 32);
 }
 
 int tc_update_next_s(cudaStream_t st, int n, int q, const float *ShT, const float *V, float *L, int64_t ldl,
