@@ -37,7 +37,7 @@ SERVE_MAX_ITER = 2000  # per request; the 1e-6 class stalls at the FP32 floor an
 # (profiles/tc_kernels_n8192_full.md); scaled by (n / 8192)^2 for other n at q = 128.
 UPDATE_TRAFFIC_N8192_Q128 = 277638912 + 208375552
 # the same for one k_tc_update_s launch (fused update + next sketch product)
-FUSED_TRAFFIC_N8192_Q128 = 289487360 + 222310144
+FUSED_TRAFFIC_N8192_Q128 = 292324352 + 231330560
 
 
 def parse():
@@ -489,9 +489,9 @@ def main():
             prof.setdefault(name, []).append(ms)
     phases = {k: statistics.median(v) for k, v in prof.items()}
     fused = "update L + next S" in phases
-    if fused:  # L += S^ V fused with S_next = L S~_next: read + write L; read V, S^, S~_next; write S_next
+    if fused:  # L += S^ V fused with S_next = L S~_next: read + write L; read V, S^, S~_next; write S_next, its lo
         upd_ms = phases["update L + next S"]
-        upd_bytes = 2 * 4 * n * n + 4 * 4 * n * q
+        upd_bytes = 2 * 4 * n * n + 5 * 4 * n * q
         kern = "fused L += S^ V and S_next = L S~_next (k_tc_update_s: 1xTF32 update, 2xTF32 product)"
         traffic = (FUSED_TRAFFIC_N8192_Q128 * (n / 8192) ** 2) if (q == 128 and FUSED_TRAFFIC_N8192_Q128) else None
     else:
