@@ -220,9 +220,11 @@ def test_adarbfgs_fp32_parity(prec, n, q):
         B.rbfgs_destroy(h)
 
 
-def test_adarbfgs_tf32x3_one_step_from_general_L():
-    # exercises the M-contiguous operand path (S = L S~ with L != I) and split-K
-    n, q = 768, 64
+@pytest.mark.parametrize("n", [768, 2100])
+def test_adarbfgs_tf32x3_one_step_from_general_L(n):
+    # exercises the M-contiguous operand path (S = L S~ with L != I) and split-K; at n = 2100 the
+    # products run stream-K (K >= 64 k-blocks) with ragged M and K, and W takes G's lo part from G's epilogue
+    q = 64
     A = wl.c2_matrix(n=n).astype(np.float32).astype(np.float64)
     rng = np.random.default_rng(4)
     L0 = np.eye(n) + 0.05 * rng.standard_normal((n, n))
@@ -258,6 +260,29 @@ def test_adarbfgs_mixed_one_step_from_general_L(n, q):
         corr = rel(Lg - L0, L1 - L0)
         assert corr <= 2e-3
         assert rel(Lg, L1) <= 2e-3 * np.linalg.norm(L1 - L0) / np.linalg.norm(L1) + 1e-5
+    finally:
+        B.rbfgs_destroy(h)
+
+
+@pytest.mark.parametrize("n,q", [(2100, 64), (2052, 128)])
+def test_adarbfgs_mixed_two_steps_streamk_ragged(n, q):
+    # sizes where the GEMMs run stream-K (pieces of a tile added by the CTA that finishes it) and
+    # several CTAs share each row block of the fused update (their S_next pieces added likewise),
+    # with ragged M and K; the second step takes S and S's lo part from the first step's fused kernel
+    A = wl.c2_matrix(n=n).astype(np.float32).astype(np.float64)
+    rng = np.random.default_rng(6)
+    L0 = (np.eye(n) + 0.05 * rng.standard_normal((n, n))).astype(np.float32).astype(np.float64)
+    h = _handle(A, B.RB_METHOD_ADARBFGS, B.RB_SKETCH_GAUSS, q, B.RB_MIXED, seed=15)
+    try:
+        Ld = to_dev(L0, torch_dtype(B.RB_MIXED))
+        B.rbfgs_import(h, B.RB_WHAT_L, Ld.data_ptr(), n)
+        B.rbfgs_set_step(h, 7)
+        B.adarbfgs_step(h, 2)
+        _, L2 = orc.adarbfgs_run(A, L0, q, orc.SKETCH_GAUSS, 15, 0, 7, 2)
+        Lg = export(h, n, B.RB_MIXED, B.RB_WHAT_L)
+        # single-pass TF32 corrections: error ~ 2^-11 of each step's correction
+        assert rel(Lg - L0, L2 - L0) <= 3e-3
+        assert rel(Lg, L2) <= 3e-3 * np.linalg.norm(L2 - L0) / np.linalg.norm(L2) + 1e-5
     finally:
         B.rbfgs_destroy(h)
 
