@@ -670,9 +670,11 @@ static void ada_step_tc(rb_ctx *h)
             launch_core_ada32(side, q, h->M, nullptr, Ci, nullptr, h->d_status);
         }
         cudaEventRecord(h->ev_core, side);
-        // the next step's sketch, off the main stream while it runs W's tail, V and S^ (its buffer is
-        // free: nothing of this step reads it); only the fused update waits for it
+        // off the main stream while it runs W's tail and V: S^ = S C^-T (it needs only S and the C
+        // core) and the next step's sketch (its buffer is free: nothing of this step reads it); only
+        // the fused update waits for them
         if (fuse) {
+            tc_gemm_nk_t(h->tc2, side, upd, TC_A_MN, n, q, q, S, n, h->Bs, q, Sh, q, stp);
             ada_draw<float>(h, St_next, h->k + 1, side);
             cudaEventRecord(h->ev_g, side);
         }
@@ -693,8 +695,9 @@ static void ada_step_tc(rb_ctx *h)
     if (tcv) {
         // V^T = [S~ | W^T] [D^-T; -C^-T] (or both halves swapped), written transposed: V is q x n (ld q)
         tc_gemm_nk_t(h->tc, st, acc, TC_A_MN, n, q, 2 * q, SW, n, h->Bv, 2 * q, V, q, stp);
-        // S^ = S C^-T, written transposed (row-major n x q) for the K-major update operand
-        tc_gemm_nk_t(h->tc, st, upd, TC_A_MN, n, q, q, S, n, h->Bs, q, Sh, q, stp);
+        // S^ = S C^-T, written transposed (row-major n x q) for the K-major update operand (side stream
+        // when the update is fused)
+        if (!fuse) tc_gemm_nk_t(h->tc, st, upd, TC_A_MN, n, q, q, S, n, h->Bs, q, Sh, q, stp);
     } else {
         // V = D^-1 S~^T - C^-1 W, stored q x n (ld q); W^T is n x q (ld n)
         gemm_simt<float>(st, false, true, q, n, q, 1.f, Di, q, St, n, 0.f, V, q, stp);
