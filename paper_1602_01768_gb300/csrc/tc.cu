@@ -21,7 +21,12 @@
 //               M-contiguous op(A); a K-contiguous 2-term hi is read from
 //               shared memory directly;
 //   warps 8-11  drain the chunk accumulators (tcgen05.ld), keep the running
-//               sums and write the output or stream-K partial tiles.
+//               sums and write the output (and, on request, its lo part for a
+//               later 3-term product) or stream-K partial tiles, and add the
+//               pieces of a tile when they finish it; they take registers from
+//               the other warps (setmaxnreg) for the BN running sums.
+// A 3-term k-step issues two MMAs: hi x [B | B lo] of width 2 BN and lo x B
+// (the MMA issue rate, not the arithmetic, bounds these products).
 // Every mbarrier wait is bounded (about two seconds of SM clock); a wait
 // that gives up records ST_TIMEOUT in the caller's status word and the CTA
 // winds down instead of hanging.
