@@ -49,8 +49,8 @@ constexpr int TSLOTS = 2;                    // S~_next tiles in flight
 constexpr int SCHUNK = 8;                    // tiles per S_next accumulation chunk (512 of K)
 constexpr uint32_t COL_SH = 128, COL_LHI = 256, COL_LLO = 320, COL_SACC = 384;
 // Registers per thread: 168 at launch (384 threads); warps 0-3 drop to REG_ISSUE and warps 8-11
-// (running sums of S_next, NQ per thread) rise to REG_DRAIN: 128 x (112 + 168 + 208) <= 384 x 168.
-constexpr int REG_ISSUE = 112, REG_DRAIN = 208;
+// (running sums of S_next, NQ per thread) rise to REG_DRAIN: 128 x (128 + 168 + 192) <= 384 x 168.
+constexpr int REG_ISSUE = 128, REG_DRAIN = 192;
 static_assert(128 * (REG_ISSUE + 168 + REG_DRAIN) <= 384 * 168, "register split");
 
 template <int KC>  // q padded to NQ = 32 KC
@@ -160,9 +160,18 @@ k_tc_update_s(const float *__restrict__ ShT, int n, int q, const __grid_constant
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    // S_next chunking: tile i sits at position p = i - (first tile of its row block in this CTA's run)
-    auto seg_pos = [&](int t) { return t - max(tb, (t / ncb) * ncb); };
-    auto last_of_rb = [&](int t) { return t + 1 == te || (t + 1) / ncb != t / ncb; };
+    // Tile i of this CTA's run is (row block rb, column block cb); every role advances the pair
+    // with its loop index instead of dividing by ncb per tile.
+    const int cb_first = tb - rb_first * ncb;
+    auto next_tile = [&](int &rb, int &cb) {
+        if (++cb == ncb) {
+            cb = 0;
+            ++rb;
+        }
+    };
+    // S_next chunking: a tile's position in this CTA's run of its row block, and whether it ends it
+    auto seg_pos = [&](int i, int rb, int cb) { return rb == rb_first ? i : cb; };
+    auto last_of_rb = [&](int i, int cb) { return i + 1 == nt || cb + 1 == ncb; };
 
     if (warp < 4) {
         // single-thread roles: give registers to the S_next drain warps
@@ -170,8 +179,9 @@ k_tc_update_s(const float *__restrict__ ShT, int n, int q, const __grid_constant
         if (warp == 0) {
             // ---------------- TMA: L tiles ----------------
             if (lane == 0) {
-                for (int i = 0; i < nt; ++i) {
-                    const int t = tb + i, rb = t / ncb, cb = t - rb * ncb, s = i % NSTAGES;
+                int rb = rb_first, cb = cb_first;
+                for (int i = 0; i < nt; ++i, next_tile(rb, cb)) {
+                    const int s = i % NSTAGES;
                     if (i >= NSTAGES && !mbar_wait(smem_u32(&lempty_s[s]), ((i / NSTAGES) - 1) & 1, err, abort_flag))
                         break;
                     const uint32_t fb = smem_u32(&lfull_s[s]);
@@ -182,8 +192,9 @@ k_tc_update_s(const float *__restrict__ ShT, int n, int q, const __grid_constant
         } else if (warp == 2) {
             // ---------------- TMA: V tiles and S~_next tiles (rows cb * 64 .. + 63) ----------------
             if (lane == 0) {
-                for (int i = 0; i < nt; ++i) {
-                    const int t = tb + i, cb = t % ncb, ts = i % TSLOTS, s = i % NSTAGES;
+                int rb = rb_first, cb = cb_first;
+                for (int i = 0; i < nt; ++i, next_tile(rb, cb)) {
+                    const int ts = i % TSLOTS, s = i % NSTAGES;
                     if (do_update) {
                         if (i >= NSTAGES && !mbar_wait(smem_u32(&vempty[s]), ((i / NSTAGES) - 1) & 1, err, abort_flag))
                             break;
@@ -207,10 +218,10 @@ k_tc_update_s(const float *__restrict__ ShT, int n, int q, const __grid_constant
                 int chunk = -1;  // S_next chunk being accumulated
                 bool ok = true;
                 // S_next product of tile j (L+ of tile j in TMEM, S~_next tile j in smem)
-                auto s_mma = [&](int j) {
-                    const int t = tb + j, p = seg_pos(t);
+                auto s_mma = [&](int j, int rb, int cb) {
+                    const int p = seg_pos(j, rb, cb);
                     const bool cstart = (p % SCHUNK) == 0;
-                    const bool cend = ((p + 1) % SCHUNK) == 0 || last_of_rb(t);
+                    const bool cend = ((p + 1) % SCHUNK) == 0 || last_of_rb(j, cb);
                     if (cstart) {
                         ++chunk;
                         if (chunk >= 1 && !mbar_wait(smem_u32(sfree), (chunk - 1) & 1, err, abort_flag)) {
@@ -236,15 +247,17 @@ k_tc_update_s(const float *__restrict__ ShT, int n, int q, const __grid_constant
                     mma_commit(smem_u32(&tempty[ts]));
                     if (cend) mma_commit(smem_u32(sfull));
                 };
-                for (int j = 0; j < nt && ok; ++j) s_mma(j);
+                int rb = rb_first, cb = cb_first;
+                for (int j = 0; j < nt && ok; ++j, next_tile(rb, cb)) s_mma(j, rb, cb);
             }
         } else if (warp == 1) {
             // ---------------- MMA issuer for the L-tile update ----------------
             if (lane == 0 && do_update) {
                 const uint32_t idesc_u = idesc_tf32(UBN, 0);
                 int cur_rb = -1;
-                for (int i = 0; i < nt; ++i) {
-                    const int t = tb + i, rb = t / ncb, s = i % NSTAGES, b = i & 1;
+                int rb = rb_first, cb = cb_first;
+                for (int i = 0; i < nt; ++i, next_tile(rb, cb)) {
+                    const int s = i % NSTAGES, b = i & 1;
                     {
                         if (rb != cur_rb) {
                             const int k = rb - rb_first;  // S^ refills of this CTA
@@ -265,7 +278,7 @@ k_tc_update_s(const float *__restrict__ ShT, int n, int q, const __grid_constant
                             }
                         mma_commit(smem_u32(&afull[b]));
                         mma_commit(smem_u32(&vempty[s]));
-                        if (last_of_rb(t)) mma_commit(smem_u32(shfree));
+                        if (last_of_rb(i, cb)) mma_commit(smem_u32(shfree));
                     }
                 }
             }
@@ -317,8 +330,9 @@ k_tc_update_s(const float *__restrict__ ShT, int n, int q, const __grid_constant
             mbar_arrive(smem_u32(shfull));
         };
         if (do_update && nt > 0) load_sh(rb_first);
-        for (int i = 0; i < nt && ok; ++i) {
-            const int t = tb + i, rb = t / ncb, s = i % NSTAGES, b = i & 1;
+        int rb = rb_first, cb = cb_first;
+        for (int i = 0; i < nt && ok; ++i, next_tile(rb, cb)) {
+            const int s = i % NSTAGES, b = i & 1;
             // the L row first (shared memory), then the accumulator (TMEM, one wait for all loads)
             if (!wwait(&lfull_s[s], (i / NSTAGES) & 1)) break;
             const float *Ls = (const float *)(stg + s * CF::STAGE_BYTES + CF::V_BYTES);  // [64 cols][128 rows]
@@ -369,7 +383,7 @@ k_tc_update_s(const float *__restrict__ ShT, int n, int q, const __grid_constant
             tc_fence_before();
             mbar_arrive(smem_u32(lfull));
             // the update MMAs of this row block are done once its last tile drained: refill S^
-            if (do_update && last_of_rb(t) && i + 1 < nt) load_sh(rb + 1);
+            if (do_update && last_of_rb(i, cb) && i + 1 < nt) load_sh(rb + 1);
         }
     } else {
         asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(REG_DRAIN));
@@ -384,8 +398,9 @@ k_tc_update_s(const float *__restrict__ ShT, int n, int q, const __grid_constant
 #pragma unroll
         for (int j = 0; j < NQ; ++j) run[j] = 0.f;
         int c = 0;
-        for (int i = 0; i < nt; ++i) {
-            const int t = tb + i, rb = t / ncb, cb = t - rb * ncb, p = seg_pos(t);
+        int rb = rb_first, cb = cb_first;
+        for (int i = 0; i < nt; ++i, next_tile(rb, cb)) {
+            const int p = seg_pos(i, rb, cb);
             // L+ of tile i (the hi slot holds the FP32 value) to the output buffer, then one TMA store
             if (!wwait(lfull, i & 1)) break;
             tc_fence_after();
@@ -415,7 +430,7 @@ k_tc_update_s(const float *__restrict__ ShT, int n, int q, const __grid_constant
                 }
             }
             // S_next chunk ends with tile i: running sums; a row block's last chunk writes its partial block
-            if (((p + 1) % SCHUNK) == 0 || last_of_rb(t)) {
+            if (((p + 1) % SCHUNK) == 0 || last_of_rb(i, cb)) {
                 if (!wwait(sfull, c & 1)) break;
                 tc_fence_after();
                 const uint32_t keep = (p < SCHUNK) ? 0u : 0xFFFFFFFFu;  // a row block starts a fresh sum
@@ -430,7 +445,7 @@ k_tc_update_s(const float *__restrict__ ShT, int n, int q, const __grid_constant
                 tc_fence_before();
                 mbar_arrive(smem_u32(sfree));
                 ++c;
-                if (last_of_rb(t)) {  // partial block (rows x NQ, column-major, ld 128)
+                if (last_of_rb(i, cb)) {  // partial block (rows x NQ, column-major, ld 128)
                     const int seg = rb - rb_first;
                     float *dst = Spart + ((size_t)blockIdx.x * maxseg + seg) * (128 * NQ) + 32 * wq + lane;
 #pragma unroll
