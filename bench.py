@@ -37,7 +37,7 @@ SERVE_MAX_ITER = 2000  # per request; the 1e-6 class stalls at the FP32 floor an
 # (profiles/tc_kernels_n8192_full.md); scaled by (n / 8192)^2 for other n at q = 128.
 UPDATE_TRAFFIC_N8192_Q128 = 277638912 + 208375552
 # the same for one k_tc_update_s launch (fused update + next sketch product)
-FUSED_TRAFFIC_N8192_Q128 = None
+FUSED_TRAFFIC_N8192_Q128 = 293947136 + 231262464
 
 
 def parse():
