@@ -21,6 +21,7 @@ import json
 import math
 import os
 import statistics
+import tempfile
 import subprocess
 import sys
 import time
@@ -98,7 +99,10 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        # the raw samples go to RB_CLOCKS_DIR (default: the system temp folder); the JSON line
+        # carries their summary
+        out_dir = os.environ.get("RB_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, f"clocks_rank{index}.csv")
 
     def start(self):
         try:
@@ -247,8 +251,8 @@ def run_reference(args):
 
 
 def estimate_steps(n, q):
-    # AdaRBFGS steps to 1e-4 on this spectrum measured on GB300; used
-    # only to scale the oracle's per-step time to a solve when no GPU count is at hand.
+    # AdaRBFGS steps to 1e-4 on this spectrum, about 11 n / q on GB300 runs; used only to
+    # scale the oracle's per-step time to a solve when no GPU count is at hand.
     return int(os.environ.get("RB_STEPS_PER_SOLVE", str(max(1, int(11 * n / q)))))
 
 

@@ -1,6 +1,6 @@
 """Replica coordination of bench.py on CPU: two gloo ranks (no GPU, no collective on the data path).
 
-The solve does not shard: N GPUs run N independent solves with their own sketch
+The solve does not shard (one iterate, updated in place every step): N GPUs run N independent solves with their own sketch
 stream (stream_id = rank), a barrier and a MAX over the ranks' timed regions, and the job value is all
 ranks' solves over the slowest rank's time.  These tests run that host logic with world_size 2.
 """
