@@ -18,17 +18,19 @@
 //               in TMEM (A = L+ hi / lo, B = S~_next), chunked every 8 tiles
 //               (a thread's commits track its own MMAs, so the two streams of
 //               MMAs are ordered independently);
-//   warps 4-7   per tile: read the L rows, release the stage as soon as the update
-//               MMAs are done with it, add the accumulator and write L+ into TMEM,
-//               as hi (the FP32 value, which the MMA truncates) and lo = L+ - hi,
-//               for the S_next MMA; refill S^ in TMEM when the row block changes;
+//   warps 4-7   per tile: read the L rows (which frees the L half of the slot),
+//               add the update accumulator and write L+ into TMEM, as hi (the FP32
+//               value, which the MMA truncates) and lo = L+ - hi, for the S_next
+//               MMA; refill S^ in TMEM when the row block changes;
 //   warps 8-11  per tile: read L+ back from TMEM, stage it in the warp's own
 //               32-row output buffer and TMA-store it from there; per chunk: drain
 //               the S_next accumulator, keep running sums (FP32, round-to-nearest),
 //               and write one partial 128 x q block per row block that the CTA
 //               touches; the warp that is last to finish its quarter of a row block
 //               (an atomic count per row block and quarter) adds the partials of the
-//               CTAs that share the row block in CTA order and writes S_next.
+//               CTAs that share the row block in CTA order and writes S_next (and its
+//               lo part when asked); these warps take registers from warps 0-3
+//               (setmaxnreg) for the q running sums.
 // TMEM: update accumulators [0, 128), S^ [128, 256), L+ hi [256, 320),
 // L+ lo [320, 384), S_next accumulator [384, 512).
 // All mbarrier waits are bounded; a wait that gives up records ST_TIMEOUT and
