@@ -240,11 +240,13 @@ rb_status rbfgs_sigma(rbfgs_t h, double *sigma);
  *   n, A_dev, lda, a_is_fp64: the SPD matrix (device pointer, column-major).
  *   power_iters: iterations from v0 = 1/sqrt(n) (0 = 100), as for
  *   newton_schulz_init.  *sigma_out receives ||A v|| after the last one.
- * n > 65536 is rejected with RB_EINVAL.  The first call on a device looks
- * up the scratch's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  All calls share
- * the one scratch array: calls that overlap on the GPU (other streams, other
- * host threads) race.  Synchronises the stream.
+ * n > 65536 is rejected with RB_EINVAL.  Every call looks up the scratch's
+ * device address (cudaGetSymbolAddress) in the context current on the calling
+ * thread, so a device reset or a switch of context is safe; the first call in
+ * a context also loads the library's device code there, so make it before any
+ * stream capture.  All calls share the one scratch array: calls that overlap
+ * on the GPU (other streams, other host threads) race.  Synchronises the
+ * stream.
  */
 rb_status rbfgs_sigma_noalloc(int n, const void *A_dev, int64_t lda, int a_is_fp64, int power_iters,
                               double *sigma_out, void *stream);

@@ -9,8 +9,6 @@
 // rbfgs_sigma_noalloc runs the same power iteration with its scratch in the
 // file-scope array below instead.  That array is part of the library image:
 // every GPU that loads this library holds it until the process exits.
-#include <mutex>
-
 #include "kernels.cuh"
 
 // Largest n accepted by rbfgs_sigma_noalloc.
@@ -22,27 +20,19 @@ static __device__ __align__(256) double g_noalloc_scratch[2 * RB_NOALLOC_MAX_N +
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-double *g_scratch_ptr[kMaxDevices] = {};
-std::mutex g_scratch_mu;
-
-// Device address of g_noalloc_scratch on the current device.  Resolved once
-// per device (cudaGetSymbolAddress, which allocates nothing) and cached.
-rb_status scratch_for_current_device(double **out)
+// Device address of g_noalloc_scratch in the CUDA context current on this
+// thread.  A __device__ array belongs to a context, not to a device ordinal:
+// after cudaDeviceReset, or under a non-primary context, an address cached per
+// device could point into memory that is no longer this array.  So it is
+// looked up on every call; cudaGetSymbolAddress allocates nothing.
+rb_status scratch_for_current_context(double **out)
 {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return RB_ECUDA;
-    if (dev < 0 || dev >= kMaxDevices) return RB_EUNSUPPORTED;
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
-    if (!g_scratch_ptr[dev]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) {
-            cudaGetLastError();
-            return RB_ECUDA;
-        }
-        g_scratch_ptr[dev] = (double *)p;
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || p == nullptr) {
+        cudaGetLastError();
+        return RB_ECUDA;
     }
-    *out = g_scratch_ptr[dev];
+    *out = (double *)p;
     return RB_OK;
 }
 
@@ -54,7 +44,7 @@ extern "C" rb_status rbfgs_sigma_noalloc(int n, const void *A_dev, int64_t lda, 
     if (!A_dev || !sigma_out || n < 1 || lda < n) return RB_EINVAL;
     if (n > RB_NOALLOC_MAX_N) return RB_EINVAL;  // beyond the static scratch
     double *scratch = nullptr;
-    RB_TRY(scratch_for_current_device(&scratch));
+    RB_TRY(scratch_for_current_context(&scratch));
     double *v = scratch, *w = scratch + RB_NOALLOC_MAX_N, *sig = scratch + 2 * RB_NOALLOC_MAX_N;
     cudaStream_t st = (cudaStream_t)stream;
     const int iters = power_iters > 0 ? power_iters : 100;
