@@ -810,25 +810,30 @@ double orc_residual_sampled(int n, const double *A, const double *X, const doubl
 {
     int *J = (int *)malloc(sizeof(int) * (size_t)m);
     orc_floyd_sample(col_seed, 0, 0, ORC_TAG_COLS, n, m, J);
+    /* the m columns A e_j side by side, so each product below is one call whose
+     * OpenMP loop runs over the m columns (every column's sums in the same order
+     * as a one-column product) */
+    double *AE = (double *)malloc(sizeof(double) * (size_t)n * m);
+    double *Z = (double *)malloc(sizeof(double) * (size_t)n * m);
+    for (int t = 0; t < m; ++t) memcpy(AE + IDX(0, t, n), A + IDX(0, J[t], n), sizeof(double) * (size_t)n);
+    if (L) {
+        double *Y = (double *)malloc(sizeof(double) * (size_t)n * m);
+        mm_tn(n, m, n, L, AE, Y); /* L^T A e_J     */
+        mm_nn(n, m, n, L, Y, Z);  /* L L^T A e_J   */
+        free(Y);
+    } else {
+        mm_nn(n, m, n, X, AE, Z); /* X A e_J       */
+    }
     double acc = 0.0;
-    double *z = (double *)malloc(sizeof(double) * (size_t)n);
-    double *y = (double *)malloc(sizeof(double) * (size_t)n);
     for (int t = 0; t < m; ++t) {
-        int j = J[t];
-        const double *a = A + IDX(0, j, n); /* A e_j */
-        if (L) {
-            mm_tn(n, 1, n, L, a, y);        /* L^T A e_j     */
-            mm_nn(n, 1, n, L, y, z);        /* L L^T A e_j   */
-        } else {
-            mm_nn(n, 1, n, X, a, z);        /* X A e_j       */
-        }
+        const int j = J[t];
         for (int i = 0; i < n; ++i) {
-            double e = ((i == j) ? 1.0 : 0.0) - z[i];
+            double e = ((i == j) ? 1.0 : 0.0) - Z[IDX(i, t, n)];
             acc += e * e;
         }
     }
     free(J);
-    free(z);
-    free(y);
+    free(AE);
+    free(Z);
     return sqrt(acc / m);
 }

@@ -435,6 +435,56 @@ def test_adarbfgs_gauss_converges_monotonically():
     assert done == 120 and np.allclose(L2, L, rtol=0, atol=1e-13)
 
 
+def test_adarbfgs_adaptive_partition_step_meets_theorem_9_1():
+    # Thm 9.1: with S = L_k I_{:C_i} for a partition {C_i} of [n], drawn with p_i proportional
+    # to Tr(S_i^T A S_i), one AdaRBFGS step satisfies
+    #   E[||X+ - A^-1||^2_F(A) | X_k] <= (1 - lambda_min(A X_k) / Tr(A X_k)) ||X_k - A^-1||^2_F(A).
+    # The conditional expectation is taken exactly, by enumerating every block of the partition.
+    n, q = 24, 4
+    A, U, lam = _spd(n, 40.0, 15)
+    Ah = _sqrt_spd(U, lam)
+    for seed in range(4):
+        rng = np.random.default_rng(100 + seed)
+        L = np.eye(n) + 0.3 * rng.standard_normal((n, n)) / np.sqrt(n)
+        X = L @ L.T
+        blocks = [np.arange(b, min(n, b + q)) for b in range(0, n, q)]
+        w = np.array([np.trace(L[:, C].T @ A @ L[:, C]) for C in blocks])
+        p = w / w.sum()
+        e_next = 0.0
+        for C, pi in zip(blocks, p):
+            St = np.zeros((n, len(C)))
+            St[C, np.arange(len(C))] = 1.0
+            rc, Lp = orc.adarbfgs_step(A, L, St)
+            assert rc == 0
+            e_next += pi * _fa_err(Ah, Lp @ Lp.T) ** 2
+        ax = np.linalg.eigvals(A @ X).real
+        bound = (1.0 - ax.min() / np.trace(A @ X)) * _fa_err(Ah, X) ** 2
+        assert e_next <= bound * (1 + 1e-10), (seed, e_next, bound)
+
+
+def test_rbfgs_rate_lower_bound_rholower():
+    # Eq. (rholower): rho >= 1 - q/n.  Each Z^ = A^{1/2} S (S^T A S)^-1 S^T A^{1/2} is a rank-q
+    # projection (Lemma of Sec. 6), so Tr E[Z^] = q and lambda_min(E[Z^]) <= q/n.  The bound is
+    # attained from X_0 = 0: there R_0 = -I and R_1 = -(I - Z^) for every sketch, so one RBFGS
+    # step contracts ||X - A^-1||^2_F(A) by exactly 1 - q/n.
+    n, q = 30, 5
+    A, U, lam = _spd(n, 60.0, 16)
+    Ah = _sqrt_spd(U, lam)
+    Zsum = np.zeros((n, n))
+    for k in range(200):
+        S = orc.gauss_sketch(21, 0, k, n, q)
+        rc, X1 = orc.rbfgs_step(A, np.zeros((n, n)), S, 1)
+        assert rc == 0
+        Zh = Ah @ X1 @ Ah  # X1 = S (S^T A S)^-1 S^T from X_0 = 0
+        assert np.linalg.norm(Zh @ Zh - Zh) < 1e-10 * n
+        assert abs(np.trace(Zh) - q) < 1e-10 * n
+        ratio = _fa_err(Ah, X1) ** 2 / _fa_err(Ah, np.zeros((n, n))) ** 2
+        assert abs(ratio - (1.0 - q / n)) < 1e-10
+        Zsum += Zh
+    rho_hat = 1.0 - np.linalg.eigvalsh(Zsum / 200).min()
+    assert rho_hat >= 1.0 - q / n - 1e-12
+
+
 def test_adarbfgs_reports_rank_deficient_sketch():
     n = 10
     A, _, _ = _spd(n, 10.0, 13)
