@@ -35,10 +35,16 @@ CHECK_EVERY, CHECK_COLS, CONFIRM_COLS = 32, 256, 1024
 MAX_ITER = 20000
 SERVE_MAX_ITER = 2000  # per request; the 1e-6 class stalls at the FP32 floor and runs to this cap
 # DRAM bytes (read + write) of one k_tc_update launch at n = 8192, q = 128, from one ncu capture
-# (profiles/tc_kernels_n8192_full.md); scaled by (n / 8192)^2 for other n at q = 128.
+# of that launch; scaled by (n / 8192)^2 for other n at q = 128 (the bytes grow as n^2 at fixed q).
 UPDATE_TRAFFIC_N8192_Q128 = 277638912 + 208375552
 # the same for one k_tc_update_s launch (fused update + next sketch product)
 FUSED_TRAFFIC_N8192_Q128 = 293947136 + 231262464
+# AdaRBFGS steps per solve of the n = 16384, q = 128 workload to 1e-4 as the GPU arm measures it
+# (mean over its timed solves); the reference arm, which cannot run a whole solve in the time
+# allowed, times a bounded sample of oracle steps and scales it by this count.
+STEPS_PER_SOLVE_MEASURED = 2016
+# rb_opts.core_fp64: 0 = the precision form's own choice, 1 = FP64 q x q core, -1 = FP32 core
+CORE_OPT = {"default": 0, "fp64": 1, "fp32": -1}
 
 
 def parse():
@@ -47,7 +53,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--prec", default="mixed", choices=["mixed", "tf32x3", "fp32", "tf32"])
+    ap.add_argument("--prec", default="mixed")
+    ap.add_argument("--core", choices=["default", "fp64", "fp32"], default="default",
+                    help="precision of the q x q Cholesky core (default: the form's own)")
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--q", type=int, default=Q_DEFAULT)
     ap.add_argument("--tol", type=float, default=TOL_DEFAULT)
@@ -62,6 +70,10 @@ def parse():
     ap.add_argument("--no-compare", action="store_true", help="skip the n = 4096 method comparison")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--batch-steps", type=int, default=2000)
+    ap.add_argument("--mode", choices=["bench", "phases", "plain"], default="bench",
+                    help="phases: per-phase CUDA-event times of single AdaRBFGS steps (--prec may list forms, "
+                         "comma-separated); plain: --warmup + --steps steps with no events, the form to put "
+                         "under a profiler")
     return ap.parse_args()
 
 
@@ -210,7 +222,7 @@ def oracle_sample(A_np, q, seed, steps_per_solve, budget_s):
     return {"value": 1.0 / per_solve, "unit": "solves/s", "cores": orc.n_threads(), "kind": "oracle",
             "sample": (f"{done} FP64 AdaRBFGS step(s) of the n={n}, q={q} workload in {dt:.1f} s "
                        f"({per_step:.2f} s/step), extrapolated to {steps_per_solve} steps per solve"),
-            "seconds_per_solve": per_solve}
+            "seconds_per_solve": per_solve, "steps_timed": done}
 
 
 def run_reference(args):
@@ -228,7 +240,7 @@ def run_reference(args):
     A = wl.c3_matrix(n=args.n, device=dev)
     A_np = np.asfortranarray(A.double().cpu().numpy() if dev else A)
     del A
-    steps_per_solve = int(os.environ.get("RB_REF_STEPS_PER_SOLVE", "0")) or estimate_steps(args.n, args.q)
+    steps_per_solve = steps_per_solve_for(args.n, args.q)
     budget = max(1.0, args.cpu_seconds / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
         oracle_sample(A_np, args.q, 1, steps_per_solve, budget)
@@ -242,7 +254,10 @@ def run_reference(args):
     out = {"impl": "reference", "metric": METRIC, "value": v, "unit": "solves/s", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_solve * 1e3,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-           "data": "synthetic", "config": config(args, "FP64 CPU oracle"),
+           "data": "synthetic", "config": config(args), "form": "FP64 CPU oracle",
+           "extrapolated": {"steps_per_solve": steps_per_solve,
+                            "source": "mean steps per solve of the GPU arm's timed solves of this workload",
+                            "oracle_steps_timed_per_bench_step": vals[0]["steps_timed"]},
            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": vals[0]["cores"], "kind": "oracle",
                             "sample": vals[0]["sample"]},
            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -250,16 +265,21 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
-def estimate_steps(n, q):
-    # AdaRBFGS steps to 1e-4 on this spectrum, about 11 n / q on GB300 runs; used only to
-    # scale the oracle's per-step time to a solve when no GPU count is at hand.
-    return int(os.environ.get("RB_STEPS_PER_SOLVE", str(max(1, int(11 * n / q)))))
+def steps_per_solve_for(n, q):
+    """Steps one solve takes, to scale the oracle's per-step time: the GPU arm's measured count for
+    the benchmarked workload (RB_REF_STEPS_PER_SOLVE overrides it), else about 11 n / q."""
+    env = int(os.environ.get("RB_REF_STEPS_PER_SOLVE", "0"))
+    if env > 0:
+        return env
+    if (n, q) == (N_DEFAULT, Q_DEFAULT):
+        return STEPS_PER_SOLVE_MEASURED
+    return max(1, int(11 * n / q))
 
 
-def config(args, form):
+def config(args):
     return {"workload": f"AdaRBFGS_gauss n={args.n} q={args.q} tol={args.tol:g}, A=M^T M/m+1e-4 I, "
                         f"M {4 * args.n}x{args.n} 1%-dense N(0,1)",
-            "n": args.n, "q": args.q, "tol": args.tol, "form": form, "parallelism": "replicas",
+            "n": args.n, "q": args.q, "tol": args.tol, "parallelism": "replicas",
             "l2": "inputs larger than L2 (A and L are 1 GiB each)",
             "residual_check": f"every {CHECK_EVERY} steps on {CHECK_COLS} columns, confirmed on {CONFIRM_COLS}"}
 
@@ -389,7 +409,7 @@ def run_exp1(B, wl, timed, st):
             try:
                 h, t_init = timed(make)
                 r0 = B.rbfgs_residual(h, 0, 0)
-                cap = 3000 if name.startswith("adarbfgs") else 300  # NS and MR stall (see DESIGN)
+                cap = 3000 if name.startswith("adarbfgs") else 300  # NS and MR stall: rounding swamps the smallest modes
                 (rc, it, r), t = timed(lambda: B.rbfgs_solve(h, 1e-2 * r0, cap, every, 256, 0))
                 row[name] = {"seconds": t_init + t, "iters": it, "relative_error": r / r0,
                              "converged": rc == B.RB_OK}
@@ -427,10 +447,43 @@ def run_batched(B, wl, args):
             "median_resid": float(np.median(resid)), "max_resid": float(np.max(resid))}
 
 
+def run_phases(args):
+    """--mode phases / plain: AdaRBFGS steps on the n x n workload, one handle per listed form."""
+    import torch
+
+    import paper_1602_01768_gb300._binding as B
+    from paper_1602_01768_gb300 import workloads as wl
+
+    torch.cuda.set_device(0)
+    A = wl.c3_matrix(n=args.n, device="cuda")
+    st = torch.cuda.current_stream().cuda_stream
+    for pn in args.prec.split(","):
+        o = B.make_opts(method=B.RB_METHOD_ADARBFGS, sketch=B.RB_SKETCH_GAUSS, q=args.q, prec=B.PREC[pn], seed=1,
+                        core_fp64=CORE_OPT[args.core])
+        h = B.rbfgs_init(args.n, A.data_ptr(), args.n, False, o, st)
+        B.adarbfgs_step(h, args.warmup)
+        if args.mode == "plain":
+            B.adarbfgs_step(h, args.steps)
+            B.rbfgs_sync(h)
+            print(json.dumps({"prec": pn, "n": args.n, "q": args.q, "steps": args.steps}), flush=True)
+        else:
+            prof = {}
+            for _ in range(args.steps):
+                for name, ms in B.rbfgs_profile_step(h):
+                    prof.setdefault(name, []).append(ms)
+            ph = {k: round(statistics.median(v), 4) for k, v in prof.items()}
+            print(json.dumps({"prec": pn, "n": args.n, "q": args.q, "phases_ms": ph,
+                              "step_ms": round(sum(ph.values()), 4)}), flush=True)
+        B.rbfgs_destroy(h)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.mode != "bench":
+        run_phases(args)
         return
     import numpy as np
     import torch
@@ -581,6 +634,7 @@ def main():
         A_np = np.asfortranarray(A.double().cpu().numpy())
         cpu = oracle_sample(A_np, q, 5, int(round(statistics.mean(iters))), args.cpu_seconds)
         cpu.pop("seconds_per_solve", None)
+        cpu.pop("steps_timed", None)
         del A_np
 
     B.rbfgs_destroy(h)
@@ -590,7 +644,7 @@ def main():
         out = {"metric": METRIC, "value": solves_per_s, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": t_solve * 1e3, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-               "data": "synthetic", "config": config(args, args.prec),
+               "data": "synthetic", "config": config(args), "form": args.prec,
                "time_to_tol_s": t_solve, "iters_per_solve": iters, "resid_final": resids,
                "latency_s": {"p50": statistics.median(lat), "p99": p99},
                "fp32_form": fp32, "roofline": roofline, "gemm_rooflines": gemm_rooflines, "phases_ms": phases, "step_ms": step_ms,
