@@ -60,7 +60,7 @@ typedef enum {
 
 typedef enum {
     RB_FP64 = 0,    /* FP64 storage and arithmetic (the parity mode) */
-    RB_FP32 = 1,    /* FP32 storage, FP32 SIMT products, FP64 q x q core */
+    RB_FP32 = 1,    /* FP32 storage, FP32 SIMT products (q x q core: see rb_opts.core_fp64) */
     RB_TF32 = 2,    /* FP32 storage, single-pass TF32 tensor-core products */
     RB_TF32X3 = 3,  /* FP32 storage, 3-term split TF32 tensor-core products (~FP32 accuracy) */
     RB_MIXED = 4    /* FP32 storage, 3xTF32 where accuracy needs it, 1xTF32 for the
@@ -93,8 +93,9 @@ typedef struct {
     uint64_t seed;      /* Philox key of the sketch stream */
     uint64_t stream_id; /* Philox counter word 3: independent streams for one seed */
     int32_t power_iters;/* Newton-Schulz: power iterations for ||A||_2 (0 = 100) */
-    int32_t core_fp64;  /* AdaRBFGS with FP32 storage: 1 = factor the q x q matrices in FP64,
-                           0 = in FP32 (default; the matrices are only FP32-accurate there) */
+    int32_t core_fp64;  /* AdaRBFGS with FP32 storage, precision of the q x q Cholesky factors and
+                           their inverses: 1 = FP64, -1 = FP32, 0 = the form's default (FP32 for
+                           every FP32-storage form; FP64 storage always factors in FP64) */
     int32_t reserved[6];
 } rb_opts;
 
@@ -114,7 +115,7 @@ rb_status rbfgs_init(rbfgs_t *h, int n, const void *A_dev, int64_t lda, int a_is
 
 /*
  * nsteps RBFGS steps (Algorithm 3, W = A^-1): draw S_k, G = A S, the q x q
- * core (Cholesky of S^T A S in FP64), Y = X G, T = G^T Y and the symmetric
+ * core (Cholesky of S^T A S in FP64 in every form), Y = X G, T = G^T Y and the symmetric
  * rank-2q update X += S W^T + W S^T, W = S (Lam + Lam T Lam)/2 - Y Lam, which
  * equals Eq. (qunac).  Asynchronous.  The handle must be an RBFGS handle.
  */
@@ -137,8 +138,8 @@ rb_status aip_step(rbfgs_t h, int nsteps);
 
 /*
  * nsteps AdaRBFGS steps (Algorithm 4, Eq. (Cholimprov)): draw S~_k,
- * S = L S~, G = A S, C C^T = S^T A S and D D^T = S~^T S~ (lower Cholesky;
- * FP64 for RB_FP64 storage or opts.core_fp64, else FP32), W = G^T L,
+ * S = L S~, G = A S, C C^T = S^T A S and D D^T = S~^T S~ (lower Cholesky in
+ * the precision opts.core_fp64 selects), W = G^T L,
  * V = D^-1 S~^T - C^-1 W, L += S C^-T V.  Asynchronous.
  */
 rb_status adarbfgs_step(rbfgs_t h, int nsteps);

@@ -313,6 +313,9 @@ static rb_status alloc_sketch_workspace(rb_ctx *h)
 
 static bool prec_ok(int prec) { return prec >= RB_FP64 && prec <= RB_MIXED; }
 
+// Default precision of the AdaRBFGS q x q core for each storage/product form.
+static int default_core_fp64(int prec) { return prec == RB_FP64 ? 1 : 0; }
+
 extern "C" rb_status rbfgs_init(rbfgs_t *out, int n, const void *A_dev, int64_t lda, int a_is_fp64,
                                 const rb_opts *opts, void *stream)
 {
@@ -337,7 +340,9 @@ extern "C" rb_status rbfgs_init(rbfgs_t *out, int n, const void *A_dev, int64_t 
     h->esz = h->f64 ? 8 : 4;
     h->seed = opts->seed;
     h->stream_id = opts->stream_id;
-    h->core_fp64 = opts->core_fp64 ? 1 : 0;
+    // q x q core precision with FP32 storage: FP64 when asked (> 0), FP32 when asked (< 0),
+    // else the form's default
+    h->core_fp64 = opts->core_fp64 > 0 ? 1 : opts->core_fp64 < 0 ? 0 : default_core_fp64(prec);
     h->st = (cudaStream_t)stream;
     rb_status s = RB_OK;
     do {
@@ -595,7 +600,10 @@ constexpr int SIDE_SMS_G = 4;
 static void ada_step_tc(rb_ctx *h)
 {
     const int n = h->n, q = h->q;
-    const bool fork = !h->core_fp64 && ensure_side_stream(h);
+    // the side-stream core writes its inverses straight into the tensor-core B operands, which
+    // needs q <= 128 and 16-byte rows; the FP64 core exists only in that form
+    const bool tcv_shape = q <= 128 && q % 4 == 0 && n % 4 == 0;
+    const bool fork = (!h->core_fp64 || tcv_shape) && ensure_side_stream(h);
     cudaStream_t user = h->st;
     if (fork) {  // run the step on st1 (every helper launches on h->st), joined to the caller's stream
         cudaEventRecord(h->ev_in, user);
@@ -613,7 +621,7 @@ static void ada_step_tc(rb_ctx *h)
     cudaStream_t side = fork ? h->st2 : st;
     // V and S^ on the tensor cores: the cores write their inverses transposed
     // straight into the B operands (needs q <= 128 and 16-byte rows)
-    bool tcv = fork && q <= 128 && q % 4 == 0 && n % 4 == 0;
+    bool tcv = fork && tcv_shape;
     if (tcv && !h->tc2) tcv = (h->tc2 = tc_plan_create(n, q, h->prec)) != nullptr;
     const bool fuse = tcv && upd == 1 && h->Spart;
     // the side stream's Gram products run stream-K on the SIDE_SMS SMs the main GEMMs leave free
@@ -646,7 +654,10 @@ static void ada_step_tc(rb_ctx *h)
         cudaStreamWaitEvent(side, h->ev_sk, 0);
         if (tcv) {  // S~^T S~ (products exact: S~ is TF32) -> D^-T into Bv
             tc_gemm_nk(h->tc2, side, 1, TC_A_K, q, q, n, St, n, St, n, h->Nf, q, stp, side_rsv_g);
-            launch_core_tr32(side, q, h->Nf, nullptr, h->Bv + dofs, 2 * q, 1.f, nullptr, 0, 0.f, h->d_status);
+            if (h->core_fp64)
+                launch_core_tr64(side, q, h->Nf, h->Bv + dofs, 2 * q, 1.f, nullptr, 0, 0.f, h->d_status);
+            else
+                launch_core_tr32(side, q, h->Nf, nullptr, h->Bv + dofs, 2 * q, 1.f, nullptr, 0, 0.f, h->d_status);
         } else {
             launch_gram<float>(side, n, q, q, St, n, St, n, h->part, h->N);  // S~^T S~ -> D^-1
             launch_core_ada32(side, q, h->N, nullptr, Di, nullptr, h->d_status);
@@ -664,7 +675,10 @@ static void ada_step_tc(rb_ctx *h)
         if (tcv) {  // S^T A S = S^T G (3 x TF32) -> -C^-T into Bv, C^-T into Bs
             tc_gemm_nk_lo(h->tc2, side, 3, TC_A_K, q, q, n, S, n, G, glo ? h->Glo : nullptr, n, h->Mf, nullptr, q,
                           stp, side_rsv);
-            launch_core_tr32(side, q, h->Mf, nullptr, h->Bv + cofs, 2 * q, -1.f, h->Bs, q, 1.f, h->d_status);
+            if (h->core_fp64)
+                launch_core_tr64(side, q, h->Mf, h->Bv + cofs, 2 * q, -1.f, h->Bs, q, 1.f, h->d_status);
+            else
+                launch_core_tr32(side, q, h->Mf, nullptr, h->Bv + cofs, 2 * q, -1.f, h->Bs, q, 1.f, h->d_status);
         } else {
             launch_gram<float>(side, n, q, q, S, n, G, n, h->part, h->M);    // S^T A S -> C^-1
             launch_core_ada32(side, q, h->M, nullptr, Ci, nullptr, h->d_status);

@@ -32,6 +32,10 @@ void launch_core_ada32(cudaStream_t, int q, const double *M, const double *N, fl
 // into xt2 (ld2) (either may be null).  Returns false for q > 128.
 bool launch_core_tr32(cudaStream_t, int q, const float *M, float *Xinv, float *xt1, int ld1, float s1, float *xt2,
                       int ld2, float s2, int *status);
+// q <= 128: the same in FP64 (core64.cu): X = L^-1 of sym(M) factored and inverted in
+// FP64, written only as the scaled FP32 transposes s1 X^T / s2 X^T.
+bool launch_core_tr64(cudaStream_t, int q, const float *M, float *xt1, int ld1, float s1, float *xt2, int ld2,
+                      float s2, int *status);
 template <typename T>
 void launch_core_rbfgs(cudaStream_t, int q, const double *M, const double *Tm, T *Lam, T *B1, int *status);
 template <typename T>
