@@ -63,8 +63,13 @@ typedef enum {
     RB_FP32 = 1,    /* FP32 storage, FP32 SIMT products (q x q core: see rb_opts.core_fp64) */
     RB_TF32 = 2,    /* FP32 storage, single-pass TF32 tensor-core products */
     RB_TF32X3 = 3,  /* FP32 storage, 3-term split TF32 tensor-core products (~FP32 accuracy) */
-    RB_MIXED = 4    /* FP32 storage, 3xTF32 where accuracy needs it, 1xTF32 for the
+    RB_MIXED = 4,   /* FP32 storage, 3xTF32 where accuracy needs it, 1xTF32 for the
                        rank-q correction whose size vanishes at the fixed point */
+    RB_BF16 = 5,    /* AdaRBFGS only: as RB_TF32, with the two n x n-streaming products
+                       G = A S and W^T = L^T G in one BF16 pass (8 significant bits) */
+    RB_BF16X3 = 6   /* AdaRBFGS only: as RB_MIXED, with G = A S and W^T = L^T G as 3-term
+                       BF16 splits (hi hi + hi lo + lo hi, ~16 significant bits): half the
+                       tensor-core work of 3xTF32 for the two passes that stream A and L */
 } rb_prec;
 
 typedef enum {
@@ -268,8 +273,10 @@ rb_status rbfgs_export_host(rbfgs_t h, int what, void *out_host, int64_t ld);
  * Run ONE step of the handle's method with a CUDA event recorded on its
  * stream at every phase boundary (sketch draw, each n x n pass, q x q core,
  * update).  ms[i] gets the device time of phase i and names[i] (if names is
- * not NULL) its name, for i < *nphases <= cap.  The step is a real step: it
- * advances the iterate and k.  Synchronises.
+ * not NULL) its name, for i < *nphases <= cap.  Entries whose name starts
+ * with '@' follow the phases: they mark the end of work on the internal side
+ * streams (the q x q cores) as the time from the start of the step.  The
+ * step is a real step: it advances the iterate and k.  Synchronises.
  */
 rb_status rbfgs_profile_step(rbfgs_t h, double *ms, const char **names, int cap, int *nphases);
 

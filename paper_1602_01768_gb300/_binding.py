@@ -13,12 +13,13 @@ from . import build as _build
 RB_OK, RB_NOTCONV = 0, 1
 RB_EINVAL, RB_ENOMEM, RB_ECUDA, RB_ENOTSPD, RB_ENONFINITE, RB_ETIMEOUT, RB_EUNSUPPORTED = -1, -2, -3, -4, -5, -6, -7
 
-RB_FP64, RB_FP32, RB_TF32, RB_TF32X3, RB_MIXED = 0, 1, 2, 3, 4
+RB_FP64, RB_FP32, RB_TF32, RB_TF32X3, RB_MIXED, RB_BF16, RB_BF16X3 = 0, 1, 2, 3, 4, 5, 6
 RB_SKETCH_GAUSS, RB_SKETCH_COORD_TRACE, RB_SKETCH_COORD_UNIFORM = 0, 1, 2
 RB_METHOD_RBFGS, RB_METHOD_ADARBFGS, RB_METHOD_NS, RB_METHOD_MR, RB_METHOD_AIP = 0, 1, 2, 3, 4
 RB_WHAT_X, RB_WHAT_L = 0, 1
 
-PREC = {"fp64": RB_FP64, "fp32": RB_FP32, "tf32": RB_TF32, "tf32x3": RB_TF32X3, "mixed": RB_MIXED}
+PREC = {"fp64": RB_FP64, "fp32": RB_FP32, "tf32": RB_TF32, "tf32x3": RB_TF32X3, "mixed": RB_MIXED, "bf16": RB_BF16,
+        "bf16x3": RB_BF16X3}
 
 
 class RbOpts(C.Structure):

@@ -8,6 +8,8 @@
 #include <algorithm>
 #include <vector>
 
+#include <cuda_bf16.h>
+
 #include "kernels.cuh"
 #include "tc.cuh"
 
@@ -32,8 +34,11 @@ struct rb_ctx {
     size_t spart_cap = 0;
     float *Slo = nullptr, *Glo = nullptr;  // lo parts (x - hi(x)) of S and G for the 3-term products
     bool slo_valid = false;                // Slo belongs to the S in place
+    bool sbf_valid = false;                // Sbf holds the BF16 parts of the S in place
     float *Bv = nullptr, *Bs = nullptr;  // tensor-core V and S^: [D^-T; -C^-T] (2q x q) and C^-T (q x q)
     float *Mf = nullptr, *Nf = nullptr;  // FP32 Gram products S^T A S and S~^T S~ (tensor-core path)
+    void *Sbf = nullptr, *Gbf = nullptr;  // BF16 forms: [hi | lo] BF16 parts of S and G (n x q each, ld ldbf)
+    int64_t ldbf = 0;
     tc_plan *tc2 = nullptr;              // plan (own workspace) for the side stream's tensor-core GEMMs
     void *P3 = nullptr;  // RBFGS: [S | W | S], n x 3q
     void *Cinv = nullptr, *Dinv = nullptr, *Lam = nullptr, *B1 = nullptr;  // q x q
@@ -59,6 +64,14 @@ struct rb_ctx {
     // events, joined back into the handle's stream at the end of each step).
     cudaStream_t st1 = nullptr, st2 = nullptr;
     cudaEvent_t ev_sk = nullptr, ev_g = nullptr, ev_core = nullptr, ev_in = nullptr, ev_out = nullptr;
+    // the D chain (S~^T S~ and its core) on a low-priority stream of its own, with its own
+    // tensor-core plan, so the C chain after G never queues behind it
+    cudaStream_t st3 = nullptr;
+    cudaEvent_t ev_d = nullptr, ev_v = nullptr;
+    tc_plan *tc3 = nullptr;
+    // fused steps: the next step's D^-T (its sketch does not depend on the iterate) is formed
+    // during this step's update; d_ready says it is in Bv for the step about to run
+    bool d_ready = false;
 
     // asynchronous residual check (rbfgs_residual_start / _poll)
     int *h_J = nullptr;           // pinned column sample
@@ -68,10 +81,11 @@ struct rb_ctx {
     cudaEvent_t ev_res = nullptr;
     int res_m = 0, res_pending = 0;
 
-    // phase profiling (rbfgs_profile_step): events recorded between phases
-    int prof_on = 0, prof_n = 0;
-    cudaEvent_t prof_ev[24];
-    const char *prof_name[24];
+    // phase profiling (rbfgs_profile_step): events recorded between phases on the handle's
+    // stream, and side-stream marks (time from the step start)
+    int prof_on = 0, prof_n = 0, prof_ns = 0;
+    cudaEvent_t prof_ev[24], prof_side_ev[8];
+    const char *prof_name[24], *prof_side_name[8];
 };
 
 std::atomic<unsigned long long> g_rb_launches{0};
@@ -83,6 +97,14 @@ static inline void mark(rb_ctx *h, const char *ended)
     if (!h->prof_on || h->prof_n >= 23) return;
     h->prof_name[h->prof_n] = ended;
     cudaEventRecord(h->prof_ev[++h->prof_n], h->st);
+}
+
+// Side-stream mark: when profiling, record an event on stream s at the end of the named work.
+static inline void mark_side(rb_ctx *h, cudaStream_t s, const char *name)
+{
+    if (!h->prof_on || h->prof_ns >= 8) return;
+    h->prof_side_name[h->prof_ns] = name;
+    cudaEventRecord(h->prof_side_ev[h->prof_ns++], s);
 }
 
 static void rb_free(void *&p)
@@ -150,6 +172,8 @@ static void destroy_ctx(rb_ctx *h)
     rb_freet(h->Glo);
     rb_freet(h->Mf);
     rb_freet(h->Nf);
+    rb_free(h->Sbf);
+    rb_free(h->Gbf);
     if (h->tc2) tc_plan_destroy(h->tc2);
     h->tc2 = nullptr;
     rb_freet(h->part);
@@ -180,6 +204,10 @@ static void destroy_ctx(rb_ctx *h)
     if (h->ev_out) cudaEventDestroy(h->ev_out);
     if (h->st1) cudaStreamDestroy(h->st1);
     if (h->st2) cudaStreamDestroy(h->st2);
+    if (h->st3) cudaStreamDestroy(h->st3);
+    if (h->ev_d) cudaEventDestroy(h->ev_d);
+    if (h->ev_v) cudaEventDestroy(h->ev_v);
+    if (h->tc3) tc_plan_destroy(h->tc3);
     delete h;
 }
 
@@ -295,6 +323,12 @@ static rb_status alloc_sketch_workspace(rb_ctx *h)
             RB_TRY(rb_alloc(&h->Slo, nq));
             RB_TRY(rb_alloc(&h->Glo, nq));
         }
+        if (h->prec == RB_BF16 || h->prec == RB_BF16X3) {
+            h->ldbf = (h->n + 7) & ~(int64_t)7;  // 16-byte rows for TMA
+            const size_t half = (size_t)h->ldbf * q * 2;  // bytes of one BF16 n x q panel
+            RB_TRY(rb_alloc(&h->Sbf, 2 * half));
+            RB_TRY(rb_alloc(&h->Gbf, 2 * half));
+        }
     }
     RB_TRY(rb_alloc(&h->V, nq));
     RB_TRY(rb_alloc(&h->Cinv, qq));
@@ -311,7 +345,8 @@ static rb_status alloc_sketch_workspace(rb_ctx *h)
     return RB_OK;
 }
 
-static bool prec_ok(int prec) { return prec >= RB_FP64 && prec <= RB_MIXED; }
+static bool prec_ok(int prec) { return prec >= RB_FP64 && prec <= RB_BF16X3; }
+static bool prec_bf16(int prec) { return prec == RB_BF16 || prec == RB_BF16X3; }
 
 // Default precision of the AdaRBFGS q x q core for each storage/product form.
 static int default_core_fp64(int prec) { return prec == RB_FP64 ? 1 : 0; }
@@ -330,6 +365,7 @@ extern "C" rb_status rbfgs_init(rbfgs_t *out, int n, const void *A_dev, int64_t 
         return RB_EUNSUPPORTED;
     if (method == RB_METHOD_ADARBFGS && sketch != RB_SKETCH_GAUSS && sketch != RB_SKETCH_COORD_UNIFORM)
         return RB_EUNSUPPORTED;
+    if (prec_bf16(prec) && method != RB_METHOD_ADARBFGS) return RB_EUNSUPPORTED;
     rb_ctx *h = new rb_ctx();
     h->method = method;
     h->sketch = sketch;
@@ -570,13 +606,14 @@ static void ada_step_simt(rb_ctx *h)
 
 static bool ensure_side_stream(rb_ctx *h)
 {
-    if (h->st1 && h->st2 && h->ev_out) return true;
+    if (h->st1 && h->st2 && h->st3 && h->ev_v) return true;
     int least = 0, greatest = 0;
     cudaDeviceGetStreamPriorityRange(&least, &greatest);
     if (!h->st1 && cudaStreamCreateWithPriority(&h->st1, cudaStreamNonBlocking, greatest) != cudaSuccess) return false;
     if (!h->st2 && cudaStreamCreateWithPriority(&h->st2, cudaStreamNonBlocking, least) != cudaSuccess) return false;
+    if (!h->st3 && cudaStreamCreateWithPriority(&h->st3, cudaStreamNonBlocking, least) != cudaSuccess) return false;
     const unsigned fl = cudaEventDisableTiming;
-    for (cudaEvent_t *e : {&h->ev_sk, &h->ev_g, &h->ev_core, &h->ev_in, &h->ev_out})
+    for (cudaEvent_t *e : {&h->ev_sk, &h->ev_g, &h->ev_core, &h->ev_in, &h->ev_out, &h->ev_d, &h->ev_v})
         if (!*e && cudaEventCreateWithFlags(e, fl) != cudaSuccess) return false;
     return true;
 }
@@ -587,6 +624,23 @@ static bool ensure_side_stream(rb_ctx *h)
 // one-pass S~^T S~ and D^-1, for which 4 suffice.
 constexpr int SIDE_SMS = 8;
 constexpr int SIDE_SMS_G = 4;
+// SMs the fused update leaves to the next step's D chain (S~^T S~ and its core)
+constexpr int SIDE_SMS_UPD = 4;
+// CTAs of S^T G when it runs on the main stream (split over K; stream-K partial tiles)
+constexpr int GRAM_CTAS = 64;
+
+// D chain on the handle's D stream: S~^T S~ (one exact pass: S~ is TF32) on the SMs other
+// work leaves free, then its core, D^-T written as rows dofs .. dofs + q - 1 of Bv.
+static void ada_d_chain(rb_ctx *h, const float *St, int dofs, int reserve)
+{
+    const int n = h->n, q = h->q;
+    tc_gemm_nk(h->tc3, h->st3, 1, TC_A_K, q, q, n, St, n, St, n, h->Nf, q, h->d_status, reserve);
+    if (h->core_fp64)
+        launch_core_tr64(h->st3, q, h->Nf, h->Bv + dofs, 2 * q, 1.f, nullptr, 0, 0.f, h->d_status);
+    else
+        launch_core_tr32(h->st3, q, h->Nf, nullptr, h->Bv + dofs, 2 * q, 1.f, nullptr, 0, 0.f, h->d_status);
+    cudaEventRecord(h->ev_d, h->st3);
+}
 
 // Tensor-core step.  The q x q work runs on a low-priority side stream while
 // the n x n passes run on a high-priority one; the GEMMs that overlap side
@@ -615,17 +669,26 @@ static void ada_step_tc(rb_ctx *h)
     float *A = (float *)h->A, *L = (float *)h->X, *S = (float *)h->S, *G = (float *)h->G;
     float *W = (float *)h->W, *V = (float *)h->V, *Sh = (float *)h->Sh, *Ci = (float *)h->Cinv,
           *Di = (float *)h->Dinv;
-    const int acc = (h->prec == RB_TF32) ? 1 : 3;  // split terms of the accuracy-critical products
+    const int acc = (h->prec == RB_TF32 || h->prec == RB_BF16) ? 1 : 3;  // split terms, accuracy-critical products
     const int upd = (h->prec == RB_TF32X3) ? 3 : 1;
-    const int rsv = fork ? SIDE_SMS : 0, rsv_g = fork ? SIDE_SMS_G : 0;
+    // BF16 forms: G = A S and W^T = L^T G as BF16-split products (1 or 3 terms)
+    const int bfterms = h->prec == RB_BF16X3 ? 3 : h->prec == RB_BF16 ? 1 : 0;
+    const size_t bfhalf = (size_t)h->ldbf * q;  // elements of one BF16 panel
+    const int side_sms = SIDE_SMS;
+    const int rsv = fork ? side_sms : 0;
     cudaStream_t side = fork ? h->st2 : st;
     // V and S^ on the tensor cores: the cores write their inverses transposed
     // straight into the B operands (needs q <= 128 and 16-byte rows)
     bool tcv = fork && tcv_shape;
     if (tcv && !h->tc2) tcv = (h->tc2 = tc_plan_create(n, q, h->prec)) != nullptr;
+    if (tcv && !h->tc3) tcv = (h->tc3 = tc_plan_create(n, q, h->prec)) != nullptr;
     const bool fuse = tcv && upd == 1 && h->Spart;
+    // the next step's D chain runs during this step's fused update
+    const bool dpipe = fuse;
+    const bool d_now = tcv && !(dpipe && h->d_ready);  // this step's D chain still to run (during G)
+    const int rsv_g = (fork && (d_now || !tcv)) ? SIDE_SMS_G : 0;
     // the side stream's Gram products run stream-K on the SIDE_SMS SMs the main GEMMs leave free
-    const int side_rsv = std::max(0, tc_num_sms() - SIDE_SMS), side_rsv_g = std::max(0, tc_num_sms() - SIDE_SMS_G);
+    const int side_rsv = std::max(0, tc_num_sms() - side_sms), side_rsv_g = std::max(0, tc_num_sms() - SIDE_SMS_G);
     // sketch buffers: [S~_a | W^T | S~_b]; step k uses S~_a (k even) or S~_b (k odd) when fused
     const bool odd = fuse && (h->k & 1);
     float *St = odd ? (float *)h->Stb : (float *)h->St;
@@ -637,12 +700,17 @@ static void ada_step_tc(rb_ctx *h)
         ada_draw<float>(h, St, h->k);
         mark(h, "sketch");
         h->slo_valid = false;
+        h->sbf_valid = false;
         if (fuse) {  // S = L S~ from the fused kernel without the update, so every S comes from one path
-            const int rc = tc_update_next_s(st, n, q, Sh, V, L, n, St, S, 0, h->Spart, h->spart_cap, stp, h->Slo);
-            if (rc != 0)
+            // (the same grid as the fused updates, so S's partial sums are added in the same order)
+            const int rc = tc_update_next_s(st, n, q, Sh, V, L, n, St, S, 0, h->Spart, h->spart_cap, stp, h->Slo,
+                                            bfterms ? h->Sbf : nullptr, h->ldbf, dpipe ? SIDE_SMS_UPD : 0);
+            if (rc != 0) {
                 tc_gemm_nk(h->tc, st, acc == 3 ? 2 : acc, TC_A_MN, n, q, n, L, n, St, n, S, n, stp);
-            else
+            } else {
                 h->slo_valid = h->Slo != nullptr;
+                h->sbf_valid = bfterms != 0;
+            }
         } else {
             // S = L S~ (A = L, M-contiguous); S~ is exact in TF32, so the split needs only L's two parts
             tc_gemm_nk(h->tc, st, acc == 3 ? 2 : acc, TC_A_MN, n, q, n, L, n, St, n, S, n, stp);
@@ -651,14 +719,14 @@ static void ada_step_tc(rb_ctx *h)
     }
     if (fork) {
         cudaEventRecord(h->ev_sk, st);
-        cudaStreamWaitEvent(side, h->ev_sk, 0);
-        if (tcv) {  // S~^T S~ (products exact: S~ is TF32) -> D^-T into Bv
-            tc_gemm_nk(h->tc2, side, 1, TC_A_K, q, q, n, St, n, St, n, h->Nf, q, stp, side_rsv_g);
-            if (h->core_fp64)
-                launch_core_tr64(side, q, h->Nf, h->Bv + dofs, 2 * q, 1.f, nullptr, 0, 0.f, h->d_status);
-            else
-                launch_core_tr32(side, q, h->Nf, nullptr, h->Bv + dofs, 2 * q, 1.f, nullptr, 0, 0.f, h->d_status);
+        if (tcv) {  // S~^T S~ -> D^-T into Bv, on the D chain's own stream (unless the previous step did it)
+            if (d_now) {
+                cudaStreamWaitEvent(h->st3, h->ev_sk, 0);
+                ada_d_chain(h, St, dofs, side_rsv_g);
+                mark_side(h, h->st3, "@D core done");
+            }
         } else {
+            cudaStreamWaitEvent(side, h->ev_sk, 0);
             launch_gram<float>(side, n, q, q, St, n, St, n, h->part, h->N);  // S~^T S~ -> D^-1
             launch_core_ada32(side, q, h->N, nullptr, Di, nullptr, h->d_status);
         }
@@ -666,15 +734,32 @@ static void ada_step_tc(rb_ctx *h)
     // G = A S (A symmetric); S's lo part comes from the kernel that formed S, and G's is
     // written beside G for the two products that take G as their B (W and S^T G)
     const bool glo = acc == 3 && h->Glo != nullptr;
-    tc_gemm_nk_lo(h->tc, st, acc, TC_A_K, n, q, n, A, n, S, (acc == 3 && h->slo_valid) ? h->Slo : nullptr, n, G,
-                  glo ? h->Glo : nullptr, n, stp, rsv_g);
+    bool gbf = false;
+    if (bfterms) {  // S's BF16 parts come from the kernel that formed S (else split here); G's are written beside G
+        __nv_bfloat16_raw *sb = (__nv_bfloat16_raw *)h->Sbf;
+        if (!h->sbf_valid) tc_split_bf16(st, n, q, S, n, sb, sb + bfhalf, h->ldbf);
+        gbf = tc_gemm_bf(h->tc, st, bfterms, n, q, n, A, n, sb, sb + bfhalf, h->ldbf, G, glo ? h->Glo : nullptr, n,
+                         stp, rsv_g, h->Gbf, h->ldbf) == 0;
+    }
+    if (!gbf)
+        tc_gemm_nk_lo(h->tc, st, acc, TC_A_K, n, q, n, A, n, S, (acc == 3 && h->slo_valid) ? h->Slo : nullptr, n, G,
+                      glo ? h->Glo : nullptr, n, stp, rsv_g);
     mark(h, fork ? "G=AS | D core" : "G=AS");
     if (fork) {
+        // S^T G (3 x TF32) on the main stream right after G, split over K on GRAM_CTAS CTAs with the
+        // whole GPU free, so that only the C core overlaps W (3-term forms, whose G carries its lo part)
+        const bool gram_main = tcv && glo &&
+                               tc_gemm_splitk(h->tc, st, 3, TC_A_K, q, q, n, S, n, G, h->Glo, n, h->Mf, q, stp,
+                                              GRAM_CTAS) == 0;
+        if (gram_main) mark(h, "S^T G");
         cudaEventRecord(h->ev_g, st);
         cudaStreamWaitEvent(side, h->ev_g, 0);
         if (tcv) {  // S^T A S = S^T G (3 x TF32) -> -C^-T into Bv, C^-T into Bs
-            tc_gemm_nk_lo(h->tc2, side, 3, TC_A_K, q, q, n, S, n, G, glo ? h->Glo : nullptr, n, h->Mf, nullptr, q,
-                          stp, side_rsv);
+            if (!gram_main) {
+                tc_gemm_nk_lo(h->tc2, side, 3, TC_A_K, q, q, n, S, n, G, glo ? h->Glo : nullptr, n, h->Mf, nullptr,
+                              q, stp, side_rsv);
+                mark_side(h, side, "@S^T G done");
+            }
             if (h->core_fp64)
                 launch_core_tr64(side, q, h->Mf, h->Bv + cofs, 2 * q, -1.f, h->Bs, q, 1.f, h->d_status);
             else
@@ -684,6 +769,7 @@ static void ada_step_tc(rb_ctx *h)
             launch_core_ada32(side, q, h->M, nullptr, Ci, nullptr, h->d_status);
         }
         cudaEventRecord(h->ev_core, side);
+        mark_side(h, side, "@C core done");
         // off the main stream while it runs W's tail and V: S^ = S C^-T (it needs only S and the C
         // core) and the next step's sketch (its buffer is free: nothing of this step reads it); only
         // the fused update waits for them
@@ -702,9 +788,19 @@ static void ada_step_tc(rb_ctx *h)
             launch_core_ada<float>(st, q, h->M, h->N, Ci, Di, h->d_status);
         mark(h, "q x q core");
     }
-    tc_gemm_nk_lo(h->tc, st, acc, TC_A_K, n, q, n, L, n, G, glo ? h->Glo : nullptr, n, W, nullptr, n, stp,
-                  rsv);  // W^T = L^T G (n x q)
-    if (fork) cudaStreamWaitEvent(st, h->ev_core, 0);                            // join: C^-1, D^-1 ready
+    bool wbf = false;
+    if (bfterms) {  // W^T = L^T G on G's BF16 parts (written by G's epilogue unless G fell back)
+        __nv_bfloat16_raw *gb = (__nv_bfloat16_raw *)h->Gbf;
+        if (!gbf) tc_split_bf16(st, n, q, G, n, gb, gb + bfhalf, h->ldbf);
+        wbf = tc_gemm_bf(h->tc, st, bfterms, n, q, n, L, n, gb, gb + bfhalf, h->ldbf, W, nullptr, n, stp, rsv) == 0;
+    }
+    if (!wbf)
+        tc_gemm_nk_lo(h->tc, st, acc, TC_A_K, n, q, n, L, n, G, glo ? h->Glo : nullptr, n, W, nullptr, n, stp,
+                      rsv);  // W^T = L^T G (n x q)
+    if (fork) {  // join: C^-1 and D^-1 ready
+        cudaStreamWaitEvent(st, h->ev_core, 0);
+        if (tcv) cudaStreamWaitEvent(st, h->ev_d, 0);
+    }
     mark(h, fork ? "W=G^TL | C core" : "W=G^TL");
     if (tcv) {
         // V^T = [S~ | W^T] [D^-T; -C^-T] (or both halves swapped), written transposed: V is q x n (ld q)
@@ -726,13 +822,23 @@ static void ada_step_tc(rb_ctx *h)
             cudaStreamWaitEvent(st, h->ev_g, 0);
         else
             ada_draw<float>(h, St_next, h->k + 1);
-        const int rc = tc_update_next_s(st, n, q, Sh, V, L, n, St_next, S, 1, h->Spart, h->spart_cap, stp, h->Slo);
+        if (dpipe) {  // V has read Bv and S~_{k+1} is drawn: the next step's D chain, beside the update
+            cudaEventRecord(h->ev_v, st);
+            cudaStreamWaitEvent(h->st3, h->ev_v, 0);
+            ada_d_chain(h, St_next, odd ? 0 : q, std::max(0, tc_num_sms() - SIDE_SMS_UPD));
+            mark_side(h, h->st3, "@next D core done");
+        }
+        const int rc = tc_update_next_s(st, n, q, Sh, V, L, n, St_next, S, 1, h->Spart, h->spart_cap, stp, h->Slo,
+                                        bfterms ? h->Sbf : nullptr, h->ldbf, dpipe ? SIDE_SMS_UPD : 0);
+        h->d_ready = dpipe && rc == 0;
         if (rc == 0) {
             h->s_valid = true;
             h->slo_valid = h->Slo != nullptr;
+            h->sbf_valid = bfterms != 0;
         } else {
             h->s_valid = false;
             h->slo_valid = false;
+            h->sbf_valid = false;
             if (tc_update_persistent(h->tc, st, n, q, Sh, V, L, n, stp) != 0)
                 tc_update(h->tc, st, upd, n, q, Sh, V, L, n, stp);
         }
@@ -942,6 +1048,7 @@ extern "C" rb_status rbfgs_footprint(int n, const rb_opts *opts, size_t *bytes)
     b += 3 * (size_t)n * 1024 * e;                        // residual workspace (<= 1024 columns)
     if (x_sketch_method(opts->method)) b += 3 * (size_t)n * q * e;
     b += 2 * (size_t)n * q * e;                           // tensor-core operand splits
+    if (opts->prec == RB_BF16 || opts->prec == RB_BF16X3) b += 4 * (size_t)(n + 8) * q * 2;  // BF16 parts of S, G
     *bytes = b + (1u << 20);
     return RB_OK;
 }
@@ -1019,6 +1126,7 @@ extern "C" rb_status rbfgs_import(rbfgs_t h, int what, const void *in, int64_t l
         launch_copy2d<float, float>(h->st, n, n, (const float *)in, ld, (float *)h->X, n, 1.0);
     RB_CUDA(cudaMemsetAsync(h->d_status, 0, sizeof(int), h->st));
     h->s_valid = false;
+    h->d_ready = false;
     RB_CUDA(cudaGetLastError());
     return RB_OK;
 }
@@ -1028,6 +1136,7 @@ extern "C" rb_status rbfgs_set_step(rbfgs_t h, uint64_t k)
     if (!h) return RB_EINVAL;
     h->k = k;
     h->s_valid = false;
+    h->d_ready = false;
     return RB_OK;
 }
 
@@ -1089,6 +1198,7 @@ static rb_status init_dense_method(rbfgs_t *out, int method, int n, const void *
 {
     if (!out || !A_dev || n < 1 || lda < n || !prec_ok(prec)) return RB_EINVAL;
     *out = nullptr;
+    if (prec_bf16(prec)) return RB_EUNSUPPORTED;
     rb_ctx *h = new rb_ctx();
     h->method = method;
     h->prec = prec;
@@ -1274,6 +1384,7 @@ extern "C" rb_status rbfgs_reset(rbfgs_t h, uint64_t seed, uint64_t stream_id)
     h->seed = seed;
     h->stream_id = stream_id;
     h->s_valid = false;
+    h->d_ready = false;
     RB_CUDA(cudaGetLastError());
     return RB_OK;
 }
@@ -1289,8 +1400,10 @@ extern "C" rb_status rbfgs_profile_step(rbfgs_t h, double *ms, const char **name
 {
     if (!h || !ms || !nphases || cap < 1) return RB_EINVAL;
     for (int i = 0; i < 24; ++i) RB_CUDA(cudaEventCreate(&h->prof_ev[i]));
+    for (int i = 0; i < 8; ++i) RB_CUDA(cudaEventCreate(&h->prof_side_ev[i]));
     h->prof_on = 1;
     h->prof_n = 0;
+    h->prof_ns = 0;
     cudaEventRecord(h->prof_ev[0], h->st);
     rb_status s;
     if (h->method == RB_METHOD_RBFGS)
@@ -1305,14 +1418,23 @@ extern "C" rb_status rbfgs_profile_step(rbfgs_t h, double *ms, const char **name
         s = mr_step(h, 1);
     h->prof_on = 0;
     cudaError_t e = cudaEventSynchronize(h->prof_ev[h->prof_n]);
-    const int np = std::min(h->prof_n, cap);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();  // the side-stream marks too
+    int np = std::min(h->prof_n, cap);
     for (int i = 0; i < np && e == cudaSuccess; ++i) {
         float t = 0.f;
         cudaEventElapsedTime(&t, h->prof_ev[i], h->prof_ev[i + 1]);
         ms[i] = t;
         if (names) names[i] = h->prof_name[i];
     }
+    // side-stream marks (names start with '@'): time from the step start, not a phase length
+    for (int i = 0; i < h->prof_ns && np < cap && e == cudaSuccess; ++i, ++np) {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, h->prof_ev[0], h->prof_side_ev[i]);
+        ms[np] = t;
+        if (names) names[np] = h->prof_side_name[i];
+    }
     for (int i = 0; i < 24; ++i) cudaEventDestroy(h->prof_ev[i]);
+    for (int i = 0; i < 8; ++i) cudaEventDestroy(h->prof_side_ev[i]);
     *nphases = np;
     if (s != RB_OK) return s;
     return e == cudaSuccess ? RB_OK : RB_ECUDA;
@@ -1343,6 +1465,7 @@ extern "C" rb_status rbfgs_load_host(rbfgs_t h, const void *A_host, int64_t lda,
     else
         launch_set_identity<float>(h->st, n, (float *)h->X, n, 1.0f);
     h->s_valid = false;
+    h->d_ready = false;
     RB_CUDA(cudaMemsetAsync(h->d_status, 0, sizeof(int), h->st));
     h->k = 0;
     if (x_sketch_method(h->method) && h->sketch == RB_SKETCH_COORD_TRACE) {

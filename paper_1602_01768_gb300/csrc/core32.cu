@@ -225,9 +225,10 @@ __global__ void __launch_bounds__(KT, 1) k_core_blk(int q, CoreOut o0, CoreOut o
     }
     __syncthreads();
     // ... then the lower triangle takes the symmetric part 0.5 (a_ij + a_ji) (upper left as it is)
-    for (int e = tid; e < QP * QP; e += KT) {
-        const int i = e % QP, j = e / QP;
-        if (i > j) ak(a, i, j) = 0.5f * (ak(a, i, j) + ak(a, j, i));
+    {
+        const int i = tid & 127;
+        if (i < QP)
+            for (int j = tid >> 7; j < i; j += 4) ak(a, i, j) = 0.5f * (ak(a, i, j) + ak(a, j, i));
     }
     __syncthreads();
     for (int p = 0; p < nb; ++p) {
@@ -235,6 +236,8 @@ __global__ void __launch_bounds__(KT, 1) k_core_blk(int q, CoreOut o0, CoreOut o
         if (warp == 0) {
             // ---- diagonal block: L_pp in place (lane = row); compact loops keep the
             // code small (this runs once per block column, mostly alone on the SM) ----
+            // column j of L travels by warp shuffle (l_cj is lane c's lij), so the row
+            // updates below read nothing another lane writes and go 8 at a time
             bool bad = false;
             for (int j = 0; j < 32; ++j) {
                 const float d = ak(a, o + j, o + j);
@@ -247,23 +250,33 @@ __global__ void __launch_bounds__(KT, 1) k_core_blk(int q, CoreOut o0, CoreOut o
                 } else if (lane == j) {
                     ak(a, o + j, o + j) = sd;
                 }
-                __syncwarp();
-                for (int c = j + 1; c <= lane; ++c) ak(a, o + lane, o + c) -= lij * ak(a, o + c, o + j);
+                for (int c = j + 1; c < 32; c += 8) {  // the same trip count on every lane
+                    float lc[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) lc[u] = __shfl_sync(0xffffffffu, lij, (c + u) & 31);
+#pragma unroll
+                    for (int u = 0; u < 8; ++u)
+                        if (c + u <= lane) ak(a, o + lane, o + c + u) -= lij * lc[u];
+                }
                 __syncwarp();
             }
             if (bad) {
                 if (lane == 0) fail = 1;
             } else {
                 // ---- X_pp = L_pp^-1 (lane = column, kept in its column of x) ----
+                // rows i in order; x above the diagonal is written as zero first, so every
+                // lane sums k from 0 with four independent partial sums
                 for (int i = 0; i < 32; ++i) {
-                    float s0 = (i == lane) ? 1.f : 0.f, s1 = 0.f;
-                    int k = lane;
-                    for (; k + 1 < i; k += 2) {
+                    float s0 = (i == lane) ? 1.f : 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+                    int k = 0;
+                    for (; k + 3 < i; k += 4) {
                         s0 -= ak(a, o + i, o + k) * ak(x, o + k, o + lane);
                         s1 -= ak(a, o + i, o + k + 1) * ak(x, o + k + 1, o + lane);
+                        s2 -= ak(a, o + i, o + k + 2) * ak(x, o + k + 2, o + lane);
+                        s3 -= ak(a, o + i, o + k + 3) * ak(x, o + k + 3, o + lane);
                     }
-                    if (k < i) s0 -= ak(a, o + i, o + k) * ak(x, o + k, o + lane);
-                    ak(x, o + i, o + lane) = (i >= lane) ? (s0 + s1) / ak(a, o + i, o + i) : 0.f;
+                    for (; k < i; ++k) s0 -= ak(a, o + i, o + k) * ak(x, o + k, o + lane);
+                    ak(x, o + i, o + lane) = (i >= lane) ? ((s0 + s1) + (s2 + s3)) / ak(a, o + i, o + i) : 0.f;
                 }
             }
         }
@@ -282,10 +295,16 @@ __global__ void __launch_bounds__(KT, 1) k_core_blk(int q, CoreOut o0, CoreOut o
             if (e < npanel) {
                 const int blk = e >> 10, w = e & 1023, r = w & 31, c = w >> 5;  // row r, column c of block
                 const int i = o + 32 * (blk + 1) + r;
-                float sacc = 0.f;
-#pragma unroll 8
-                for (int k = 0; k <= c; ++k) sacc += ak(a, i, o + k) * ak(x, o + c, o + k);  // X_pp lower: k <= c
-                pv[u] = sacc;
+                float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+                int k = 0;
+                for (; k + 3 <= c; k += 4) {  // X_pp lower: k <= c
+                    s0 += ak(a, i, o + k) * ak(x, o + c, o + k);
+                    s1 += ak(a, i, o + k + 1) * ak(x, o + c, o + k + 1);
+                    s2 += ak(a, i, o + k + 2) * ak(x, o + c, o + k + 2);
+                    s3 += ak(a, i, o + k + 3) * ak(x, o + c, o + k + 3);
+                }
+                for (; k <= c; ++k) s0 += ak(a, i, o + k) * ak(x, o + c, o + k);
+                pv[u] = (s0 + s1) + (s2 + s3);
             }
         }
         __syncthreads();
@@ -309,10 +328,15 @@ __global__ void __launch_bounds__(KT, 1) k_core_blk(int q, CoreOut o0, CoreOut o
             }
             const int bi = bj + blk, w = e & 1023, r = w & 31, c = w >> 5;
             const int i = o + 32 * (bi + 1) + r, j = o + 32 * (bj + 1) + c;
-            float sacc = 0.f;
-#pragma unroll 8
-            for (int k = 0; k < 32; ++k) sacc += ak(a, i, o + k) * ak(a, j, o + k);
-            ak(a, i, j) -= sacc;
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+#pragma unroll 2
+            for (int k = 0; k < 32; k += 4) {
+                s0 += ak(a, i, o + k) * ak(a, j, o + k);
+                s1 += ak(a, i, o + k + 1) * ak(a, j, o + k + 1);
+                s2 += ak(a, i, o + k + 2) * ak(a, j, o + k + 2);
+                s3 += ak(a, i, o + k + 3) * ak(a, j, o + k + 3);
+            }
+            ak(a, i, j) -= (s0 + s1) + (s2 + s3);
         }
         __syncthreads();
     }
@@ -322,34 +346,47 @@ __global__ void __launch_bounds__(KT, 1) k_core_blk(int q, CoreOut o0, CoreOut o
         // T_(j+d, j) = sum_{k=j}^{j+d-1} L_(j+d, k) X_(k, j), stored in the upper block (j, j+d) of x
         for (int e = tid; e < nt; e += KT) {
             const int bj = e >> 10, w = e & 1023, r = w & 31, c = w >> 5, bi = bj + d;
-            float sacc = 0.f;
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
             for (int bk = bj; bk < bi; ++bk) {
-#pragma unroll 8
-                for (int k = 0; k < 32; ++k) sacc += ak(a, 32 * bi + r, 32 * bk + k) * ak(x, 32 * bk + k, 32 * bj + c);
+#pragma unroll 2
+                for (int k = 0; k < 32; k += 4) {
+                    s0 += ak(a, 32 * bi + r, 32 * bk + k) * ak(x, 32 * bk + k, 32 * bj + c);
+                    s1 += ak(a, 32 * bi + r, 32 * bk + k + 1) * ak(x, 32 * bk + k + 1, 32 * bj + c);
+                    s2 += ak(a, 32 * bi + r, 32 * bk + k + 2) * ak(x, 32 * bk + k + 2, 32 * bj + c);
+                    s3 += ak(a, 32 * bi + r, 32 * bk + k + 3) * ak(x, 32 * bk + k + 3, 32 * bj + c);
+                }
             }
-            ak(x, 32 * bj + r, 32 * bi + c) = sacc;  // transposed slot: row r of T at (bj, bi)
+            ak(x, 32 * bj + r, 32 * bi + c) = (s0 + s1) + (s2 + s3);  // transposed slot: row r of T at (bj, bi)
         }
         __syncthreads();
         // X_(i, j) = -X_ii T,  X_ii lower
         for (int e = tid; e < nt; e += KT) {
             const int bj = e >> 10, w = e & 1023, r = w & 31, c = w >> 5, bi = bj + d;
-            float sacc = 0.f;
-#pragma unroll 8
-            for (int k = 0; k <= r; ++k) sacc += ak(x, 32 * bi + r, 32 * bi + k) * ak(x, 32 * bj + k, 32 * bi + c);
-            ak(x, 32 * bi + r, 32 * bj + c) = -sacc;
+            float s0 = 0.f, s1 = 0.f, s2 = 0.f, s3 = 0.f;
+            int k = 0;
+            for (; k + 3 <= r; k += 4) {
+                s0 += ak(x, 32 * bi + r, 32 * bi + k) * ak(x, 32 * bj + k, 32 * bi + c);
+                s1 += ak(x, 32 * bi + r, 32 * bi + k + 1) * ak(x, 32 * bj + k + 1, 32 * bi + c);
+                s2 += ak(x, 32 * bi + r, 32 * bi + k + 2) * ak(x, 32 * bj + k + 2, 32 * bi + c);
+                s3 += ak(x, 32 * bi + r, 32 * bi + k + 3) * ak(x, 32 * bj + k + 3, 32 * bi + c);
+            }
+            for (; k <= r; ++k) s0 += ak(x, 32 * bi + r, 32 * bi + k) * ak(x, 32 * bj + k, 32 * bi + c);
+            ak(x, 32 * bi + r, 32 * bj + c) = -((s0 + s1) + (s2 + s3));
         }
         __syncthreads();
     }
     // ---- write X (lower; the upper triangle is zero) and the scaled transposes ----
-    for (int e = tid; e < q * q; e += KT) {
-        const int r = e % q, c = e / q;
-        const float v = (r >= c) ? ak(x, r, c) : 0.f;
-        if (!isfinite(v)) atomicOr(status, ST_NONFINITE);
-        if (out.dst) out.dst[e] = v;
-        // transposes walk r fastest over their own columns: entry (c, r) of X^T is X(r, c)
-        const float w = (c >= r) ? ak(x, c, r) : 0.f;  // X(c, r) = X^T(r, c)
-        if (out.xt1) out.xt1[r + (size_t)c * out.ld1] = out.s1 * w;
-        if (out.xt2) out.xt2[r + (size_t)c * out.ld2] = out.s2 * w;
+    const int r = tid & 127;  // thread: row r, every fourth column
+    if (r < q) {
+        for (int c = tid >> 7; c < q; c += 4) {
+            const float v = (r >= c) ? ak(x, r, c) : 0.f;
+            if (!isfinite(v)) atomicOr(status, ST_NONFINITE);
+            if (out.dst) out.dst[r + (size_t)c * q] = v;
+            // the transposes walk r fastest over their own columns: entry (r, c) of X^T is X(c, r)
+            const float w = (c >= r) ? ak(x, c, r) : 0.f;
+            if (out.xt1) out.xt1[r + (size_t)c * out.ld1] = out.s1 * w;
+            if (out.xt2) out.xt2[r + (size_t)c * out.ld2] = out.s2 * w;
+        }
     }
 }
 

@@ -31,6 +31,7 @@
 // that gives up records ST_TIMEOUT in the caller's status word and the CTA
 // winds down instead of hanging.
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -43,7 +44,14 @@
 namespace {
 using namespace tcx;
 
-template <int BN, int TERMS, int AMN>
+// BF = 1: kind::f16 products on BF16 parts of the FP32 operands.  The A tile
+// (FP32, K-contiguous) lands as two 128 x 32 boxes per 64-wide k-block and the
+// converter writes its BF16 parts into TMEM, two K-consecutive values per
+// 32-bit column (the lower K index in the low half); B comes pre-split as BF16
+// hi and lo panels (64 BF16 = one 128-byte swizzle row).  x = hi + lo with
+// hi = bf16(x), lo = bf16(x - hi) (round to nearest): the 3-term product
+// hi hi + hi lo + lo hi carries ~16 bits, each MMA covers K = 16.
+template <int BN, int TERMS, int AMN, int BF = 0>
 struct Cfg {
     // The A tile lands in shared memory by TMA; the converter warps write the
     // lo part (2 and 3 terms) into TMEM, and the hi part too for an
@@ -52,7 +60,7 @@ struct Cfg {
     // cuts the tensor core's shared-memory reads per k-block from 80 to 48 KB,
     // which is what held the two shared-memory-operand MMAs back (measured on
     // GB300: 0.31 against 0.36 ms for a 16384 x 16384 x 128 product).
-    static constexpr bool HI_TMEM = AMN != 0 || TERMS == 3;
+    static constexpr bool HI_TMEM = AMN != 0 || TERMS == 3 || BF != 0;
     // A k-step of a 3-term product issues two MMAs instead of three: hi x [B | B lo]
     // is one MMA of width 2 BN (B lo follows B in the stage, so the two form one
     // K-major operand of 2 BN rows) and lo x B the other.  The MMA issue rate, not
@@ -66,8 +74,10 @@ struct Cfg {
     static constexpr bool LO_TMEM = TERMS >= 2;
     static constexpr bool CONVERT = HI_TMEM || LO_TMEM;
     static constexpr int LO_OFF = HI_TMEM ? 32 : 0;  // TMEM column of lo within a stage
-    static constexpr int A_BYTES = A_TILE_BYTES;
-    static constexpr int B_BYTES = BN * BK * 4;
+    static constexpr int BKE = BF ? 64 : BK;          // K elements per k-block
+    static constexpr int CHUNK = CHUNK_KB * BK / BKE;  // k-blocks per accumulation chunk (512 of K)
+    static constexpr int A_BYTES = BM * BKE * 4;
+    static constexpr int B_BYTES = BN * BKE * (BF ? 2 : 4);
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES * (TERMS == 3 ? 2 : 1);  // [A | B | B lo]
     static constexpr int A_TMEM_COLS = 32 * ((HI_TMEM ? 1 : 0) + (LO_TMEM ? 1 : 0));
     // TMEM: two chunk accumulators (2 BN columns), then the A stages
@@ -78,6 +88,7 @@ struct Cfg {
     static constexpr int TMEM_COLS = CONVERT ? 512 : (2 * BN < 32 ? 32 : 2 * BN);
     static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 /*align*/ + 512 /*barriers*/;
     static_assert(STAGES >= 2, "pipeline needs two stages");
+    static_assert(!BF || (AMN == 0 && TERMS != 2), "BF16 products: K-contiguous A, 1 or 3 terms");
 };
 
 __device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
@@ -108,6 +119,25 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16
         "%15, %16};" ::"r"(taddr),
         "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
         "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+}
+
+// Instruction descriptor, kind::f16 with BF16 A and B (both the same type), D F32,
+// A and B K-major, N = n, M = 128.
+__host__ __device__ constexpr uint32_t idesc_bf16(int n)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
+
+// D (TMEM) += A (TMEM, BF16 pairs: M rows on lanes, K/2 on columns) x B (smem descriptor, BF16).
+__device__ __forceinline__ void mma_bf16_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b, uint32_t idesc,
+                                            uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b), "r"(idesc), "r"(acc)
         : "memory");
 }
 
@@ -151,14 +181,15 @@ __device__ __forceinline__ void load_a_half(const unsigned char *raw, int m, int
     }
 }
 
-template <int BN, int TERMS, int AMN>
+template <int BN, int TERMS, int AMN, int BF>
 __global__ void __launch_bounds__(384, 1)
 k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
           const __grid_constant__ CUtensorMap tmBlo, int M, int N, int mt, int nkb, long long U, int maxseg,
           float alpha, float beta, const float *Cin, int64_t ldcin, float *C, float *Clo, int64_t ldc, int ctrans,
-          float *part, int *tile_cnt, const int *status, int *err)
+          float *part, int *tile_cnt, const int *status, int *err, __nv_bfloat16 *Cbf, int64_t ldbf,
+          long long bfhalf)
 {
-    using CF = Cfg<BN, TERMS, AMN>;
+    using CF = Cfg<BN, TERMS, AMN, BF>;
     constexpr int STAGES = CF::STAGES;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     if (status_bad(status)) return;  // uniform: every thread reads the same word
@@ -227,8 +258,11 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                     if (i >= STAGES && !mbar_wait(smem_u32(&empty[s]), ((i / STAGES) - 1) & 1, err, abort_flag)) break;
                     const uint32_t fb = smem_u32(&full[s]);
                     mbar_expect_tx(fb, CF::STAGE_BYTES);
-                    const int k = kb * BK;
-                    if (AMN) {
+                    const int k = kb * CF::BKE;
+                    if (BF) {  // two 128 x 32 FP32 boxes per 64-wide k-block
+                        tma_load_2d(smem_u32(stage_a(s)), &tmA, k, m0, fb);
+                        tma_load_2d(smem_u32(stage_a(s) + A_TILE_BYTES), &tmA, k + BK, m0, fb);
+                    } else if (AMN) {
     #pragma unroll
                         for (int c = 0; c < BM / 32; ++c)
                             tma_load_2d(smem_u32(stage_a(s) + c * 4096), &tmA, m0 + 32 * c, k, fb);
@@ -254,8 +288,8 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                 int kb = kb_b, p = 0;  // k-block in the tile, position in the segment
                 for (int i = 0; i < nk; ++i) {
                     const int s = i % STAGES;
-                    const bool cstart = (p % CHUNK_KB) == 0;
-                    const bool cend = ((p + 1) % CHUNK_KB) == 0 || kb + 1 == nkb || i + 1 == nk;
+                    const bool cstart = (p % CF::CHUNK) == 0;
+                    const bool cend = ((p + 1) % CF::CHUNK) == 0 || kb + 1 == nkb || i + 1 == nk;
                     if (cstart) ++c;
                     const int b = CF::NACC == 2 ? (c & 1) : 0;
                     if (CF::NACC == 2) {
@@ -270,6 +304,25 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                     const uint32_t dacc = tmem + (uint32_t)(b * CF::ACC_COLS);
                     const uint32_t a_s = smem_u32(stage_a(s)), b_hi = smem_u32(stage_b(s)), b_lo = smem_u32(stage_blo(s));
                     const uint32_t ta = tmem + a_col(s);
+                    if (BF) {
+                        // K = 16 BF16 per MMA: 32 bytes along a 128-byte swizzle row of B, 8 TMEM columns of A
+    #pragma unroll
+                        for (int kk = 0; kk < CF::BKE / 16; ++kk) {
+                            const uint64_t db = umma_desc(b_hi + kk * 32, 16, 1024);
+                            const uint32_t first = (cstart && kk == 0) ? 0u : 1u;
+                            if (CF::PACK) {
+                                mma_bf16_ts(dacc, ta + 8 * kk, db, idesc_bf16(2 * BN), first);              // hi x [hi | lo]
+                                mma_bf16_ts(dacc, ta + CF::LO_OFF + 8 * kk, db, idesc_bf16(BN), 1u);        // lo x hi
+                            } else if (TERMS == 3) {
+                                mma_bf16_ts(dacc, ta + CF::LO_OFF + 8 * kk, db, idesc_bf16(BN), first);     // lo x hi
+                                mma_bf16_ts(dacc, ta + 8 * kk, umma_desc(b_lo + kk * 32, 16, 1024), idesc_bf16(BN),
+                                            1u);                                                            // hi x lo
+                                mma_bf16_ts(dacc, ta + 8 * kk, db, idesc_bf16(BN), 1u);                     // hi x hi
+                            } else {
+                                mma_bf16_ts(dacc, ta + 8 * kk, db, idesc_bf16(BN), first);
+                            }
+                        }
+                    } else {
     #pragma unroll
                     for (int kk = 0; kk < BK / 8; ++kk) {
                         // K = 8 TF32 per MMA: 32 bytes along a 128-byte swizzle row, 8 TMEM columns
@@ -295,6 +348,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                             mma_hi(db_hi, first, idesc);
                         }
                     }
+                    }
                     mma_commit(smem_u32(&empty[s]));
                     if (cend) mma_commit(smem_u32(&chunk_full[b]));
                     ++p;
@@ -315,6 +369,28 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                 const int s = i % STAGES;
                 if (!mbar_wait(smem_u32(&full[s]), (i / STAGES) & 1, err, abort_flag)) break;
                 const uint32_t taddr = lane_base + a_col(s);
+                if (BF) {
+                    // row r's 64 FP32 values -> 32 columns of BF16 hi pairs (and 32 of lo pairs)
+#pragma unroll
+                    for (int g = 0; g < 2; ++g) {  // one 128 x 32 box each
+                        uint32_t wh[16], wl[16];
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) {
+                            float v[16];
+                            load_a_half<0>(stage_a(s) + g * A_TILE_BYTES, r, h, v);
+#pragma unroll
+                            for (int k = 0; k < 8; ++k) {
+                                const __nv_bfloat162 hi = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
+                                const float2 hf = __bfloat1622float2(hi);
+                                const __nv_bfloat162 lo = __floats2bfloat162_rn(v[2 * k] - hf.x, v[2 * k + 1] - hf.y);
+                                wh[8 * h + k] = *reinterpret_cast<const uint32_t *>(&hi);
+                                wl[8 * h + k] = *reinterpret_cast<const uint32_t *>(&lo);
+                            }
+                        }
+                        tmem_st16(taddr + 16 * g, wh);
+                        if (CF::LO_TMEM) tmem_st16(taddr + CF::LO_OFF + 16 * g, wl);
+                    }
+                } else {
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     float v[16];
@@ -330,6 +406,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                         for (int k = 0; k < 16; ++k) w[k] = __float_as_uint(v[k] - tf32_hi(v[k]));
                         tmem_st16(taddr + CF::LO_OFF + 16 * h, w);
                     }
+                }
                 }
                 asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 tc_fence_before();
@@ -350,7 +427,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
         int u = u_b, t = t_b, kb = kb_b, c = 0;
         bool fresh = true;  // next chunk starts a segment
         while (u < u_e) {
-            const int len = min(CHUNK_KB, min(nkb - kb, u_e - u));
+            const int len = min(CF::CHUNK, min(nkb - kb, u_e - u));
             const int b = CF::NACC == 2 ? (c & 1) : 0;
             const uint32_t ph = CF::NACC == 2 ? ((c >> 1) & 1) : (c & 1);
             if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&chunk_full[b]), ph, err, abort_flag))) break;
@@ -401,9 +478,11 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                     const int b0 = cta_of(t0), b1 = cta_of(t1 - 1);
                     __threadfence();
                     __syncwarp();
-                    int old = 0;
-                    if (lane == 0) old = atomicAdd(&tile_cnt[4 * t + wq], 1);
-                    old = __shfl_sync(0xffffffffu, old, 0);
+                    int old = -1;  // split-K launch (no counts): a separate kernel adds the pieces
+                    if (tile_cnt) {
+                        if (lane == 0) old = atomicAdd(&tile_cnt[4 * t + wq], 1);
+                        old = __shfl_sync(0xffffffffu, old, 0);
+                    }
                     if (old == b1 - b0) {  // every other piece is written
                         if (lane == 0) tile_cnt[4 * t + wq] = 0;  // ready for the next launch
                         __threadfence();
@@ -428,6 +507,8 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                         const float *ci = Cin + m * si + (int64_t)n0 * sj;
                         // C's lo part (x - hi(x)) beside C when a later product takes C as its B
                         float *cl = Clo ? Clo + m * sm + (int64_t)n0 * sn : nullptr;
+                        // and its BF16 parts (hi, then lo bfhalf elements later) for a later BF16-split product
+                        __nv_bfloat16 *cb = Cbf ? Cbf + m + (int64_t)n0 * ldbf : nullptr;
 #pragma unroll
                         for (int j = 0; j < BN; ++j) {
                             if (n0 + j < N) {
@@ -435,6 +516,11 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                                 if (beta != 0.f) o = fmaf(beta, *ci, o);
                                 *cp = o;
                                 if (cl) cl[j * sn] = o - tf32_hi(o);
+                                if (cb) {
+                                    const __nv_bfloat16 hb = __float2bfloat16_rn(o);
+                                    cb[j * ldbf] = hb;
+                                    cb[bfhalf + j * ldbf] = __float2bfloat16_rn(o - __bfloat162float(hb));
+                                }
                             }
                             cp += sn;
                             ci += sj;
@@ -456,6 +542,21 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                      "r"((uint32_t)CF::TMEM_COLS)
                      : "memory");
     }
+}
+
+// Split-K sum: C (M x N, M, N <= one tile) = alpha sum_b part[b] in CTA order b = 0, 1, ..,
+// each piece a BM x BN tile (element (m, n) at m + n BM).
+__global__ void k_splitk_sum(const float *part, int nparts, int tile, int M, int N, float alpha, float *C, int64_t ldc,
+                             const int *status)
+{
+    if (status_bad(status)) return;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= tile) return;
+    const int m = e % BM, n = e / BM;
+    if (m >= M || n >= N) return;
+    float acc = 0.f;
+    for (int b = 0; b < nparts; ++b) acc += __ldcg(part + (size_t)b * tile + e);
+    C[m + (int64_t)n * ldc] = alpha * acc;
 }
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
@@ -570,35 +671,37 @@ int tc_plan_error(tc_plan *p, cudaStream_t st)
     return e;
 }
 
-template <int BN, int TERMS, int AMN>
+template <int BN, int TERMS, int AMN, int BF = 0>
 static int launch_bn(tc_plan *p, cudaStream_t st, const CUtensorMap &ma, const CUtensorMap &mb,
                      const CUtensorMap &mblo, int M, int N, int K,
                      float alpha, float beta, const float *Cin, int64_t ldcin, float *C, float *Clo, int64_t ldc,
-                     const int *status, int *err, int reserve, int ctrans)
+                     const int *status, int *err, int reserve, int ctrans, void *Cbf = nullptr, int64_t ldbf = 0,
+                     long long bfhalf = 0, int splitk = 0)
 {
-    using CF = Cfg<BN, TERMS, AMN>;
+    using CF = Cfg<BN, TERMS, AMN, BF>;
     static bool attr = false;
     if (!attr) {
-        if (cudaFuncSetAttribute(k_tc_gemm<BN, TERMS, AMN>, cudaFuncAttributeMaxDynamicSharedMemorySize, CF::SMEM) !=
-            cudaSuccess)
+        if (cudaFuncSetAttribute(k_tc_gemm<BN, TERMS, AMN, BF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 CF::SMEM) != cudaSuccess)
             return -1;
         // the register split raises warps 8-11 out of what the CTA holds: refuse a
         // build whose launch count leaves too few (setmaxnreg.inc would never return)
         cudaFuncAttributes fa;
-        if (cudaFuncGetAttributes(&fa, k_tc_gemm<BN, TERMS, AMN>) != cudaSuccess ||
+        if (cudaFuncGetAttributes(&fa, k_tc_gemm<BN, TERMS, AMN, BF>) != cudaSuccess ||
             384 * fa.numRegs < 128 * (2 * GEMM_REG_LOW + GEMM_REG_DRAIN))
             return -1;
         attr = true;
     }
     const int mt = (M + BM - 1) / BM, nt = (N + BN - 1) / BN;
-    const int nkb = (K + BK - 1) / BK;
+    const int nkb = (K + CF::BKE - 1) / CF::BKE;
     const int tiles = mt * nt;
     const long long U = (long long)tiles * nkb;
     // stream-K when the tiles alone leave SMs idle and each SM still gets a few
     // k-blocks; `reserve` SMs are left free for work on other streams
     const int sms = std::max(1, g_num_sms - std::max(0, reserve));
-    const bool streamk = tiles < sms && U >= 4LL * sms && nkb >= 4 * CHUNK_KB;  // short K: one tile per CTA
-    const int G = streamk ? sms : tiles;
+    // split-K (one output tile, splitk CTAs): every CTA writes its piece and k_splitk_sum adds them
+    const bool streamk = splitk > 0 || (tiles < sms && U >= 4LL * sms && nkb >= 4 * CF::CHUNK);  // short K: one tile per CTA
+    const int G = splitk > 0 ? (int)std::min<long long>(splitk, U) : streamk ? sms : tiles;
     int maxseg = 1;
     float *part = nullptr;
     if (streamk) {
@@ -625,8 +728,13 @@ static int launch_bn(tc_plan *p, cudaStream_t st, const CUtensorMap &ma, const C
         }
     }
     rb_count_launch();
-    k_tc_gemm<BN, TERMS, AMN><<<G, 384, CF::SMEM, st>>>(ma, mb, mblo, M, N, mt, nkb, U, maxseg, alpha, beta, Cin,
-                                                        ldcin, C, Clo, ldc, ctrans, part, p->cnt, status, err);
+    k_tc_gemm<BN, TERMS, AMN, BF><<<G, 384, CF::SMEM, st>>>(ma, mb, mblo, M, N, mt, nkb, U, maxseg, alpha, beta, Cin,
+                                                        ldcin, C, Clo, ldc, ctrans, part, splitk > 0 ? nullptr : p->cnt,
+                                                        status, err, (__nv_bfloat16 *)Cbf, ldbf, bfhalf);
+    if (splitk > 0) {
+        rb_count_launch();
+        k_splitk_sum<<<(BM * BN + 255) / 256, 256, 0, st>>>(part, G, BM * BN, M, N, alpha, C, ldc, status);
+    }
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
@@ -634,7 +742,7 @@ template <int TERMS>
 static int launch_terms(tc_plan *p, cudaStream_t st, int a_layout, int M, int N, int K, float alpha, const float *A,
                         int64_t lda, const float *B, const float *Blo, int64_t ldb, float beta, const float *Cin,
                         int64_t ldcin, float *C, float *Clo, int64_t ldc, const int *status, int *err, int reserve,
-                        int ctrans)
+                        int ctrans, int splitk = 0)
 {
     const int a_mn = (a_layout == TC_A_MN);
     const int bn = N <= 32 ? 32 : N <= 64 ? 64 : 128;
@@ -664,9 +772,9 @@ static int launch_terms(tc_plan *p, cudaStream_t st, int a_layout, int M, int N,
 #define RB_TC_CASE(BNV)                                                                                     \
     case BNV:                                                                                                  \
         return a_mn ? launch_bn<BNV, TERMS, 1>(p, st, ma, mb, mblo, M, N, K, alpha, beta, Cin, ldcin, C, Clo, ldc, \
-                                               status, err, reserve, ctrans)                                    \
+                                               status, err, reserve, ctrans, nullptr, 0, 0, splitk)             \
                     : launch_bn<BNV, TERMS, 0>(p, st, ma, mb, mblo, M, N, K, alpha, beta, Cin, ldcin, C, Clo, ldc, \
-                                               status, err, reserve, ctrans);
+                                               status, err, reserve, ctrans, nullptr, 0, 0, splitk);
     switch (bn) {
         RB_TC_CASE(32)
         RB_TC_CASE(64)
@@ -752,4 +860,112 @@ int tc_gemm_nk_lo(tc_plan *p, cudaStream_t st, int terms, int a_layout, int M, i
 {
     return tc_run(p, st, terms, a_layout, M, N, K, 1.f, A, lda, B, ldb, 0.f, nullptr, 0, C, ldc, status, reserve_sms,
                   0, Blo, Clo);
+}
+
+// ---------------------------------------------------------------------------
+// BF16-split products (kind::f16).
+// ---------------------------------------------------------------------------
+namespace {
+
+// hi = bf16(x), lo = bf16(x - hi) (round to nearest) of a column-major rows x cols panel
+__global__ void k_split_bf16(int rows, int cols, const float *X, int64_t ldx, __nv_bfloat16 *H, __nv_bfloat16 *L,
+                             int64_t ldo)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y;
+    if (i < rows) {
+        const float v = X[i + (int64_t)j * ldx];
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        H[i + (int64_t)j * ldo] = h;
+        if (L) L[i + (int64_t)j * ldo] = __float2bfloat16_rn(v - __bfloat162float(h));
+    }
+}
+
+// 2-D BF16 tensor map: inner extent `inner` (contiguous), row pitch ld elements;
+// box {64, box_rows} (one 128-byte swizzle row); out-of-range elements read as zero.
+bool make_map_bf16(CUtensorMap *map, const void *ptr, int inner, int outer, int64_t ld, int box_rows)
+{
+    cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    cuuint32_t box[2] = {64, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+}  // namespace
+
+void tc_split_bf16(cudaStream_t st, int rows, int cols, const float *X, int64_t ldx, void *Xh, void *Xl, int64_t ldo)
+{
+    if (rows <= 0 || cols <= 0) return;
+    rb_count_launch();
+    k_split_bf16<<<dim3((rows + 255) / 256, cols), 256, 0, st>>>(rows, cols, X, ldx, (__nv_bfloat16 *)Xh,
+                                                                   (__nv_bfloat16 *)Xl, ldo);
+}
+
+int tc_gemm_bf(tc_plan *p, cudaStream_t st, int terms, int M, int N, int K, const float *A, int64_t lda,
+               const void *Bh, const void *Bl, int64_t ldb, float *C, float *Clo, int64_t ldc, const int *status,
+               int reserve_sms, void *Cbf, int64_t ldcbf)
+{
+    if (M <= 0 || N <= 0) return 0;
+    if (!p || K <= 0 || (terms != 1 && terms != 3) || (terms == 3 && !Bl)) return -1;
+    if (!tma_ok(A, lda) || (uintptr_t)Bh % 16 || (Bl && (uintptr_t)Bl % 16) || ldb % 8) return -6;
+    if (Clo && terms == 1) return -7;
+    const int bn = N <= 32 ? 32 : N <= 64 ? 64 : 128;
+    CUtensorMap ma, mb, mblo;
+    bool ok = get_encoder() && make_map(&ma, A, K, M, lda, BM) && make_map_bf16(&mb, Bh, K, N, ldb, bn);
+    mblo = mb;
+    if (terms == 3) ok = ok && make_map_bf16(&mblo, Bl, K, N, ldb, bn);
+    if (!ok) return -4;
+    int *err = status ? const_cast<int *>(status) : p->err;
+#define RB_BF_CASE(BNV)                                                                                          \
+    case BNV:                                                                                                       \
+        return terms == 3 ? launch_bn<BNV, 3, 0, 1>(p, st, ma, mb, mblo, M, N, K, 1.f, 0.f, nullptr, 0, C, Clo, ldc, \
+                                                    status, err, reserve_sms, 0, Cbf, ldcbf,                       \
+                                                    (long long)ldcbf * N)                                          \
+                          : launch_bn<BNV, 1, 0, 1>(p, st, ma, mb, mblo, M, N, K, 1.f, 0.f, nullptr, 0, C, nullptr,  \
+                                                    ldc, status, err, reserve_sms, 0, Cbf, ldcbf,                  \
+                                                    (long long)ldcbf * N);
+    switch (bn) {
+        RB_BF_CASE(32)
+        RB_BF_CASE(64)
+        RB_BF_CASE(128)
+    default: return -5;
+    }
+#undef RB_BF_CASE
+}
+
+int tc_gemm_splitk(tc_plan *p, cudaStream_t st, int terms, int a_layout, int M, int N, int K, const float *A,
+                   int64_t lda, const float *B, const float *Blo, int64_t ldb, float *C, int64_t ldc, const int *status,
+                   int nctas)
+{
+    if (M <= 0 || N <= 0) return 0;
+    if (!p || K <= 0 || M > BM || N > 128 || nctas < 1 || !tma_ok(A, lda) || !tma_ok(B, ldb) ||
+        (Blo && !tma_ok(Blo, ldb)) || (terms == 3 && !Blo))
+        return -6;
+    int *err = status ? const_cast<int *>(status) : p->err;
+    CUtensorMap ma, mb, mblo;
+    const int bn = N <= 32 ? 32 : N <= 64 ? 64 : 128;
+    const int a_mn = (a_layout == TC_A_MN);
+    bool ok = get_encoder() && (a_mn ? make_map(&ma, A, M, K, lda, 32) : make_map(&ma, A, K, M, lda, BM)) &&
+              make_map(&mb, B, K, N, ldb, bn);
+    mblo = mb;
+    if (terms == 3) ok = ok && make_map(&mblo, Blo, K, N, ldb, bn);
+    if (!ok) return -4;
+#define RB_SK_CASE(BNV, TT)                                                                                          \
+    if (bn == BNV && terms == TT)                                                                                       \
+        return a_mn ? launch_bn<BNV, TT, 1>(p, st, ma, mb, mblo, M, N, K, 1.f, 0.f, nullptr, 0, C, nullptr, ldc, status, \
+                                            err, 0, 0, nullptr, 0, 0, nctas)                                            \
+                    : launch_bn<BNV, TT, 0>(p, st, ma, mb, mblo, M, N, K, 1.f, 0.f, nullptr, 0, C, nullptr, ldc, status, \
+                                            err, 0, 0, nullptr, 0, 0, nctas);
+    RB_SK_CASE(128, 1)
+    RB_SK_CASE(128, 3)
+    RB_SK_CASE(64, 1)
+    RB_SK_CASE(64, 3)
+    RB_SK_CASE(32, 1)
+    RB_SK_CASE(32, 3)
+#undef RB_SK_CASE
+    return -5;
 }

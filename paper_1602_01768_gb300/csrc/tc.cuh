@@ -45,6 +45,28 @@ int tc_gemm_nk_lo(tc_plan *p, cudaStream_t st, int terms, int a_layout, int M, i
 int tc_gemm_nk_axpby(tc_plan *p, cudaStream_t st, int terms, int a_layout, int M, int N, int K, float alpha,
                      const float *A, int64_t lda, const float *B, int64_t ldb, float beta, const float *Cin,
                      int64_t ldcin, float *C, int64_t ldc);
+// BF16-split products (kind::f16): C = op(A) B with op(A) K-contiguous FP32
+// (element (m, k) at A[k + m lda]) and B given as its BF16 parts Bh (hi) and Bl
+// (lo, needed for terms = 3), K x N, K contiguous, ld ldb (a multiple of 8),
+// 16-byte aligned.  terms = 1: hi(A) hi(B); terms = 3: hi hi + hi lo + lo hi
+// (~16 significant bits).  FP32 accumulation restarted every 512 of K.  Clo
+// (terms = 3, may be null): C's TF32 lo part beside C, as tc_gemm_nk_lo writes
+// it.  Returns 0 when launched, < 0 when the shape or alignment is outside the
+// kernel.  Cbf (may be null): C's own BF16 parts written beside C, hi at
+// Cbf[m + n ldcbf] and lo ldcbf N elements later (ldcbf a multiple of 8), for a
+// later BF16-split product that takes C as its B.
+int tc_gemm_bf(tc_plan *p, cudaStream_t st, int terms, int M, int N, int K, const float *A, int64_t lda,
+               const void *Bh, const void *Bl, int64_t ldb, float *C, float *Clo, int64_t ldc, const int *status,
+               int reserve_sms = 0, void *Cbf = nullptr, int64_t ldcbf = 0);
+// One-tile products (M <= 128, N <= 128) split over K on nctas CTAs: each CTA
+// writes its partial tile and a second kernel adds them in CTA order (every SM
+// takes part in the sum; no CTA waits for the others).  terms 1 or 3 (3 needs
+// Blo, B's lo part).  Returns 0 when launched, < 0 when outside the kernel.
+int tc_gemm_splitk(tc_plan *p, cudaStream_t st, int terms, int a_layout, int M, int N, int K, const float *A,
+                   int64_t lda, const float *B, const float *Blo, int64_t ldb, float *C, int64_t ldc, const int *status,
+                   int nctas);
+// Xh = bf16(X), Xl = bf16(X - Xh) (Xl may be null), column-major rows x cols, ld ldo.
+void tc_split_bf16(cudaStream_t st, int rows, int cols, const float *X, int64_t ldx, void *Xh, void *Xl, int64_t ldo);
 // L += S^ V with S^ given row-major (element (i, c) at ShT[c + i q]) and V
 // q x n column-major (ld q).
 int tc_update(tc_plan *p, cudaStream_t st, int terms, int n, int q, const float *ShT, const float *V, float *L,
@@ -74,6 +96,10 @@ int tc_update_persistent(tc_plan *p, cudaStream_t st, int n, int q, const float 
 // outside the kernel (q > 128, q or n not a multiple of 4, unaligned
 // pointers), < 0 on error.
 size_t tc_update_s_workspace(int n, int q);
+// S_bf (may be null): S_out's BF16 parts, hi at S_bf[i + j ld_bf] and lo ld_bf q
+// elements later, for the BF16-split product that takes S as its B.  reserve_sms
+// (at most 8) SMs are left free for work on other streams.
 int tc_update_next_s(cudaStream_t st, int n, int q, const float *ShT, const float *V, float *L, int64_t ldl,
                      const float *St_next, float *S_out, int do_update, float *Spart, size_t spart_elems,
-                     const int *status, float *S_lo = nullptr);
+                     const int *status, float *S_lo = nullptr, void *S_bf = nullptr, int64_t ld_bf = 0,
+                     int reserve_sms = 0);

@@ -35,6 +35,8 @@
 // L+ lo [320, 384), S_next accumulator [384, 512).
 // All mbarrier waits are bounded; a wait that gives up records ST_TIMEOUT and
 // the CTA winds down.
+#include <cuda_bf16.h>
+
 #include <algorithm>
 
 #include "tc.cuh"
@@ -94,7 +96,7 @@ k_tc_update_s(const float *__restrict__ ShT, int n, int q, const __grid_constant
               const __grid_constant__ CUtensorMap tmL, const __grid_constant__ CUtensorMap tmLo,
               const __grid_constant__ CUtensorMap tmT, int ncb, int ntiles,
               int do_update, float *Spart, int *rb_cnt, int maxseg, float *S, float *Slo, int64_t lds,
-              const int *status, int *err)
+              const int *status, int *err, __nv_bfloat16 *Sbf, int64_t ldbf)
 {
     using CF = SCfg<KC>;
     constexpr int NQ = CF::NQ;
@@ -483,6 +485,12 @@ k_tc_update_s(const float *__restrict__ ShT, int n, int q, const __grid_constant
                                 if (j < q) {
                                     S[row + (int64_t)j * lds] = run[j];
                                     if (Slo) Slo[row + (int64_t)j * lds] = run[j] - hi_tf32(run[j]);  // for a 3-term product
+                                    if (Sbf) {  // BF16 hi and lo, for a BF16-split product
+                                        const __nv_bfloat16 hb = __float2bfloat16_rn(run[j]);
+                                        Sbf[row + (int64_t)j * ldbf] = hb;
+                                        Sbf[(int64_t)q * ldbf + row + (int64_t)j * ldbf] =
+                                            __float2bfloat16_rn(run[j] - __bfloat162float(hb));
+                                    }
                                 }
                     }
                 }
@@ -502,7 +510,7 @@ template <int KC>
 int launch_update_s(cudaStream_t st, const float *ShT, int n, int q, const CUtensorMap &mv, const CUtensorMap &ml,
                     const CUtensorMap &mlo,
                     const CUtensorMap &mt, int do_update, float *Spart, size_t spart_elems, float *S, float *Slo,
-                    int64_t lds, const int *status, int *err)
+                    int64_t lds, const int *status, int *err, void *Sbf, int64_t ldbf, int reserve_sms)
 {
     using CF = SCfg<KC>;
     static bool attr = false;
@@ -520,7 +528,8 @@ int launch_update_s(cudaStream_t st, const float *ShT, int n, int q, const CUten
     }
     const int nrb = (n + 127) / 128, ncb = (n + UBN - 1) / UBN;
     const int ntiles = nrb * ncb;
-    const int grid = std::min(ntiles, tc_num_sms());
+    // reserve_sms SMs stay free for work on other streams
+    const int grid = std::min(ntiles, std::max(1, tc_num_sms() - std::max(0, std::min(reserve_sms, 8))));
     int maxseg = 1;
     for (int b = 0; b < grid; ++b) {
         const long long t0 = (long long)ntiles * b / grid, t1 = (long long)ntiles * (b + 1) / grid;
@@ -532,7 +541,7 @@ int launch_update_s(cudaStream_t st, const float *ShT, int n, int q, const CUten
     rb_count_launch();
     k_tc_update_s<KC><<<grid, 384, CF::SMEM, st>>>(ShT, n, q, mv, ml, mlo, mt, ncb, ntiles, do_update,
                                                    Spart + cnt_floats, (int *)Spart, maxseg, S, Slo, lds, status,
-                                                   err);
+                                                   err, (__nv_bfloat16 *)Sbf, ldbf);
     return cudaGetLastError() == cudaSuccess ? 0 : -3;
 }
 
@@ -540,19 +549,28 @@ int launch_update_s(cudaStream_t st, const float *ShT, int n, int q, const CUten
 
 size_t tc_update_s_workspace(int n, int q)
 {
-    // upper bound: every CTA touches at most (its tiles / tiles per row block) + 2 row blocks
+    // the partial blocks of every grid a launch may use (all SMs but 0 .. 8 reserved): the
+    // largest CTAs x (row blocks a CTA's tile run meets)
     const int nrb = (n + 127) / 128, ncb = (n + UBN - 1) / UBN, ntiles = nrb * ncb;
-    const int grid = std::min(ntiles, tc_num_sms());
-    const int per = (ntiles + grid - 1) / grid;
-    const int maxseg = per / ncb + 2;
+    size_t blocks = 0;
+    for (int r = 0; r <= 8; ++r) {
+        const int grid = std::min(ntiles, std::max(1, tc_num_sms() - r));
+        int maxseg = 1;
+        for (int b = 0; b < grid; ++b) {
+            const long long t0 = (long long)ntiles * b / grid, t1 = (long long)ntiles * (b + 1) / grid;
+            if (t1 > t0) maxseg = std::max(maxseg, (int)((t1 - 1) / ncb - t0 / ncb + 1));
+        }
+        blocks = std::max(blocks, (size_t)grid * maxseg);
+    }
     const size_t cnt_floats = ((size_t)4 * nrb + 31) / 32 * 32;  // arrival counts (as int)
-    return cnt_floats + (size_t)grid * maxseg * 128 * (size_t)(((q + 31) / 32) * 32);
+    return cnt_floats + blocks * 128 * (size_t)(((q + 31) / 32) * 32);
 }
 
 int tc_update_next_s(cudaStream_t st, int n, int q, const float *ShT, const float *V, float *L, int64_t ldl,
                      const float *St_next, float *S_out, int do_update, float *Spart, size_t spart_elems,
-                     const int *status, float *S_lo)
+                     const int *status, float *S_lo, void *S_bf, int64_t ld_bf, int reserve_sms)
 {
+    if (S_bf && (ld_bf < n || ld_bf % 8)) return 1;
     if (q < 1 || q > 128 || (q % 4) || (ldl % 4) || (n % 4) || ((uintptr_t)ShT % 16) || ((uintptr_t)V % 16) ||
         ((uintptr_t)L % 16) || ((uintptr_t)St_next % 16) || ((uintptr_t)S_lo % 16))
         return 1;
@@ -564,10 +582,10 @@ int tc_update_next_s(cudaStream_t st, int n, int q, const float *ShT, const floa
         return -4;
     int *err = const_cast<int *>(status);
     switch (nq / 32) {
-    case 1: return launch_update_s<1>(st, ShT, n, q, mv, ml, mlo, mt, do_update, Spart, spart_elems, S_out, S_lo, n, status, err);
-    case 2: return launch_update_s<2>(st, ShT, n, q, mv, ml, mlo, mt, do_update, Spart, spart_elems, S_out, S_lo, n, status, err);
-    case 3: return launch_update_s<3>(st, ShT, n, q, mv, ml, mlo, mt, do_update, Spart, spart_elems, S_out, S_lo, n, status, err);
+    case 1: return launch_update_s<1>(st, ShT, n, q, mv, ml, mlo, mt, do_update, Spart, spart_elems, S_out, S_lo, n, status, err, S_bf, ld_bf, reserve_sms);
+    case 2: return launch_update_s<2>(st, ShT, n, q, mv, ml, mlo, mt, do_update, Spart, spart_elems, S_out, S_lo, n, status, err, S_bf, ld_bf, reserve_sms);
+    case 3: return launch_update_s<3>(st, ShT, n, q, mv, ml, mlo, mt, do_update, Spart, spart_elems, S_out, S_lo, n, status, err, S_bf, ld_bf, reserve_sms);
     default:
-        return launch_update_s<4>(st, ShT, n, q, mv, ml, mlo, mt, do_update, Spart, spart_elems, S_out, S_lo, n, status, err);
+        return launch_update_s<4>(st, ShT, n, q, mv, ml, mlo, mt, do_update, Spart, spart_elems, S_out, S_lo, n, status, err, S_bf, ld_bf, reserve_sms);
     }
 }

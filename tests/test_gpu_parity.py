@@ -420,6 +420,84 @@ def test_rbfgs_fp32_parity(sketch, kind, q):
 
 
 # --------------------------------------------------------------------------
+# BF16-split forms: G = A S and W^T = L^T G as kind::f16 products
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("n,q", [(768, 64), (4100, 128)])
+def test_adarbfgs_bf16x3_one_step_from_general_L(n, q):
+    # 3-term BF16 splits carry ~2^-16 relative error per product (x = hi + lo to 2^-17, the
+    # dropped lo lo term 2^-16); the rank-q correction is single-pass TF32 as in the mixed form,
+    # so the step's change is within 3e-3 of the oracle's.  At n = 4100 the BF16 GEMMs run
+    # stream-K (65 k-blocks of 64 per tile) with ragged M and K.
+    A = wl.c2_matrix(n=n).astype(np.float32).astype(np.float64)
+    rng = np.random.default_rng(9)
+    L0 = (np.eye(n) + 0.05 * rng.standard_normal((n, n))).astype(np.float32).astype(np.float64)
+    h = _handle(A, B.RB_METHOD_ADARBFGS, B.RB_SKETCH_GAUSS, q, B.RB_BF16X3, seed=21)
+    try:
+        Ld = to_dev(L0, torch_dtype(B.RB_BF16X3))
+        B.rbfgs_import(h, B.RB_WHAT_L, Ld.data_ptr(), n)
+        B.rbfgs_set_step(h, 2)
+        B.adarbfgs_step(h, 2)
+        _, L2 = orc.adarbfgs_run(A, L0, q, orc.SKETCH_GAUSS, 21, 0, 2, 2)
+        Lg = export(h, n, B.RB_BF16X3, B.RB_WHAT_L)
+        corr = rel(Lg - L0, L2 - L0)
+        assert corr <= 3e-3, corr
+    finally:
+        B.rbfgs_destroy(h)
+
+
+def test_adarbfgs_bf16x3_reaches_tolerance_like_oracle():
+    # the n x n sparse ridge-Hessian recipe of the n = 16384 workload at n = 1024 (kappa ~ 10):
+    # the BF16x3 form reaches tol 1e-4 and its factor, evaluated exactly in FP64, is within
+    # 0.1 tol of the oracle's after the same number of steps
+    n, q, tol = 1024, 32, 1e-4
+    A = wl.c3_matrix(n=n).astype(np.float32).astype(np.float64)
+    h = _handle(A, B.RB_METHOD_ADARBFGS, B.RB_SKETCH_GAUSS, q, B.RB_BF16X3, seed=22)
+    try:
+        st, iters, r = B.rbfgs_solve(h, tol, 5000, 16, 256, 0)
+        assert st == B.RB_OK and r <= tol
+        _, L = orc.adarbfgs_run(A, np.eye(n), q, orc.SKETCH_GAUSS, 22, 0, 0, iters)
+        r_orc = orc.residual_factored(A, L)
+        r_gpu = orc.residual_factored(A, export(h, n, B.RB_BF16X3, B.RB_WHAT_L))
+        assert abs(r_gpu - r_orc) <= 0.1 * tol, (r_gpu, r_orc, iters)
+        assert r_gpu <= 1.1 * tol
+    finally:
+        B.rbfgs_destroy(h)
+
+
+def test_adarbfgs_bf16_single_pass_parity():
+    # RB_BF16: G and W^T in one BF16 pass (unit roundoff 2^-8 per operand), the rest single-pass
+    # TF32.  Bar: relative Frobenius error of L <= 1e-1 after 10 and 30 steps, the exact residual
+    # within 2e-1 relative of the oracle's.
+    n, q = 512, 32
+    A = wl.c2_matrix(n=n).astype(np.float32).astype(np.float64)
+    h = _handle(A, B.RB_METHOD_ADARBFGS, B.RB_SKETCH_GAUSS, q, B.RB_BF16, seed=23)
+    try:
+        L = np.eye(n)
+        done = 0
+        for chk in (10, 30):
+            B.adarbfgs_step(h, chk - done)
+            _, L = orc.adarbfgs_run(A, L, q, orc.SKETCH_GAUSS, 23, 0, done, chk - done)
+            done = chk
+            Lg = export(h, n, B.RB_BF16, B.RB_WHAT_L)
+            assert rel(Lg, L) <= 1e-1, (chk, rel(Lg, L))
+        r_orc = orc.residual_factored(A, L)
+        assert abs(orc.residual_factored(A, Lg) - r_orc) <= 2e-1 * r_orc
+    finally:
+        B.rbfgs_destroy(h)
+
+
+def test_bf16_forms_rejected_where_not_built():
+    A = to_dev(np.eye(64), torch_dtype(B.RB_BF16X3))
+    for method in (B.RB_METHOD_RBFGS, B.RB_METHOD_AIP):
+        with pytest.raises(B.RbfgsError) as e:
+            B.rbfgs_init(64, A.data_ptr(), 64, False, B.make_opts(method=method, q=8, prec=B.RB_BF16X3), 0)
+        assert e.value.status == B.RB_EUNSUPPORTED
+    with pytest.raises(B.RbfgsError) as e:
+        B.newton_schulz_init(64, A.data_ptr(), 64, False, B.RB_BF16X3, 0, 1.0, 0)
+    assert e.value.status == B.RB_EUNSUPPORTED
+
+
+# --------------------------------------------------------------------------
 # Comparison methods
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("prec,tol", [(B.RB_FP64, 1e-10), (B.RB_FP32, 1e-4), (B.RB_TF32X3, 1e-4)])
