@@ -4,14 +4,19 @@ One bench "step" is one complete AdaRBFGS solve (Algorithm 4) of the
 n = 16384 SPD matrix A = M^T M / m + 1e-4 I (M 65536 x 16384, 1 % dense
 N(0,1)) from L0 = I with a Gaussian sketch of q = 128 columns, run until the
 residual ||I - L L^T A||_F / sqrt(n) <= 1e-4 (sampled every 32 steps on 256
-columns, confirmed on 1024 columns).  Each step uses a fresh sketch seed.
+columns, confirmed on 1024 columns).  Each step uses a fresh sketch seed.  The
+default form is the mixed-precision BF16x3 one: the two n x n-streaming GEMMs
+as 3-term BF16 splits, the other products 3xTF32, the rank-q correction 1xTF32.
 
 Reported: solves/s (whole job), time to tolerance per solve, the roofline of
-the dominant kernel (the rank-q update L += S^ V, an HBM-bound pass reading
-and writing L) measured live with CUDA events on the library's stream, the
-plain-FP32 form's time to the same tolerance, an end-to-end number through
-the host-buffer entry points, and the FP64 CPU oracle timed on a bounded
-sample on the host cores.
+the dominant kernel (the fused rank-q update L += S^ V and next S = L S~, an
+HBM-bound pass reading and writing L) and of the n x n GEMMs, measured live with
+CUDA events on the library's stream; the 3xTF32 mixed form, the FP64 q x q core
+and the plain FP32 form's times to the same tolerance; the factor of one timed
+solve checked by the FP64 oracle on 256 sampled columns; an end-to-end number
+through the host-buffer entry points; and the FP64 CPU oracle timed on a
+bounded sample on the host cores (all cores, and one core on the n = 4096
+workload).
 
 --impl reference times the FP64 CPU oracle (the only reference that exists:
 the paper ships no code) on the same workload.
@@ -43,6 +48,10 @@ FUSED_TRAFFIC_N8192_Q128 = 293947136 + 231262464
 # (mean over its timed solves); the reference arm, which cannot run a whole solve in the time
 # allowed, times a bounded sample of oracle steps and scales it by this count.
 STEPS_PER_SOLVE_MEASURED = 2016
+# arithmetic of each form: storage / products
+DTYPE = {"bf16x3": "f32 storage, bf16x3 + tf32x3 products", "bf16": "f32 storage, bf16 + tf32 products",
+         "mixed": "f32 storage, tf32x3 + tf32 products", "tf32x3": "f32 storage, tf32x3 products",
+         "tf32": "f32 storage, tf32 products", "fp32": "f32", "fp64": "f64"}
 # rb_opts.core_fp64: 0 = the precision form's own choice, 1 = FP64 q x q core, -1 = FP32 core
 CORE_OPT = {"default": 0, "fp64": 1, "fp32": -1}
 
@@ -53,13 +62,16 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--prec", default="mixed")
+    ap.add_argument("--prec", default="bf16x3")
     ap.add_argument("--core", choices=["default", "fp64", "fp32"], default="default",
                     help="precision of the q x q Cholesky core (default: the form's own)")
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--q", type=int, default=Q_DEFAULT)
     ap.add_argument("--tol", type=float, default=TOL_DEFAULT)
     ap.add_argument("--no-fp32", action="store_true", help="skip the plain FP32 comparison solve")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the other-form solves (3xTF32 mixed, FP64 q x q core)")
+    ap.add_argument("--no-fp64-check", action="store_true", help="skip the FP64 oracle check of a timed solve")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0, help="budget of the oracle sample")
@@ -99,6 +111,15 @@ def load_tf32_sustained_peak():
         return float(p["bf16_tflops_sustained"]) * TF32_PER_BF16, "measured sustained BF16 x 1.1/2.25"
     except Exception:
         return 1700.0 * TF32_PER_BF16, "fallback sustained BF16 x 1.1/2.25"
+
+
+def load_bf16_sustained_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["bf16_tflops_sustained"]), "measured sustained BF16"
+    except Exception:
+        return 1700.0, "fallback sustained BF16"
 
 
 class ClockSampler:
@@ -223,6 +244,26 @@ def oracle_sample(A_np, q, seed, steps_per_solve, budget_s):
             "sample": (f"{done} FP64 AdaRBFGS step(s) of the n={n}, q={q} workload in {dt:.1f} s "
                        f"({per_step:.2f} s/step), extrapolated to {steps_per_solve} steps per solve"),
             "seconds_per_solve": per_solve, "steps_timed": done}
+
+
+def oracle_core_scaling(wl, n=4096, q=64, steps=2):
+    """The oracle's seconds per AdaRBFGS step on the n = 4096 workload on one host core and on all
+    of them (the n = 16384 step takes about a minute on one core, too long for a bounded sample)."""
+    import numpy as np
+
+    from oracle import oracle as orc
+
+    A = np.asfortranarray(wl.c2_matrix(n=n))
+    out = {"workload": f"AdaRBFGS_gauss n={n} q={q} (A = M^T M/m + 1e-3 I)", "steps": steps}
+    for label, threads in (("one_core", 1), ("all_cores", orc.n_threads())):
+        orc.set_threads(threads)
+        t0 = time.perf_counter()
+        orc.adarbfgs_run(A, np.eye(n), q, orc.SKETCH_GAUSS, 1, 0, 0, steps)
+        out[f"s_per_step_{label}"] = (time.perf_counter() - t0) / steps
+        out[f"threads_{label}"] = threads
+    orc.set_threads(orc.n_threads())
+    out["speedup"] = out["s_per_step_one_core"] / out["s_per_step_all_cores"]
+    return out
 
 
 def run_reference(args):
@@ -501,7 +542,7 @@ def main():
     A = wl.c3_matrix(n=n, device=dev)  # FP32, symmetric: row/column-major identical
     torch.cuda.synchronize()
     opts = B.make_opts(method=B.RB_METHOD_ADARBFGS, sketch=B.RB_SKETCH_GAUSS, q=q, prec=prec, seed=0,
-                       stream_id=rank)
+                       stream_id=rank, core_fp64=CORE_OPT[args.core])
     h = B.rbfgs_init(n, A.data_ptr(), n, False, opts, stream)
 
     def solve(seed):
@@ -563,19 +604,71 @@ def main():
                 "peak_kind": f"{peak_kind} HBM copy", "traffic": traffic,
                 "algorithmic_bytes_per_launch": upd_bytes, "ms_per_launch": upd_ms}
     step_ms = sum(v for k, v in phases.items() if not k.startswith("@"))  # '@' marks: side-stream times
-    # the tcgen05 GEMMs of the step against the TF32 tensor peak: MMA work = terms x 2 n^2 q
+    # the n x n-streaming GEMMs of the step: algorithmic bytes n^2 b (A or L read once) against the
+    # HBM copy peak, and their MMA work (terms x 2 n^2 q) against the tensor peak of their kind
     tf32_peak, tf32_kind = load_tf32_sustained_peak()
+    bf16_peak, bf16_kind = load_bf16_sustained_peak()
+    bf = args.prec in ("bf16x3", "bf16")
+    bterms = 3 if args.prec == "bf16x3" else 1
     gemm_rooflines = []
-    for ph, kern, terms in (("S=LS~", "S = L S~ (k_tc_gemm, 2 x TF32)", 2),
-                            ("G=AS | D core", "G = A S (k_tc_gemm, 3 x TF32, 148 SMs)", 3),
-                            ("W=G^TL | C core", "W^T = L^T G (k_tc_gemm, 3 x TF32, 144 SMs)", 3),
-                            ("update L + next S", "fused update (1 x TF32) + S_next (2 x TF32), k_tc_update_s", 3)):
+    for ph, kern, terms, kind in (
+            ("S=LS~", "S = L S~ (k_tc_gemm, 2 x TF32)", 2, "tf32"),
+            ("G=AS | D core", f"G = A S (k_tc_gemm, {bterms} x BF16)" if bf else "G = A S (k_tc_gemm, 3 x TF32)",
+             bterms if bf else 3, "bf16" if bf else "tf32"),
+            ("W=G^TL | C core", f"W^T = L^T G (k_tc_gemm, {bterms} x BF16, C core beside it)" if bf
+             else "W^T = L^T G (k_tc_gemm, 3 x TF32, C core beside it)", bterms if bf else 3, "bf16" if bf else "tf32"),
+            ("update L + next S", "fused update (1 x TF32) + S_next (2 x TF32), k_tc_update_s", 3, "tf32")):
         if ph in phases:
+            peak_t, kind_t = (bf16_peak, bf16_kind) if kind == "bf16" else (tf32_peak, tf32_kind)
             tflops = terms * 2.0 * n * n * q / (phases[ph] * 1e-3) / 1e12
-            gemm_rooflines.append({"kernel": kern, "bound": "tensor", "achieved": tflops, "peak": tf32_peak,
-                                   "unit": "TFLOP/s", "frac": tflops / tf32_peak, "peak_kind": tf32_kind,
-                                   "hbm_gbs": 4.0 * n * n / (phases[ph] * 1e-3) / 1e9,
-                                   "ms_per_launch": phases[ph]})
+            gbs = 4.0 * n * n / (phases[ph] * 1e-3) / 1e9
+            gemm_rooflines.append({"kernel": kern, "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s",
+                                   "frac": gbs / hbm, "algorithmic_bytes_per_launch": 4 * n * n,
+                                   "tensor_tflops": tflops, "tensor_peak": peak_t, "tensor_frac": tflops / peak_t,
+                                   "tensor_peak_kind": kind_t, "ms_per_launch": phases[ph]})
+
+    # ---- FP64 check of the last timed solve's factor: the oracle on 256 sampled columns ----
+    fp64_check = None
+    if not args.no_fp64_check and rank == 0:
+        from oracle import oracle as orc
+
+        L_host = torch.empty(n, n, dtype=torch.float32)
+        B.rbfgs_reset(h, args.steps - 1, rank)  # the last timed solve again (same seed: same iterates)
+        st_c, it_c, r_c = B.rbfgs_solve(h, tol, MAX_ITER, CHECK_EVERY, CHECK_COLS, CONFIRM_COLS)
+        Ld = torch.empty(n, n, dtype=torch.float32, device=dev)
+        B.rbfgs_export(h, B.RB_WHAT_L, Ld.data_ptr(), n)
+        torch.cuda.synchronize()
+        L_host.copy_(Ld)
+        del Ld
+        A64 = np.asfortranarray(A.double().cpu().numpy())
+        t_c = time.perf_counter()
+        r64 = orc.residual_sampled(A64, 256, 12345, L=L_host.numpy().T.astype(np.float64))
+        fp64_check = {"solve": f"timed solve {args.steps - 1} (seed {args.steps - 1}), repeated", "iters": it_c,
+                      "resid_monitor": r_c, "resid_fp64_oracle_256_cols": r64, "tol": tol,
+                      "passed": bool(r64 <= tol), "oracle_seconds": time.perf_counter() - t_c}
+        del A64, L_host
+
+    # ---- the other precision forms and the FP64 q x q core, same tolerance (one solve each) ----
+    def one_solve(prec_o, core=0):
+        oo = B.make_opts(method=B.RB_METHOD_ADARBFGS, sketch=B.RB_SKETCH_GAUSS, q=q, prec=prec_o, seed=0,
+                         stream_id=rank, core_fp64=core)
+        hh = B.rbfgs_init(n, A.data_ptr(), n, False, oo, stream)
+        B.adarbfgs_step(hh, 2)
+        torch.cuda.synchronize()
+        B.rbfgs_reset(hh, 0, rank)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        st_o, it_o, r_o = B.rbfgs_solve(hh, tol, MAX_ITER, CHECK_EVERY, CHECK_COLS, CONFIRM_COLS)
+        e1.record()
+        torch.cuda.synchronize()
+        B.rbfgs_destroy(hh)
+        return {"time_to_tol_s": e0.elapsed_time(e1) / 1e3, "iters": it_o, "resid": r_o, "converged": st_o == B.RB_OK}
+
+    forms = {}
+    if not args.no_forms:
+        if prec != B.RB_MIXED:
+            forms["mixed_3xtf32"] = one_solve(B.RB_MIXED)
+        forms[f"{args.prec}_fp64_core"] = one_solve(prec, core=1)
 
     # ---- plain FP32 form, same tolerance (one solve) ----
     fp32 = None
@@ -631,12 +724,14 @@ def main():
 
     # ---- CPU oracle on a bounded sample (rank 0, N = 1 only) ----
     cpu = None
+    cpu_scaling = None
     if rank == 0 and world == 1 and not args.no_cpu:
         A_np = np.asfortranarray(A.double().cpu().numpy())
         cpu = oracle_sample(A_np, q, 5, int(round(statistics.mean(iters))), args.cpu_seconds)
         cpu.pop("seconds_per_solve", None)
         cpu.pop("steps_timed", None)
         del A_np
+        cpu_scaling = oracle_core_scaling(wl)
 
     B.rbfgs_destroy(h)
     if rank == 0:
@@ -644,12 +739,14 @@ def main():
         p99 = lat_sorted[min(len(lat_sorted) - 1, int(math.ceil(0.99 * len(lat_sorted))) - 1)]
         out = {"metric": METRIC, "value": solves_per_s, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": t_solve * 1e3, "higher_is_better": True,
-               "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+               "scaling": "weak", "vs_baseline": None, "dtype": DTYPE.get(args.prec, args.prec),
                "data": "synthetic", "config": config(args), "form": args.prec,
                "time_to_tol_s": t_solve, "iters_per_solve": iters, "resid_final": resids,
                "latency_s": {"p50": statistics.median(lat), "p99": p99},
-               "fp32_form": fp32, "roofline": roofline, "gemm_rooflines": gemm_rooflines, "phases_ms": phases, "step_ms": step_ms,
-               "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
+               "core": "fp64" if args.core == "fp64" or prec == B.RB_FP64 else "fp32",
+               "fp32_form": fp32, "forms": forms, "fp64_check": fp64_check,
+               "roofline": roofline, "gemm_rooflines": gemm_rooflines, "phases_ms": phases, "step_ms": step_ms,
+               "cpu_baseline": cpu, "cpu_scaling": cpu_scaling, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,
                "serving": serving, "batched": batched, "comparison": comparison,
                "wall_s": wall}
         print(json.dumps(out), flush=True)

@@ -30,9 +30,13 @@
  *   residuals       exact vs. sampled estimator with all columns; closed forms
  */
 #include <math.h>
+#include <omp.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+
+/* Threads of the OpenMP loops (timing of the oracle on a chosen number of host cores). */
+void orc_set_threads(int threads) { omp_set_num_threads(threads > 0 ? threads : 1); }
 
 /* ------------------------------------------------------------------------- */
 /* Philox4x32-10: Salmon, Moraes, Dror & Shaw, "Parallel random numbers: as   */

@@ -51,6 +51,7 @@ def lib():
             "orc_logf32": (C.c_float, [C.c_float]),
             "orc_sincospif32": (None, [C.c_float, p, p]),
             "orc_round_tf32": (C.c_float, [C.c_float]),
+            "orc_set_threads": (None, [i]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -221,6 +222,11 @@ def residual_sampled(A, m, col_seed, X=None, L=None):
     Xp = _ptr(Xc) if Xc is not None else None
     Lp = _ptr(Lc) if Lc is not None else None
     return lib().orc_residual_sampled(A.shape[0], _ptr(A), Xp, Lp, m, col_seed)
+
+
+def set_threads(threads):
+    """Threads of the oracle's OpenMP loops from now on."""
+    lib().orc_set_threads(int(threads))
 
 
 def n_threads():

@@ -1,6 +1,7 @@
 """The n = 16384, q = 128 workload in the launch configuration the benchmark
-times (mixed form): one step against the FP64 oracle's step, then a solve to
-1e-4 whose factor is checked by the oracle in FP64 on 256 sampled columns."""
+times (the BF16x3 form, and the 3xTF32 mixed form): one step against the FP64
+oracle's step, then a solve to 1e-4 whose factor is checked by the oracle in
+FP64 on 256 sampled columns."""
 import numpy as np
 import pytest
 
@@ -39,9 +40,10 @@ def _L(h):
     return out.cpu().numpy().T.astype(np.float64)  # column-major view
 
 
-def test_first_step_matches_oracle_at_full_size(c3):
+@pytest.mark.parametrize("prec", [B.RB_MIXED, B.RB_BF16X3])
+def test_first_step_matches_oracle_at_full_size(c3, prec):
     A, A64 = c3
-    h = _handle(A, B.RB_MIXED)
+    h = _handle(A, prec)
     try:
         B.adarbfgs_step(h, 1)
         Lg = _L(h)
@@ -49,14 +51,16 @@ def test_first_step_matches_oracle_at_full_size(c3):
         B.rbfgs_destroy(h)
     _, L1 = orc.adarbfgs_run(A64, np.eye(N), Q, orc.SKETCH_GAUSS, 3, 0, 0, 1)
     I = np.eye(N)
-    # the correction S^ V carries single-pass TF32 rounding (2^-11) and FP32 sketch differences
+    # the correction S^ V carries single-pass TF32 rounding (2^-11) and FP32 sketch differences (the
+    # BF16x3 form's G and W^T add ~2^-16 relative, far below that)
     corr = np.linalg.norm(Lg - L1) / np.linalg.norm(L1 - I)
     assert corr <= 2e-3, corr
 
 
-def test_solve_to_tolerance_checked_in_fp64(c3):
+@pytest.mark.parametrize("prec", [B.RB_MIXED, B.RB_BF16X3])
+def test_solve_to_tolerance_checked_in_fp64(c3, prec):
     A, A64 = c3
-    h = _handle(A, B.RB_MIXED)
+    h = _handle(A, prec)
     try:
         st, iters, r = B.rbfgs_solve(h, TOL, 20000, 32, 256, 1024)
         assert st == B.RB_OK and r <= TOL
