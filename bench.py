@@ -408,9 +408,12 @@ def run_comparison(B, wl, args):
     out["newton_schulz_tf32x3"] = {"time_to_tol_s": t0 + t, "init_s": t0, "iters": it, "resid": r,
                                    "converged": rc == B.RB_OK}
     B.rbfgs_destroy(h)
-    for name, method, step in (("rbfgs_fp32_q64", B.RB_METHOD_RBFGS, B.rbfgs_step),
-                               ("aip_fp32_q64", B.RB_METHOD_AIP, B.aip_step)):
-        h = B.rbfgs_init(n, A.data_ptr(), n, False, B.make_opts(method=method, q=q, prec=B.RB_FP32, seed=1), st)
+    hbm, _, peak_kind = load_peaks()
+    for name, method, step, prec in (("rbfgs_fp32_q64", B.RB_METHOD_RBFGS, B.rbfgs_step, B.RB_FP32),
+                                     ("rbfgs_mixed_q64", B.RB_METHOD_RBFGS, B.rbfgs_step, B.RB_MIXED),
+                                     ("aip_fp32_q64", B.RB_METHOD_AIP, B.aip_step, B.RB_FP32),
+                                     ("aip_mixed_q64", B.RB_METHOD_AIP, B.aip_step, B.RB_MIXED)):
+        h = B.rbfgs_init(n, A.data_ptr(), n, False, B.make_opts(method=method, q=q, prec=prec, seed=1), st)
         step(h, 2)
         torch.cuda.synchronize()
         B.rbfgs_reset(h, 1, 0)
@@ -421,6 +424,22 @@ def run_comparison(B, wl, args):
             traj.append({"steps": 200 * (len(traj) + 1), "seconds": elapsed,
                          "resid": B.rbfgs_residual(h, 256, 12345)})
         out[name] = {"trajectory": traj, "ms_per_step": 1e3 * elapsed / 1200}
+        if prec == B.RB_MIXED:  # the update's roofline: read + write X, read its two n x K panels
+            prof = {}
+            for _ in range(5):
+                for ph, ms in B.rbfgs_profile_step(h):
+                    prof.setdefault(ph, []).append(ms)
+            ph = {k: statistics.median(v) for k, v in prof.items()}
+            kk = 2 * q if method == B.RB_METHOD_RBFGS else q
+            upd_bytes = 2 * 4 * n * n + 2 * 4 * n * kk
+            gbs = upd_bytes / (ph["update X"] * 1e-3) / 1e9
+            out[name]["phases_ms"] = ph
+            out[name]["update_roofline"] = {
+                "kernel": ("X += [S W][W S]^T (k_tc_update, rank 2q, 1 x TF32)" if method == B.RB_METHOD_RBFGS
+                           else "X += S V (k_tc_update, rank q, 1 x TF32)"),
+                "bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                "peak_kind": f"{peak_kind} HBM copy", "algorithmic_bytes_per_launch": upd_bytes,
+                "ms_per_launch": ph["update X"]}
         B.rbfgs_destroy(h)
     out["exp1"] = run_exp1(B, wl, timed, st)
     return out

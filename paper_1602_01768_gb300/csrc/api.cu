@@ -40,7 +40,10 @@ struct rb_ctx {
     void *Sbf = nullptr, *Gbf = nullptr;  // BF16 forms: [hi | lo] BF16 parts of S and G (n x q each, ld ldbf)
     int64_t ldbf = 0;
     tc_plan *tc2 = nullptr;              // plan (own workspace) for the side stream's tensor-core GEMMs
-    void *P3 = nullptr;  // RBFGS: [S | W | S], n x 3q
+    void *P3 = nullptr;  // RBFGS: [S | W | S], n x 3q; tensor-core RBFGS [S | Y | -], AIP [S | W^T | -]
+    float *PQ = nullptr;   // tensor-core RBFGS: the update's row-major panels [S W] and [W S] (n x 2q each);
+                           // AIP: S row-major (n x q)
+    float *Ylo = nullptr;  // tensor-core RBFGS: Y's lo part
     void *Cinv = nullptr, *Dinv = nullptr, *Lam = nullptr, *B1 = nullptr;  // q x q
     double *part = nullptr, *M = nullptr, *N = nullptr, *Tm = nullptr;
     double *dots = nullptr, *dpart = nullptr;
@@ -170,6 +173,8 @@ static void destroy_ctx(rb_ctx *h)
     rb_freet(h->Spart);
     rb_freet(h->Slo);
     rb_freet(h->Glo);
+    rb_freet(h->PQ);
+    rb_freet(h->Ylo);
     rb_freet(h->Mf);
     rb_freet(h->Nf);
     rb_free(h->Sbf);
@@ -342,6 +347,11 @@ static rb_status alloc_sketch_workspace(rb_ctx *h)
     RB_TRY(rb_alloc(&h->blk, sizeof(int) * 2));
     RB_TRY(rb_alloc(&h->idx, sizeof(int) * q));
     if (x_sketch_method(h->method)) RB_TRY(rb_alloc(&h->P3, 3 * nq));
+    if (x_sketch_method(h->method) && !h->f64 && h->prec != RB_FP32) {  // tensor-core RBFGS / AIP
+        RB_TRY(rb_alloc(&h->PQ, 4 * n * q * sizeof(float)));
+        RB_TRY(rb_alloc(&h->Glo, nq));
+        RB_TRY(rb_alloc(&h->Ylo, nq));
+    }
     return RB_OK;
 }
 
@@ -454,7 +464,11 @@ static void rbfgs_step_coord(rb_ctx *h)
     launch_coord_trace_draw(st, n, q, h->nb, h->P, h->seed, h->stream_id, h->k, h->blk);
     launch_coord_gather<T>(st, n, q, A, n, h->blk, G, n, h->M, stp);               // G = A[:, C], M = A[C, C]
     mark(h, "draw + gather");
-    gemm_simt<T>(st, false, false, n, q, n, T(1), X, n, G, n, T(0), Y, n, stp);   // Y = X G
+    bool ytc = false;  // Y = X G, the one pass over X: on the tensor cores in the FP32-storage tensor forms
+    if constexpr (sizeof(T) == 4)
+        if (h->tc && h->prec != RB_FP32)
+            ytc = tc_gemm_nk(h->tc, st, h->prec == RB_TF32 ? 1 : 3, TC_A_K, n, q, n, X, n, G, n, Y, n, stp) >= 0;
+    if (!ytc) gemm_simt<T>(st, false, false, n, q, n, T(1), X, n, G, n, T(0), Y, n, stp);  // Y = X G
     mark(h, "Y=XG");
     launch_gram<T>(st, n, q, q, G, n, Y, n, h->part, h->Tm);                       // T = G^T X G
     launch_core_rbfgs<T>(st, q, h->M, h->Tm, (T *)h->Lam, (T *)h->B1, h->d_status);
@@ -463,6 +477,98 @@ static void rbfgs_step_coord(rb_ctx *h)
     launch_coord_add_b1<T>(st, q, h->blk, (const T *)h->B1, W, n, stp);                     //   + S B1
     launch_coord_update<T>(st, n, q, h->blk, W, n, X, n, stp);                               // rows/cols C
     mark(h, "update rows/cols");
+}
+
+// ---------------------------------------------------------------------------
+// Tensor-core RBFGS and AIP steps (FP32 storage; Gaussian sketch, exact in TF32).
+// ---------------------------------------------------------------------------
+// CTAs of a q x q Gram product when it runs split over K
+constexpr int GRAM_CTAS = 64;
+
+// q x q Gram product X1^T X2 (K = n) into out (ld q): split over K on the tensor cores
+// (3 terms with X2's lo part, else 1), any other shape by the general product.
+static void tc_gram(rb_ctx *h, int terms, const float *X1, const float *X2, const float *X2lo, float *out)
+{
+    const int n = h->n, q = h->q;
+    if (tc_gemm_splitk(h->tc, h->st, terms, TC_A_K, q, q, n, X1, n, X2, terms == 3 ? X2lo : nullptr, n, out, q,
+                       h->d_status, GRAM_CTAS) != 0)
+        tc_gemm_nk(h->tc, h->st, terms, TC_A_K, q, q, n, X1, n, X2, n, out, q, h->d_status);
+}
+
+// shapes the tensor-core RBFGS / AIP steps take: 16-byte rows of X and of the 2q-wide panels
+static bool x_tc_shape(rb_ctx *h)
+{
+    return !h->f64 && h->tc && h->PQ && h->n % 4 == 0 && h->q % 4 == 0 && h->q <= 64;
+}
+
+// RBFGS, Eq. (qunac) in its expanded form:
+//   G = A S, M = S^T G, Y = X G, T = G^T Y, [B1; -Lam] from the core,
+//   W = [S | Y] [B1; -Lam] = S B1 - Y Lam,  X += S W^T + W S^T.
+// The rank-2q update is one pass over X: X += P Q^T with the row-major panels P = [S W]
+// and Q = [W S] (W written into both, transposed, by its product's epilogue).
+static void rbfgs_step_tc(rb_ctx *h)
+{
+    const int n = h->n, q = h->q;
+    cudaStream_t st = h->st;
+    const int *stp = h->d_status;
+    float *A = (float *)h->A, *X = (float *)h->X, *G = (float *)h->G;
+    float *S = (float *)h->P3, *Y = S + (size_t)n * q;  // [S | Y]: W's M-contiguous A operand
+    float *P = h->PQ, *Q = h->PQ + 2 * (size_t)n * q;
+    const int acc = (h->prec == RB_TF32) ? 1 : 3, upd = (h->prec == RB_TF32X3) ? 3 : 1;
+    float *Glo = acc == 3 ? h->Glo : nullptr, *Ylo = acc == 3 ? h->Ylo : nullptr;
+    launch_gauss_sketch<float>(st, n, q, h->seed, h->stream_id, h->k, S, n);
+    mark(h, "sketch");
+    // G = A S: S is exact in TF32, so A's two parts carry the product; G's lo part beside G
+    tc_gemm_nk_lo(h->tc, st, acc == 3 ? 2 : 1, TC_A_K, n, q, n, A, n, S, nullptr, n, G, Glo, n, stp);
+    mark(h, "G=AS");
+    tc_gram(h, acc, S, G, Glo, h->Mf);  // M = S^T A S
+    // Y = X G (X symmetric: its columns are its rows), Y's lo part beside Y
+    tc_gemm_nk_lo(h->tc, st, acc, TC_A_K, n, q, n, X, n, G, Glo, n, Y, Ylo, n, stp);
+    mark(h, "Y=XG");
+    tc_gram(h, acc, G, Y, Ylo, h->Nf);  // T = G^T X G
+    launch_core_pack(st, q, h->Mf, h->Nf, h->Bv, h->d_status);
+    mark(h, "grams + core");
+    // W = [S | Y] [B1; -Lam], transposed into columns q .. 2q-1 of P's rows and 0 .. q-1 of Q's
+    tc_gemm_nk_t(h->tc, st, acc, TC_A_MN, n, q, 2 * q, S, n, h->Bv, 2 * q, P + q, 2 * q, stp);
+    tc_gemm_nk_t(h->tc, st, acc, TC_A_MN, n, q, 2 * q, S, n, h->Bv, 2 * q, Q, 2 * q, stp);
+    launch_rows_from_cols(st, n, q, S, n, P, 2 * q, 0);
+    launch_rows_from_cols(st, n, q, S, n, Q, 2 * q, q);
+    mark(h, "W");
+    // X += [S W][W S]^T: W -> 0 at the fixed point, so the mixed form takes one TF32 pass
+    if (upd != 1 || tc_update_persistent(h->tc, st, n, 2 * q, P, Q, X, n, stp) != 0)
+        tc_update(h->tc, st, upd, n, 2 * q, P, Q, X, n, stp);
+    mark(h, "update X");
+}
+
+// AIP, Eq. (BFGSas): G = A S, Lam = (S^T G)^-1, W^T = X^T G,
+//   V^T = [S | W^T] [Lam; -Lam] = (S - W^T) Lam,  X += S V  (one pass over X).
+static void aip_step_tc(rb_ctx *h)
+{
+    const int n = h->n, q = h->q;
+    cudaStream_t st = h->st;
+    const int *stp = h->d_status;
+    float *A = (float *)h->A, *X = (float *)h->X, *G = (float *)h->G, *V = (float *)h->V;
+    float *S = (float *)h->P3, *Wt = S + (size_t)n * q;  // [S | W^T]: V^T's M-contiguous A operand
+    float *Srow = h->PQ;
+    const int acc = (h->prec == RB_TF32) ? 1 : 3, upd = (h->prec == RB_TF32X3) ? 3 : 1;
+    float *Glo = acc == 3 ? h->Glo : nullptr;
+    launch_gauss_sketch<float>(st, n, q, h->seed, h->stream_id, h->k, S, n);
+    mark(h, "sketch");
+    tc_gemm_nk_lo(h->tc, st, acc == 3 ? 2 : 1, TC_A_K, n, q, n, A, n, S, nullptr, n, G, Glo, n, stp);  // G = A S
+    mark(h, "G=AS");
+    tc_gram(h, acc, S, G, Glo, h->Mf);
+    launch_core_pack(st, q, h->Mf, nullptr, h->Bv, h->d_status);  // [Lam; -Lam]
+    mark(h, "gram + core");
+    // W^T = X^T G (element (m, k) of X^T at X[k + m n])
+    tc_gemm_nk_lo(h->tc, st, acc, TC_A_K, n, q, n, X, n, G, Glo, n, Wt, nullptr, n, stp);
+    mark(h, "W=G^TX");
+    tc_gemm_nk_t(h->tc, st, acc, TC_A_MN, n, q, 2 * q, S, n, h->Bv, 2 * q, V, q, stp);  // V (q x n, ld q)
+    launch_rows_from_cols(st, n, q, S, n, Srow, q, 0);
+    mark(h, "V");
+    // X += S V: V -> 0 at the fixed point, so the mixed form takes one TF32 pass
+    if (upd != 1 || tc_update_persistent(h->tc, st, n, q, Srow, V, X, n, stp) != 0)
+        tc_update(h->tc, st, upd, n, q, Srow, V, X, n, stp);
+    mark(h, "update X");
 }
 
 extern "C" rb_status rbfgs_step(rbfgs_t h, int nsteps)
@@ -477,6 +583,8 @@ extern "C" rb_status rbfgs_step(rbfgs_t h, int nsteps)
         } else {
             if (h->f64)
                 rbfgs_step_gauss<double>(h);
+            else if (x_tc_shape(h))
+                rbfgs_step_tc(h);
             else
                 rbfgs_step_gauss<float>(h);
         }
@@ -524,7 +632,11 @@ static void aip_step_coord(rb_ctx *h)
     launch_coord_gather<T>(st, n, q, A, n, h->blk, G, n, h->M, stp);               // G = A[:, C], M = A[C, C]
     launch_core_rbfgs<T>(st, q, h->M, h->M, Lam, (T *)h->B1, h->d_status);        // Lambda = M^-1 (padded)
     mark(h, "draw + gather + core");
-    gemm_simt<T>(st, true, false, q, n, n, T(1), G, n, X, n, T(0), W, q, stp);    // W = G^T X
+    bool wtc = false;  // W = G^T X, the one pass over X, as W^T = X^T G with a transposed output (q x n, ld q)
+    if constexpr (sizeof(T) == 4)
+        if (h->tc && h->prec != RB_FP32)
+            wtc = tc_gemm_nk_t(h->tc, st, h->prec == RB_TF32 ? 1 : 3, TC_A_K, n, q, n, X, n, G, n, W, q, stp) == 0;
+    if (!wtc) gemm_simt<T>(st, true, false, q, n, n, T(1), G, n, X, n, T(0), W, q, stp);  // W = G^T X
     mark(h, "W=G^TX");
     gemm_simt<T>(st, false, false, q, n, q, T(-1), Lam, q, W, q, T(0), V, q, stp); // V = -Lambda W
     launch_aip_coord<T>(st, n, q, h->blk, Lam, V, q, X, n, stp);                  // + Lambda I[C,:]; X[C,:] += V
@@ -543,6 +655,8 @@ extern "C" rb_status aip_step(rbfgs_t h, int nsteps)
         } else {
             if (h->f64)
                 aip_step_gauss<double>(h);
+            else if (x_tc_shape(h))
+                aip_step_tc(h);
             else
                 aip_step_gauss<float>(h);
         }
@@ -626,8 +740,7 @@ constexpr int SIDE_SMS = 8;
 constexpr int SIDE_SMS_G = 4;
 // SMs the fused update leaves to the next step's D chain (S~^T S~ and its core)
 constexpr int SIDE_SMS_UPD = 4;
-// CTAs of S^T G when it runs on the main stream (split over K; stream-K partial tiles)
-constexpr int GRAM_CTAS = 64;
+
 
 // D chain on the handle's D stream: S~^T S~ (one exact pass: S~ is TF32) on the SMs other
 // work leaves free, then its core, D^-T written as rows dofs .. dofs + q - 1 of Bv.

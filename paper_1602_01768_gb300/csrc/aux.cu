@@ -397,3 +397,16 @@ template void launch_aip_coord<float>(cudaStream_t, int, int, const int *, const
 template void launch_aip_coord<double>(cudaStream_t, int, int, const int *, const double *, double *, int64_t,
                                        double *, int64_t, const int *);
 
+
+// out[off + c + i rp] = X[i + c ldx]: thread (i, c), coalesced reads along i.
+__global__ void k_rows_from_cols(int n, int q, const float *X, int64_t ldx, float *out, int rp, int off)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, c = blockIdx.y;
+    if (i < n) out[off + c + (int64_t)i * rp] = X[i + (int64_t)c * ldx];
+}
+
+void launch_rows_from_cols(cudaStream_t st, int n, int q, const float *X, int64_t ldx, float *out, int rp, int off)
+{
+    rb_count_launch();
+    k_rows_from_cols<<<dim3((n + 255) / 256, q), 256, 0, st>>>(n, q, X, ldx, out, rp, off);
+}

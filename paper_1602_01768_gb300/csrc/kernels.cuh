@@ -36,6 +36,11 @@ bool launch_core_tr32(cudaStream_t, int q, const float *M, float *Xinv, float *x
 // FP64, written only as the scaled FP32 transposes s1 X^T / s2 X^T.
 bool launch_core_tr64(cudaStream_t, int q, const float *M, float *xt1, int ld1, float s1, float *xt2, int ld2,
                       float s2, int *status);
+// q <= 64: the RBFGS / AIP core (FP64) from FP32 Gram matrices, packed as the 2q x q B operand
+// [B1; -Lam] (Tf given: RBFGS) or [Lam; -Lam] (Tf null: AIP), ld 2q.
+void launch_core_pack(cudaStream_t, int q, const float *Mf, const float *Tf, float *Bw, int *status);
+// out[off + c + i rp] = X[i + c ldx] for i < n, c < q: a column-major panel into rows of pitch rp.
+void launch_rows_from_cols(cudaStream_t, int n, int q, const float *X, int64_t ldx, float *out, int rp, int off);
 template <typename T>
 void launch_core_rbfgs(cudaStream_t, int q, const double *M, const double *Tm, T *Lam, T *B1, int *status);
 template <typename T>

@@ -323,6 +323,71 @@ template void launch_core_rbfgs<float>(cudaStream_t, int, const double *, const 
 template void launch_core_rbfgs<double>(cudaStream_t, int, const double *, const double *, double *, double *,
                                         int *);
 
+// Tensor-core forms of RBFGS and AIP: the same FP64 core from FP32 Gram matrices
+// (M = S^T A S and, for RBFGS, T = G^T X G), written straight into the
+// 2q x q B operand (ld 2q) of the product that forms the update's panel:
+//   RBFGS (Tf != null): [B1; -Lam], B1 = (Lam + Lam T Lam) / 2, for W = [S | Y] [B1; -Lam];
+//   AIP   (Tf == null): [Lam; -Lam], for V^T = [S | W^T] [Lam; -Lam].
+__global__ void k_core_pack(int q, const float *Mf, const float *Tf, float *Bw, int *status)
+{
+    extern __shared__ double sm[];
+    double *a = sm;               // C, then C^-1
+    double *lam = sm + q * q;     // Lam
+    double *tl = sm + 2 * q * q;  // T Lam
+    if (status_bad(status)) return;
+    for (int e = threadIdx.x; e < q * q; e += blockDim.x) {
+        const int i = e % q, c = e / q;
+        a[e] = 0.5 * ((double)Mf[i + c * q] + (double)Mf[c + i * q]);
+    }
+    __syncthreads();
+    if (!smem_cholesky(a, q)) {
+        if (threadIdx.x == 0) atomicOr(status, ST_NOTSPD);
+        return;
+    }
+    smem_tri_inverse(a, q);
+    // Lam = C^-T C^-1: Lam_ij = sum_k Cinv_ki Cinv_kj (k >= max(i, j))
+    for (int e = threadIdx.x; e < q * q; e += blockDim.x) {
+        const int i = e % q, j = e / q;
+        double s = 0.0;
+        for (int k = max(i, j); k < q; ++k) s += a[k + i * q] * a[k + j * q];
+        lam[e] = s;
+    }
+    __syncthreads();
+    if (Tf) {
+        for (int e = threadIdx.x; e < q * q; e += blockDim.x) {  // T Lam (T symmetrised)
+            const int i = e % q, j = e / q;
+            double s = 0.0;
+            for (int k = 0; k < q; ++k) s += 0.5 * ((double)Tf[i + k * q] + (double)Tf[k + i * q]) * lam[k + j * q];
+            tl[e] = s;
+        }
+        __syncthreads();
+    }
+    for (int e = threadIdx.x; e < q * q; e += blockDim.x) {
+        const int i = e % q, j = e / q;
+        double top = lam[e];
+        if (Tf) {
+            double s = 0.0;
+            for (int k = 0; k < q; ++k) s += lam[i + k * q] * tl[k + j * q];
+            top = 0.5 * (lam[e] + s);
+        }
+        if (!isfinite(top) || !isfinite(lam[e])) atomicOr(status, ST_NONFINITE);
+        Bw[i + (size_t)j * 2 * q] = (float)top;
+        Bw[q + i + (size_t)j * 2 * q] = (float)-lam[e];
+    }
+}
+
+void launch_core_pack(cudaStream_t st, int q, const float *Mf, const float *Tf, float *Bw, int *status)
+{
+    const size_t smem = sizeof(double) * 3 * q * q;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_core_pack, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        attr_set = true;
+    }
+    rb_count_launch();
+    k_core_pack<<<1, 512, smem, st>>>(q, Mf, Tf, Bw, status);
+}
+
 // ---------------------------------------------------------------------------
 // Elementwise helpers
 // ---------------------------------------------------------------------------

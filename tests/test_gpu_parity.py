@@ -420,6 +420,90 @@ def test_rbfgs_fp32_parity(sketch, kind, q):
 
 
 # --------------------------------------------------------------------------
+# Tensor-core RBFGS (Eq. (qunac)) and AIP (Eq. (BFGSas)) steps
+# --------------------------------------------------------------------------
+# Bars: 3xTF32 products <= 1e-4 relative along 40 steps (~FP32 accuracy); mixed (the rank-2q or
+# rank-q update in one TF32 pass: it vanishes at the fixed point, so its 2^-11 rounding scales
+# with the step's change) <= 1.5e-2; single-pass TF32 <= 2e-2.
+_X_BARS = {B.RB_TF32X3: 1e-4, B.RB_MIXED: 1.5e-2, B.RB_TF32: 2e-2}
+
+
+@pytest.mark.parametrize("prec", [B.RB_TF32X3, B.RB_MIXED, B.RB_TF32])
+@pytest.mark.parametrize("n,q", [(512, 32), (1028, 64)])
+def test_rbfgs_tensor_core_parity(prec, n, q):
+    A = wl.c2_matrix(n=n).astype(np.float32).astype(np.float64)
+    h = _handle(A, B.RB_METHOD_RBFGS, B.RB_SKETCH_GAUSS, q, prec, seed=24)
+    try:
+        X = np.eye(n)
+        done = 0
+        for chk in (1, 10, 40):
+            B.rbfgs_step(h, chk - done)
+            _, X = orc.rbfgs_run(A, X, q, orc.SKETCH_GAUSS, 24, 0, done, chk - done)
+            done = chk
+            Xg = export(h, n, prec, B.RB_WHAT_X)
+            assert rel(Xg, X) <= _X_BARS[prec], (chk, rel(Xg, X))
+            assert rel(Xg, Xg.T) <= 1e-5  # the rank-2q update keeps X symmetric up to rounding
+        r_orc = orc.residual(A, X)
+        assert abs(orc.residual(A, Xg) - r_orc) <= (1e-3 if prec == B.RB_TF32X3 else 5e-2) * r_orc
+    finally:
+        B.rbfgs_destroy(h)
+
+
+def test_rbfgs_mixed_reaches_tolerance_like_oracle():
+    # a well-conditioned matrix (kappa = 10), n = 256, q = 32: the mixed tensor-core RBFGS reaches
+    # 1e-4 and its iterate, evaluated exactly in FP64, is within 0.1 tol of the oracle's
+    n, q, tol = 256, 32, 1e-4
+    A, _, _ = wl.spd_spectrum(n, 10.0, 43)
+    A = A.astype(np.float32).astype(np.float64)
+    h = _handle(A, B.RB_METHOD_RBFGS, B.RB_SKETCH_GAUSS, q, B.RB_MIXED, seed=25)
+    try:
+        st, iters, r = B.rbfgs_solve(h, tol, 5000, 16, 0, 0)
+        assert st == B.RB_OK and r <= tol
+        _, X = orc.rbfgs_run(A, np.eye(n), q, orc.SKETCH_GAUSS, 25, 0, 0, iters)
+        r_orc = orc.residual(A, X)
+        r_gpu = orc.residual(A, export(h, n, B.RB_MIXED, B.RB_WHAT_X))
+        assert abs(r_gpu - r_orc) <= 0.1 * tol, (r_gpu, r_orc, iters)
+    finally:
+        B.rbfgs_destroy(h)
+
+
+@pytest.mark.parametrize("prec", [B.RB_TF32X3, B.RB_MIXED])
+def test_aip_tensor_core_parity(prec):
+    n, q = 512, 32
+    A, _, _ = wl.spd_spectrum(n, 50.0, 44)
+    A = A.astype(np.float32).astype(np.float64)
+    h = _handle(A, B.RB_METHOD_AIP, B.RB_SKETCH_GAUSS, q, prec, seed=26)
+    try:
+        X = np.eye(n)
+        done = 0
+        for chk in (1, 10, 40):
+            B.aip_step(h, chk - done)
+            _, X = orc.aip_run(A, X, q, orc.SKETCH_GAUSS, 26, 0, done, chk - done)
+            done = chk
+            assert rel(export(h, n, prec, B.RB_WHAT_X), X) <= _X_BARS[prec], chk
+    finally:
+        B.rbfgs_destroy(h)
+
+
+@pytest.mark.parametrize("method,kind,step", [(B.RB_METHOD_RBFGS, "rbfgs", B.rbfgs_step),
+                                              (B.RB_METHOD_AIP, "aip", B.aip_step)])
+def test_coordinate_tensor_core_parity(method, kind, step):
+    # trace-weighted coordinate blocks (bit-exact draws); the one pass over X (Y = X A[:, C], or
+    # W^T = X^T A[:, C]) on the tensor cores in 3 terms: <= 1e-4 along 100 steps
+    n, q = 512, 16
+    A, _, _ = wl.spd_spectrum(n, 30.0, 45)
+    A = A.astype(np.float32).astype(np.float64)
+    h = _handle(A, method, B.RB_SKETCH_COORD_TRACE, q, B.RB_TF32X3, seed=27)
+    run = orc.rbfgs_run if kind == "rbfgs" else orc.aip_run
+    try:
+        step(h, 100)
+        _, X = run(A, np.eye(n), q, orc.SKETCH_COORD_TRACE, 27, 0, 0, 100)
+        assert rel(export(h, n, B.RB_TF32X3, B.RB_WHAT_X), X) <= 1e-4
+    finally:
+        B.rbfgs_destroy(h)
+
+
+# --------------------------------------------------------------------------
 # BF16-split forms: G = A S and W^T = L^T G as kind::f16 products
 # --------------------------------------------------------------------------
 @pytest.mark.parametrize("n,q", [(768, 64), (4100, 128)])
