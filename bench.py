@@ -38,7 +38,7 @@ METRIC = "time to ‖I−XA‖_F/√n≤1e-4 at n=16384 (mixed vs FP32); solves/
 N_DEFAULT, Q_DEFAULT, TOL_DEFAULT = 16384, 128, 1e-4
 CHECK_EVERY, CHECK_COLS, CONFIRM_COLS = 32, 256, 1024
 MAX_ITER = 20000
-SERVE_MAX_ITER = 2000  # per request; the 1e-6 class stalls at the FP32 floor and runs to this cap
+SERVE_MAX_ITER = 4000  # per request; requests that stall at their floor stop earlier (floor-limited)
 # DRAM bytes (read + write) of one k_tc_update launch at n = 8192, q = 128, from one ncu capture
 # of that launch; scaled by (n / 8192)^2 for other n at q = 128 (the bytes grow as n^2 at fixed q).
 UPDATE_TRAFFIC_N8192_Q128 = 277638912 + 208375552
@@ -78,6 +78,8 @@ def parse():
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=64)
     ap.add_argument("--serve-rate", type=float, default=200.0)
+    ap.add_argument("--serve-sub-requests", type=int, default=24, help="requests of the sub-capacity serving run")
+    ap.add_argument("--serve-sub-rate", type=float, default=1.0, help="arrival rate of the sub-capacity run")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-compare", action="store_true", help="skip the n = 4096 method comparison")
     ap.add_argument("--batch-count", type=int, default=512)
@@ -325,19 +327,22 @@ def config(args):
             "residual_check": f"every {CHECK_EVERY} steps on {CHECK_COLS} columns, confirmed on {CONFIRM_COLS}"}
 
 
-def run_serving(B, wl, args):
-    """Open-loop Poisson stream (first --serve-requests requests of the seeded stream) through
-    the continuous-batching server: mixed form, check every 32 steps on 128 columns."""
+def run_serving(B, wl, args, requests=None, rate=None):
+    """Poisson stream (the first `requests` requests of the seeded stream at `rate` req/s) through
+    the continuous-batching server: BF16x3 for tolerances >= 1e-4, mixed below; check every 32 steps
+    on 128 columns; requests that stall at their arithmetic's floor finish as floor-limited."""
     import numpy as np
     import torch
 
-    stream = wl.c5_stream(requests=args.serve_requests, rate=args.serve_rate)
+    requests = requests or args.serve_requests
+    rate = rate or args.serve_rate
+    stream = wl.c5_stream(requests=requests, rate=rate)
     mats = {}
     for r in stream:  # inputs built before the clock starts (device-resident)
         mats[r["seed"]] = wl.c5_matrix(r["n"], r["seed"], device="cuda")
     torch.cuda.synchronize()
     budget = wl.WORKLOADS["c5_serving"]["budget_bytes"]
-    s = B.rb_srv_create(budget, 64, B.RB_MIXED, 32, 128, SERVE_MAX_ITER)
+    s = B.rb_srv_create(budget, 64, B.RB_BF16X3, 32, 128, SERVE_MAX_ITER)
     tickets = []
     t0 = time.perf_counter()
     for r in stream:
@@ -354,19 +359,23 @@ def run_serving(B, wl, args):
     lat = sorted(r.latency_s for r in res)
     by_tol = {}
     for r, req in zip(res, stream):
-        c = by_tol.setdefault(f"{req['tol']:g}", {"requests": 0, "converged": 0, "resid": [], "latency": []})
+        c = by_tol.setdefault(f"{req['tol']:g}", {"requests": 0, "converged": 0, "floor_limited": 0, "resid": [],
+                                                  "latency": [], "iters": []})
         c["requests"] += 1
         c["converged"] += int(r.status == B.RB_OK)
+        c["floor_limited"] += int(r.floor_limited)
         c["resid"].append(r.resid)
         c["latency"].append(r.latency_s)
-    per_tol = {k: {"requests": v["requests"], "converged": v["converged"],
-                   "median_final_resid": statistics.median(v["resid"]),
+        c["iters"].append(r.iters)
+    per_tol = {k: {"requests": v["requests"], "converged": v["converged"], "floor_limited": v["floor_limited"],
+                   "median_final_resid": statistics.median(v["resid"]), "median_iters": statistics.median(v["iters"]),
                    "p50_s": statistics.median(v["latency"])} for k, v in sorted(by_tol.items())}
-    return {"workload": f"first {len(stream)} requests of the Poisson stream at {args.serve_rate:g} req/s, "
+    return {"workload": f"first {len(stream)} requests of the Poisson stream at {rate:g} req/s, "
                         "n log-uniform in [512, 8192], A = M^T M/(2n) + 1e-3 I, tol in {1e-3,1e-4,1e-6}, "
-                        "q = 32 round(sqrt(n)/32), mixed form, HBM budget 120 GiB, <= 64 live",
+                        "q = 32 round(sqrt(n)/32), BF16x3 (tol >= 1e-4) / 3xTF32 mixed (tol < 1e-4), "
+                        "HBM budget 120 GiB, <= 64 live",
             "requests": len(res), "converged": len(ok), "max_iter": SERVE_MAX_ITER,
-            "not_converged": len(res) - len(ok),
+            "not_converged": len(res) - len(ok), "floor_limited": sum(r.floor_limited for r in res),
             "solves_per_s": len(res) / wall, "p50_s": lat[len(lat) // 2],
             "p99_s": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)],
             "mean_queue_s": statistics.mean(r.queue_s for r in res), "wall_s": wall,
@@ -448,29 +457,39 @@ def run_comparison(B, wl, args):
 def run_exp1(B, wl, timed, st):
     """Sec. 10, Experiment 1: A = Abar^T Abar with Abar uniform on [0, 1]^{n x n}; each method from
     the paper's X_0 until ||I - AX_k||_F / ||I - AX_0||_F <= 1e-2 (exact residuals at start and end).
-    kappa(A) is far beyond binary32 (the paper ran these in double), so every method runs in FP64."""
+    The text's sizes (n = 1000, 2000, 5000) run in FP64 like the paper's MATLAB runs (kappa(A) is far
+    beyond binary32); the captions' sizes (1e4, 2e4, 5e4) run the AdaRBFGS variants in the BF16x3
+    form with FP32 storage, the matrix built on the GPU.  Newton-Schulz and MR stall on these
+    matrices (rounding swamps the smallest modes): 300 steps at n <= 2000, 20 at 5000, not run above."""
     import numpy as np
     import torch
 
     res = {}
-    for n in (1000, 2000):
-        A = torch.from_numpy(np.ascontiguousarray(wl.spd_uniform_gram(n, 10 + n).T)).cuda()
-        q = 32 * max(1, round(n ** 0.5 / 32))
+    for n in (1000, 2000, 5000, 10000, 20000, 50000):
+        big = n > 5000
+        if big:
+            A = wl.spd_uniform_gram_torch(n, 10 + n, device="cuda")
+        else:
+            A = torch.from_numpy(np.ascontiguousarray(wl.spd_uniform_gram(n, 10 + n).T)).cuda()
+        q = min(128, 32 * max(1, round(n ** 0.5 / 32)))
+        prec = B.RB_BF16X3 if big else B.RB_FP64
+        fp64 = not big
         row = {}
-        runs = (("adarbfgs_gauss", lambda: B.rbfgs_init(n, A.data_ptr(), n, True, B.make_opts(
-                    method=B.RB_METHOD_ADARBFGS, sketch=B.RB_SKETCH_GAUSS, q=q, prec=B.RB_FP64, seed=1), st), 32),
-                ("adarbfgs_cols", lambda: B.rbfgs_init(n, A.data_ptr(), n, True, B.make_opts(
-                    method=B.RB_METHOD_ADARBFGS, sketch=B.RB_SKETCH_COORD_UNIFORM, q=q, prec=B.RB_FP64, seed=1),
-                    st), 32),
-                ("newton_schulz", lambda: B.newton_schulz_init(n, A.data_ptr(), n, True, B.RB_FP64, stream=st), 1),
-                ("mr", lambda: B.mr_init(n, A.data_ptr(), n, True, B.RB_FP64, stream=st), 1))
+        runs = [("adarbfgs_gauss", lambda: B.rbfgs_init(n, A.data_ptr(), n, fp64, B.make_opts(
+                    method=B.RB_METHOD_ADARBFGS, sketch=B.RB_SKETCH_GAUSS, q=q, prec=prec, seed=1), st), 32),
+                ("adarbfgs_cols", lambda: B.rbfgs_init(n, A.data_ptr(), n, fp64, B.make_opts(
+                    method=B.RB_METHOD_ADARBFGS, sketch=B.RB_SKETCH_COORD_UNIFORM, q=q, prec=prec, seed=1),
+                    st), 32)]
+        if not big:
+            runs += [("newton_schulz", lambda: B.newton_schulz_init(n, A.data_ptr(), n, True, B.RB_FP64, stream=st), 1),
+                     ("mr", lambda: B.mr_init(n, A.data_ptr(), n, True, B.RB_FP64, stream=st), 1)]
         for name, make, every in runs:
             h = None
             try:
                 h, t_init = timed(make)
-                r0 = B.rbfgs_residual(h, 0, 0)
-                cap = 3000 if name.startswith("adarbfgs") else 300  # NS and MR stall: rounding swamps the smallest modes
-                (rc, it, r), t = timed(lambda: B.rbfgs_solve(h, 1e-2 * r0, cap, every, 256, 0))
+                r0 = B.rbfgs_residual(h, 0 if n <= 5000 else 1024, 0)
+                cap = 3000 if name.startswith("adarbfgs") else (300 if n <= 2000 else 20)
+                (rc, it, r), t = timed(lambda: B.rbfgs_solve(h, 1e-2 * r0, cap, every, 256, 0 if n <= 5000 else 1024))
                 row[name] = {"seconds": t_init + t, "iters": it, "relative_error": r / r0,
                              "converged": rc == B.RB_OK}
             except B.RbfgsError as e:
@@ -478,7 +497,10 @@ def run_exp1(B, wl, timed, st):
             finally:
                 if h is not None:
                     B.rbfgs_destroy(h)
-        res[f"n{n}"] = dict(q=q, prec="fp64", **row)
+        res[f"n{n}"] = dict(q=q, prec="bf16x3 (FP32 storage)" if big else "fp64",
+                            residual="sampled on 1024 columns" if n > 5000 else "exact", **row)
+        del A
+        torch.cuda.empty_cache()
     return res
 
 
@@ -668,8 +690,8 @@ def main():
         del A64, L_host
 
     # ---- the other precision forms and the FP64 q x q core, same tolerance (one solve each) ----
-    def one_solve(prec_o, core=0):
-        oo = B.make_opts(method=B.RB_METHOD_ADARBFGS, sketch=B.RB_SKETCH_GAUSS, q=q, prec=prec_o, seed=0,
+    def one_solve(prec_o, core=0, sketch=B.RB_SKETCH_GAUSS):
+        oo = B.make_opts(method=B.RB_METHOD_ADARBFGS, sketch=sketch, q=q, prec=prec_o, seed=0,
                          stream_id=rank, core_fp64=core)
         hh = B.rbfgs_init(n, A.data_ptr(), n, False, oo, stream)
         B.adarbfgs_step(hh, 2)
@@ -688,6 +710,8 @@ def main():
         if prec != B.RB_MIXED:
             forms["mixed_3xtf32"] = one_solve(B.RB_MIXED)
         forms[f"{args.prec}_fp64_core"] = one_solve(prec, core=1)
+        # AdaRBFGS_cols (Sec. 10): S = L[:, C] gathered, D = I
+        forms[f"{args.prec}_cols"] = one_solve(prec, sketch=B.RB_SKETCH_COORD_UNIFORM)
 
     # ---- plain FP32 form, same tolerance (one solve) ----
     fp32 = None
@@ -729,7 +753,9 @@ def main():
     # ---- serving loop on the request-stream workload (bounded sample, open loop) ----
     serving = None
     if not args.no_serve:
-        serving = run_serving(B, wl, args)
+        serving = {"open_loop": run_serving(B, wl, args),
+                   "sub_capacity": run_serving(B, wl, args, requests=args.serve_sub_requests,
+                                               rate=args.serve_sub_rate)}
 
     # ---- batched coordinate RBFGS (one persistent launch per round) ----
     batched = None

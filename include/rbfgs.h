@@ -286,6 +286,20 @@ rb_status rbfgs_profile_step(rbfgs_t h, double *ms, const char **names, int cap,
  */
 rb_status rbfgs_reset(rbfgs_t h, uint64_t seed, uint64_t stream_id);
 
+/*
+ * Failure-path check of the bounded device-side waits (no counterpart in the
+ * paper).  Every mbarrier wait in this library's tensor-core kernels gives up
+ * after a fixed number of SM cycles (about two seconds), records the failure
+ * in the handle's device status word and lets the kernel return instead of
+ * hanging the GPU.  This call queues, on the handle's stream, one small kernel
+ * that waits on a barrier nothing ever completes (it issues no copy and no
+ * MMA, so nothing is left in flight) with a limit of limit_cycles SM cycles
+ * (1 .. 2^32).  The wait runs out and marks the handle failed: later steps
+ * leave the iterate untouched and the next synchronising call returns
+ * RB_ETIMEOUT.  Asynchronous.  Errors: RB_EINVAL.
+ */
+rb_status rbfgs_wait_selftest(rbfgs_t h, int64_t limit_cycles);
+
 /* Number of kernels this library has launched since it was loaded. */
 rb_status rbfgs_launch_count(uint64_t *count);
 
@@ -323,7 +337,14 @@ rb_status rb_batch_destroy(rb_batch_t b);
 
 /*
  * Serving loop with continuous batching (AdaRBFGS, Gaussian sketch).
- * rb_srv_create starts a scheduler thread on the current device.  Each
+ * rb_srv_create starts a scheduler thread on the current device.  Each request
+ * runs in the server's form `prec`, except that a BF16 form serves only
+ * tolerances >= 1e-4 (smaller ones run in RB_MIXED): its products leave a
+ * residual floor near 2e-5.  A request whose sampled residual has not fallen
+ * by 10 % over 8 checks is finished as floor-limited (RB_NOTCONV with
+ * floor_limited = 1): every FP32-storage form stops falling near a floor set by
+ * its rounding (measured: ~3e-6 FP32, ~7e-6 3xTF32 at n / q = 64), so smaller
+ * tolerances are not reachable in them.  Each
  * submitted request (an SPD A, tol, seed; q = 0 picks 32 round(sqrt(n)/32),
  * at least 32) waits in a FIFO queue until its device footprint
  * (rbfgs_footprint, plus a staging copy when A is in host memory) fits in
@@ -346,6 +367,9 @@ typedef struct {
     double latency_s; /* submit -> done */
     double queue_s;   /* submit -> admitted */
     int32_t n, q;
+    int32_t prec;          /* the form the request ran in */
+    int32_t floor_limited; /* 1: stopped above tol because the residual stopped falling (RB_NOTCONV;
+                              resid is then the floor its arithmetic reached) */
 } rb_srv_result;
 typedef struct {
     int32_t completed, failed, queued, live;

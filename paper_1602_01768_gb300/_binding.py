@@ -65,6 +65,7 @@ _SIGS = {
     "rbfgs_export_host": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64]),
     "rbfgs_profile_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]),
     "rbfgs_launch_count": (C.c_int, [C.c_void_p]),
+    "rbfgs_wait_selftest": (C.c_int, [C.c_void_p, C.c_int64]),
     "rbfgs_reset": (C.c_int, [C.c_void_p, C.c_uint64, C.c_uint64]),
     "rbfgs_destroy": (C.c_int, [C.c_void_p]),
     "rb_batch_create": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
@@ -257,6 +258,10 @@ def rbfgs_reset(h, seed, stream_id=0):
     return _check(_lib().rbfgs_reset(h, seed, stream_id), "rbfgs_reset")
 
 
+def rbfgs_wait_selftest(h, limit_cycles):
+    return _check(_lib().rbfgs_wait_selftest(h, int(limit_cycles)), "rbfgs_wait_selftest")
+
+
 def rbfgs_launch_count():
     c = C.c_uint64()
     _check(_lib().rbfgs_launch_count(C.byref(c)), "rbfgs_launch_count")
@@ -328,7 +333,8 @@ def rbfgs_footprint(n, opts):
 
 class SrvResult(C.Structure):
     _fields_ = [("ticket", C.c_int64), ("status", C.c_int32), ("iters", C.c_int32), ("resid", C.c_double),
-                ("latency_s", C.c_double), ("queue_s", C.c_double), ("n", C.c_int32), ("q", C.c_int32)]
+                ("latency_s", C.c_double), ("queue_s", C.c_double), ("n", C.c_int32), ("q", C.c_int32),
+                ("prec", C.c_int32), ("floor_limited", C.c_int32)]
 
 
 class SrvStats(C.Structure):

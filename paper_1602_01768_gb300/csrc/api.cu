@@ -340,7 +340,8 @@ static rb_status alloc_sketch_workspace(rb_ctx *h)
     RB_TRY(rb_alloc(&h->Dinv, qq));
     RB_TRY(rb_alloc(&h->Lam, qq));
     RB_TRY(rb_alloc(&h->B1, qq));
-    RB_TRY(rb_alloc(&h->part, sizeof(double) * q * q * nch));
+    // FP64 Gram partials (one q x q block per chunk of rows); also the RBFGS / AIP packed core's scratch (3 q x q)
+    RB_TRY(rb_alloc(&h->part, sizeof(double) * q * q * std::max(nch, 3)));
     RB_TRY(rb_alloc(&h->M, sizeof(double) * q * q));
     RB_TRY(rb_alloc(&h->N, sizeof(double) * q * q));
     RB_TRY(rb_alloc(&h->Tm, sizeof(double) * q * q));
@@ -526,7 +527,7 @@ static void rbfgs_step_tc(rb_ctx *h)
     tc_gemm_nk_lo(h->tc, st, acc, TC_A_K, n, q, n, X, n, G, Glo, n, Y, Ylo, n, stp);
     mark(h, "Y=XG");
     tc_gram(h, acc, G, Y, Ylo, h->Nf);  // T = G^T X G
-    launch_core_pack(st, q, h->Mf, h->Nf, h->Bv, h->d_status);
+    launch_core_pack(st, q, h->Mf, h->Nf, h->Bv, h->part, h->d_status);
     mark(h, "grams + core");
     // W = [S | Y] [B1; -Lam], transposed into columns q .. 2q-1 of P's rows and 0 .. q-1 of Q's
     tc_gemm_nk_t(h->tc, st, acc, TC_A_MN, n, q, 2 * q, S, n, h->Bv, 2 * q, P + q, 2 * q, stp);
@@ -557,7 +558,7 @@ static void aip_step_tc(rb_ctx *h)
     tc_gemm_nk_lo(h->tc, st, acc == 3 ? 2 : 1, TC_A_K, n, q, n, A, n, S, nullptr, n, G, Glo, n, stp);  // G = A S
     mark(h, "G=AS");
     tc_gram(h, acc, S, G, Glo, h->Mf);
-    launch_core_pack(st, q, h->Mf, nullptr, h->Bv, h->d_status);  // [Lam; -Lam]
+    launch_core_pack(st, q, h->Mf, nullptr, h->Bv, h->part, h->d_status);  // [Lam; -Lam]
     mark(h, "gram + core");
     // W^T = X^T G (element (m, k) of X^T at X[k + m n])
     tc_gemm_nk_lo(h->tc, st, acc, TC_A_K, n, q, n, X, n, G, Glo, n, Wt, nullptr, n, stp);
@@ -795,11 +796,14 @@ static void ada_step_tc(rb_ctx *h)
     bool tcv = fork && tcv_shape;
     if (tcv && !h->tc2) tcv = (h->tc2 = tc_plan_create(n, q, h->prec)) != nullptr;
     if (tcv && !h->tc3) tcv = (h->tc3 = tc_plan_create(n, q, h->prec)) != nullptr;
-    const bool fuse = tcv && upd == 1 && h->Spart;
+    // AdaRBFGS_cols: S = L[:, C] is a gather of q columns and S~^T S~ = I (distinct coordinates),
+    // so there is no product to fuse into the update and the D chain writes D^-T = I
+    const bool cols = h->sketch == RB_SKETCH_COORD_UNIFORM;
+    const bool fuse = tcv && upd == 1 && h->Spart && !cols;
     // the next step's D chain runs during this step's fused update
     const bool dpipe = fuse;
     const bool d_now = tcv && !(dpipe && h->d_ready);  // this step's D chain still to run (during G)
-    const int rsv_g = (fork && (d_now || !tcv)) ? SIDE_SMS_G : 0;
+    const int rsv_g = (fork && ((d_now && !cols) || !tcv)) ? SIDE_SMS_G : 0;
     // the side stream's Gram products run stream-K on the SIDE_SMS SMs the main GEMMs leave free
     const int side_rsv = std::max(0, tc_num_sms() - side_sms), side_rsv_g = std::max(0, tc_num_sms() - SIDE_SMS_G);
     // sketch buffers: [S~_a | W^T | S~_b]; step k uses S~_a (k even) or S~_b (k odd) when fused
@@ -824,6 +828,8 @@ static void ada_step_tc(rb_ctx *h)
                 h->slo_valid = h->Slo != nullptr;
                 h->sbf_valid = bfterms != 0;
             }
+        } else if (cols) {
+            launch_gather_cols<float>(st, n, q, L, n, h->idx, S, n);  // S = L[:, C] (C ascending, as S~'s columns)
         } else {
             // S = L S~ (A = L, M-contiguous); S~ is exact in TF32, so the split needs only L's two parts
             tc_gemm_nk(h->tc, st, acc == 3 ? 2 : acc, TC_A_MN, n, q, n, L, n, St, n, S, n, stp);
@@ -835,7 +841,12 @@ static void ada_step_tc(rb_ctx *h)
         if (tcv) {  // S~^T S~ -> D^-T into Bv, on the D chain's own stream (unless the previous step did it)
             if (d_now) {
                 cudaStreamWaitEvent(h->st3, h->ev_sk, 0);
-                ada_d_chain(h, St, dofs, side_rsv_g);
+                if (cols) {  // D = I
+                    launch_set_identity<float>(h->st3, q, h->Bv + dofs, 2 * q, 1.f);
+                    cudaEventRecord(h->ev_d, h->st3);
+                } else {
+                    ada_d_chain(h, St, dofs, side_rsv_g);
+                }
                 mark_side(h, h->st3, "@D core done");
             }
         } else {
@@ -1295,6 +1306,12 @@ static void coord_block_matrix(rb_ctx *h, uint64_t k, T *out, int64_t ld)
     launch_coord_trace_draw(h->st, n, q, h->nb, h->P, h->seed, h->stream_id, k, h->blk);
     // 0/1 matrix from the block: column c has a one in row first + c (c < size)
     launch_block_matrix<T>(h->st, n, q, h->blk, out, ld);
+}
+
+void rb_handle_status(rbfgs_t h, int **status, cudaStream_t *st)
+{
+    *status = h->d_status;
+    *st = h->st;
 }
 
 extern "C" rb_status rbfgs_sync(rbfgs_t h)

@@ -4,6 +4,9 @@
 
 constexpr int GRAM_CHUNK = 128;  // rows per FP32 Gram partial (summed in FP64)
 
+// api.cu: a handle's device status word and stream
+void rb_handle_status(rbfgs_t h, int **status, cudaStream_t *st);
+
 // sketch.cu
 template <typename T>
 void launch_gauss_sketch(cudaStream_t, int n, int q, uint64_t seed, uint64_t stream, uint64_t k, T *S, int64_t lds);
@@ -37,8 +40,9 @@ bool launch_core_tr32(cudaStream_t, int q, const float *M, float *Xinv, float *x
 bool launch_core_tr64(cudaStream_t, int q, const float *M, float *xt1, int ld1, float s1, float *xt2, int ld2,
                       float s2, int *status);
 // q <= 64: the RBFGS / AIP core (FP64) from FP32 Gram matrices, packed as the 2q x q B operand
-// [B1; -Lam] (Tf given: RBFGS) or [Lam; -Lam] (Tf null: AIP), ld 2q.
-void launch_core_pack(cudaStream_t, int q, const float *Mf, const float *Tf, float *Bw, int *status);
+// [B1; -Lam] (Tf given: RBFGS) or [Lam; -Lam] (Tf null: AIP), ld 2q; scratch: 3 q^2 doubles.
+void launch_core_pack(cudaStream_t, int q, const float *Mf, const float *Tf, float *Bw, double *scratch,
+                      int *status);
 // out[off + c + i rp] = X[i + c ldx] for i < n, c < q: a column-major panel into rows of pitch rp.
 void launch_rows_from_cols(cudaStream_t, int n, int q, const float *X, int64_t ldx, float *out, int rp, int off);
 template <typename T>

@@ -52,7 +52,24 @@ struct Req {
     double resid = INFINITY;
     int status = RB_OK;
     uint64_t col_seed = 0;
+    int prec = RB_MIXED;     // the form this request runs in (chosen from its tolerance)
+    double best = INFINITY;  // smallest residual seen, and checks since it last fell by 10 %
+    int stale = 0;
+    int floor_limited = 0;
 };
+
+// Form of a request: the server's form, except that a BF16 form serves only tolerances down to
+// 1e-4 (the 3-term BF16 products leave a residual floor near 2e-5 on the request matrices; the
+// 3xTF32 mixed form's is near 7e-6 at n / q = 64).
+int request_prec(int server_prec, double tol)
+{
+    if ((server_prec == RB_BF16X3 || server_prec == RB_BF16) && tol < 1e-4) return RB_MIXED;
+    return server_prec;
+}
+
+// Checks without a 10 % fall of the residual after which a request is finished as floor-limited:
+// the residual then sits at the floor of the request's arithmetic, above its tolerance.
+constexpr int STALL_CHECKS = 8;
 
 double now_s(const std::chrono::steady_clock::time_point &t0)
 {
@@ -97,7 +114,7 @@ static void start_request(rb_srv *s, Req *r)
     o.method = RB_METHOD_ADARBFGS;
     o.sketch = RB_SKETCH_GAUSS;
     o.q = r->q;
-    o.prec = s->prec;
+    o.prec = r->prec;
     o.seed = r->seed;
     rb_status st = RB_OK;
     if (cudaStreamCreateWithFlags(&r->st, cudaStreamNonBlocking) != cudaSuccess) st = RB_ECUDA;
@@ -191,10 +208,21 @@ static void worker_loop(rb_srv *s)
                 } else if (ready) {
                     progressed = true;
                     r->resid = res;
+                    if (res < 0.9 * r->best) {
+                        r->best = res;
+                        r->stale = 0;
+                    } else {
+                        ++r->stale;
+                    }
                     if (res <= r->tol) {
                         done = true;
                     } else if (r->steps >= s->max_iter) {
                         r->status = RB_NOTCONV;
+                        done = true;
+                    } else if (r->stale >= STALL_CHECKS) {  // at the floor of its arithmetic
+                        r->status = RB_NOTCONV;
+                        r->floor_limited = 1;
+                        r->resid = r->best;
                         done = true;
                     } else {
                         const int chunk = std::min(s->check_every, s->max_iter - r->steps);
@@ -237,7 +265,8 @@ extern "C" rb_status rb_srv_create(rb_srv_t *out, size_t hbm_budget_bytes, int m
 {
     if (!out || hbm_budget_bytes == 0 || max_live < 1 || check_every < 1 || check_cols < 1 || max_iter < 1)
         return RB_EINVAL;
-    if (prec != RB_FP32 && prec != RB_TF32 && prec != RB_TF32X3 && prec != RB_MIXED && prec != RB_FP64)
+    if (prec != RB_FP32 && prec != RB_TF32 && prec != RB_TF32X3 && prec != RB_MIXED && prec != RB_FP64 &&
+        prec != RB_BF16 && prec != RB_BF16X3)
         return RB_EINVAL;
     rb_srv *s = new rb_srv();
     s->budget = hbm_budget_bytes;
@@ -267,7 +296,7 @@ extern "C" rb_status rb_srv_submit(rb_srv_t s, int n, const void *A, int a_on_de
     rbfgs_default_opts(&o);
     o.method = RB_METHOD_ADARBFGS;
     o.q = q;
-    o.prec = s->prec;
+    o.prec = request_prec(s->prec, tol);
     size_t bytes = 0;
     if (rbfgs_footprint(n, &o, &bytes) != RB_OK) return RB_EINVAL;
     if (!a_on_device) bytes += (size_t)n * n * (a_is_fp64 ? 8 : 4);  // staging copy at admission
@@ -286,6 +315,7 @@ extern "C" rb_status rb_srv_submit(rb_srv_t s, int n, const void *A, int a_on_de
     r->ldo = ldo;
     r->bytes = bytes;
     r->col_seed = seed ^ 0x9e3779b97f4a7c15ull;
+    r->prec = o.prec;
     {
         std::lock_guard<std::mutex> lk(s->mu);
         if (s->stop) {
@@ -332,6 +362,8 @@ extern "C" rb_status rb_srv_wait(rb_srv_t s, int64_t ticket, double timeout_s, r
     res->queue_s = r->t_admit - r->t_submit;
     res->n = r->n;
     res->q = r->q;
+    res->prec = r->prec;
+    res->floor_limited = r->floor_limited;
     s->reqs.erase(it);
     delete r;
     return RB_OK;

@@ -328,12 +328,14 @@ template void launch_core_rbfgs<double>(cudaStream_t, int, const double *, const
 // 2q x q B operand (ld 2q) of the product that forms the update's panel:
 //   RBFGS (Tf != null): [B1; -Lam], B1 = (Lam + Lam T Lam) / 2, for W = [S | Y] [B1; -Lam];
 //   AIP   (Tf == null): [Lam; -Lam], for V^T = [S | W^T] [Lam; -Lam].
-__global__ void k_core_pack(int q, const float *Mf, const float *Tf, float *Bw, int *status)
+// GB300 runs FP64 at a small fraction of its FP32 rate, so only the factorisation
+// stays on one CTA: k_pack_chol factors M = C C^T and inverts C (FP64, shared
+// memory); then q CTAs form one column each of Lam = C^-T C^-1 and T Lam
+// (k_pack_lam), and of Lam (T Lam) with the packed output (k_pack_out).
+__global__ void k_pack_chol(int q, const float *Mf, double *Cinv, int *status)
 {
     extern __shared__ double sm[];
-    double *a = sm;               // C, then C^-1
-    double *lam = sm + q * q;     // Lam
-    double *tl = sm + 2 * q * q;  // T Lam
+    double *a = sm;  // C, then C^-1
     if (status_bad(status)) return;
     for (int e = threadIdx.x; e < q * q; e += blockDim.x) {
         const int i = e % q, c = e / q;
@@ -345,47 +347,64 @@ __global__ void k_core_pack(int q, const float *Mf, const float *Tf, float *Bw, 
         return;
     }
     smem_tri_inverse(a, q);
-    // Lam = C^-T C^-1: Lam_ij = sum_k Cinv_ki Cinv_kj (k >= max(i, j))
-    for (int e = threadIdx.x; e < q * q; e += blockDim.x) {
-        const int i = e % q, j = e / q;
+    for (int e = threadIdx.x; e < q * q; e += blockDim.x) Cinv[e] = a[e];
+}
+
+// block j, thread i: Lam_ij = sum_{k >= max(i, j)} Cinv_ki Cinv_kj, then (T Lam)_ij (T symmetrised)
+__global__ void k_pack_lam(int q, const double *Cinv, const float *Tf, double *Lam, double *TL, const int *status)
+{
+    __shared__ double lj[128];
+    if (status_bad(status)) return;
+    const int i = threadIdx.x, j = blockIdx.x;
+    if (i < q) {
         double s = 0.0;
-        for (int k = max(i, j); k < q; ++k) s += a[k + i * q] * a[k + j * q];
-        lam[e] = s;
+        for (int k = max(i, j); k < q; ++k) s += Cinv[k + i * q] * Cinv[k + j * q];
+        lj[i] = s;
+        Lam[i + j * q] = s;
     }
     __syncthreads();
-    if (Tf) {
-        for (int e = threadIdx.x; e < q * q; e += blockDim.x) {  // T Lam (T symmetrised)
-            const int i = e % q, j = e / q;
-            double s = 0.0;
-            for (int k = 0; k < q; ++k) s += 0.5 * ((double)Tf[i + k * q] + (double)Tf[k + i * q]) * lam[k + j * q];
-            tl[e] = s;
-        }
-        __syncthreads();
-    }
-    for (int e = threadIdx.x; e < q * q; e += blockDim.x) {
-        const int i = e % q, j = e / q;
-        double top = lam[e];
-        if (Tf) {
-            double s = 0.0;
-            for (int k = 0; k < q; ++k) s += lam[i + k * q] * tl[k + j * q];
-            top = 0.5 * (lam[e] + s);
-        }
-        if (!isfinite(top) || !isfinite(lam[e])) atomicOr(status, ST_NONFINITE);
-        Bw[i + (size_t)j * 2 * q] = (float)top;
-        Bw[q + i + (size_t)j * 2 * q] = (float)-lam[e];
+    if (Tf && i < q) {
+        double s = 0.0;
+        for (int k = 0; k < q; ++k) s += 0.5 * ((double)Tf[i + k * q] + (double)Tf[k + i * q]) * lj[k];
+        TL[i + j * q] = s;
     }
 }
 
-void launch_core_pack(cudaStream_t st, int q, const float *Mf, const float *Tf, float *Bw, int *status)
+// block j, thread i: the packed output column j
+__global__ void k_pack_out(int q, const double *Lam, const double *TL, int with_t, float *Bw, int *status)
 {
-    const size_t smem = sizeof(double) * 3 * q * q;
+    if (status_bad(status)) return;
+    const int i = threadIdx.x, j = blockIdx.x;
+    if (i >= q) return;
+    const double lam = Lam[i + j * q];
+    double top = lam;
+    if (with_t) {
+        double s = 0.0;
+        for (int k = 0; k < q; ++k) s += Lam[i + k * q] * TL[k + j * q];  // (Lam T Lam)_ij
+        top = 0.5 * (lam + s);
+    }
+    if (!isfinite(top) || !isfinite(lam)) atomicOr(status, ST_NONFINITE);
+    Bw[i + (size_t)j * 2 * q] = (float)top;
+    Bw[q + i + (size_t)j * 2 * q] = (float)-lam;
+}
+
+void launch_core_pack(cudaStream_t st, int q, const float *Mf, const float *Tf, float *Bw, double *scratch,
+                      int *status)
+{
+    const size_t smem = sizeof(double) * q * q;
     static bool attr_set = false;
     if (!attr_set) {
-        cudaFuncSetAttribute(k_core_pack, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        cudaFuncSetAttribute(k_pack_chol, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
         attr_set = true;
     }
+    double *Cinv = scratch, *Lam = scratch + (size_t)q * q, *TL = scratch + 2 * (size_t)q * q;
+    const int tpb = ((q + 31) / 32) * 32;
     rb_count_launch();
-    k_core_pack<<<1, 512, smem, st>>>(q, Mf, Tf, Bw, status);
+    k_pack_chol<<<1, 512, smem, st>>>(q, Mf, Cinv, status);
+    rb_count_launch();
+    k_pack_lam<<<q, tpb, 0, st>>>(q, Cinv, Tf, Lam, TL, status);
+    rb_count_launch();
+    k_pack_out<<<q, tpb, 0, st>>>(q, Lam, TL, Tf != nullptr, Bw, status);
 }
 
 // ---------------------------------------------------------------------------

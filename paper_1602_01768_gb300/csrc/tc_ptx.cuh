@@ -44,19 +44,25 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity)
 }
 
 // Bounded wait: false (and ST_TIMEOUT recorded, abort flag raised) when the
-// phase does not complete within WAIT_LIMIT_CYCLES.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err, volatile int *abort_flag)
+// phase does not complete within `limit` SM cycles.
+__device__ __forceinline__ bool mbar_wait_for(uint32_t bar, uint32_t parity, int *err, volatile int *abort_flag,
+                                              long long limit)
 {
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
         if (*abort_flag) return false;
-        if (clock64() - t0 > WAIT_LIMIT_CYCLES) {
+        if (clock64() - t0 > limit) {
             if (err) atomicOr(err, ST_TIMEOUT);
             *abort_flag = 1;
             return false;
         }
     }
     return true;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *err, volatile int *abort_flag)
+{
+    return mbar_wait_for(bar, parity, err, abort_flag, WAIT_LIMIT_CYCLES);
 }
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar)

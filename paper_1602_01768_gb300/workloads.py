@@ -126,6 +126,25 @@ def spd_uniform_gram(n: int, seed: int):
     return np.asfortranarray(0.5 * (A + A.T))
 
 
+def spd_uniform_gram_torch(n: int, seed: int, device):
+    """Same construction as ``spd_uniform_gram`` on a torch device, FP32 (TF32 off): the large
+    sizes of Sec. 10.1, where a CPU build would take hours."""
+    import torch
+
+    g = torch.Generator(device=device)
+    g.manual_seed(seed)
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = False
+    try:
+        Bm = torch.rand(n, n, generator=g, device=device, dtype=torch.float32)
+        A = Bm.t() @ Bm
+        del Bm
+        A = 0.5 * (A + A.t())
+        return A.contiguous()
+    finally:
+        torch.backends.cuda.matmul.allow_tf32 = prev
+
+
 # --------------------------------------------------------------------------
 # The five workloads (sizes, spectra and sketch choices).
 # --------------------------------------------------------------------------

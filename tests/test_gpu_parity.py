@@ -364,11 +364,11 @@ def test_adarbfgs_tf32_single_pass_parity():
         B.rbfgs_destroy(h)
 
 
-@pytest.mark.parametrize("prec", [B.RB_MIXED, B.RB_TF32X3])
+@pytest.mark.parametrize("prec", [B.RB_MIXED, B.RB_TF32X3, B.RB_BF16X3])
 def test_adarbfgs_cols_tensor_core_parity(prec):
-    # AdaRBFGS_cols (q uniform distinct coordinates, Sec. 10) through the tensor-core step: the
-    # 0/1 sketch is exact in TF32, so S = L[:, C] carries only L's own FP32 rounding.  Two steps
-    # from a general L: 3xTF32 <= 2e-5; mixed within 3e-3 of the change (single-pass correction).
+    # AdaRBFGS_cols (q uniform distinct coordinates, Sec. 10) through the tensor-core step: S = L[:, C]
+    # is a gather (exact) and S~^T S~ = I, so D = I.  Two steps from a general L: 3xTF32 <= 2e-5;
+    # mixed and BF16x3 within 3e-3 of the change (single-pass correction).
     n, q = 1024, 32
     A = wl.c2_matrix(n=n).astype(np.float32).astype(np.float64)
     rng = np.random.default_rng(8)
@@ -644,6 +644,38 @@ def test_indefinite_matrix_reports_notspd_and_keeps_iterate():
         assert np.array_equal(export(h, n, B.RB_FP64, B.RB_WHAT_L), np.eye(n))
     finally:
         B.rbfgs_destroy(h)
+
+
+def test_bounded_wait_runs_out_and_leaves_the_iterate():
+    # a kernel waits on an mbarrier that nothing completes (no copy or MMA in flight) with a limit
+    # of 2e6 SM cycles (about a millisecond): the wait gives up, the handle's status word records the
+    # timeout, later steps leave L untouched, the next synchronising call reports RB_ETIMEOUT, and a
+    # fresh handle on the same device then steps normally
+    n, q = 256, 32
+    A = wl.c2_matrix(n=n).astype(np.float32).astype(np.float64)
+    h = _handle(A, B.RB_METHOD_ADARBFGS, B.RB_SKETCH_GAUSS, q, B.RB_MIXED, seed=28)
+    try:
+        B.adarbfgs_step(h, 3)
+        B.rbfgs_sync(h)
+        L0 = export(h, n, B.RB_MIXED, B.RB_WHAT_L)
+        B.rbfgs_wait_selftest(h, 2_000_000)
+        B.adarbfgs_step(h, 2)
+        with pytest.raises(B.RbfgsError) as e:
+            B.rbfgs_sync(h)
+        assert e.value.status == B.RB_ETIMEOUT
+        assert np.array_equal(export(h, n, B.RB_MIXED, B.RB_WHAT_L), L0)
+    finally:
+        B.rbfgs_destroy(h)
+    h = _handle(A, B.RB_METHOD_ADARBFGS, B.RB_SKETCH_GAUSS, q, B.RB_MIXED, seed=28)
+    try:
+        B.adarbfgs_step(h, 3)
+        B.rbfgs_sync(h)
+        assert np.array_equal(export(h, n, B.RB_MIXED, B.RB_WHAT_L), L0)  # the same three steps
+    finally:
+        B.rbfgs_destroy(h)
+    with pytest.raises(B.RbfgsError) as e:
+        B.rbfgs_wait_selftest(None, 10)
+    assert e.value.status == B.RB_EINVAL
 
 
 def test_invalid_arguments_are_rejected():

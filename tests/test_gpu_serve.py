@@ -84,3 +84,24 @@ def test_oversize_request_is_rejected():
         assert e.value.status == B.RB_ENOMEM
     finally:
         B.rb_srv_destroy(s)
+
+
+def test_form_per_tolerance_and_floor_limited_requests():
+    # a BF16x3 server runs tol >= 1e-4 in BF16x3 and smaller tolerances in the 3xTF32 mixed form; a
+    # tolerance below what FP32 storage reaches (1e-9) finishes as floor-limited (RB_NOTCONV) well
+    # before max_iter, with the floor it reached, which the oracle confirms in FP64
+    n = 384
+    s = B.rb_srv_create(8 << 30, 8, B.RB_BF16X3, 16, 128, 20000)
+    try:
+        A, Ah, out = _req(n, 81)
+        _, Ah2, out2 = _req(n, 81)
+        t1 = _submit(s, Ah, out, n, 1e-4, 90)
+        t2 = _submit(s, Ah2, out2, n, 1e-9, 91)
+        r1, r2 = B.rb_srv_wait(s, t1), B.rb_srv_wait(s, t2)
+        assert r1.status == B.RB_OK and r1.prec == B.RB_BF16X3 and not r1.floor_limited
+        assert r2.status == B.RB_NOTCONV and r2.prec == B.RB_MIXED and r2.floor_limited
+        assert r2.iters < 20000 and r2.resid < 1e-4
+        r64 = orc.residual_factored(A.astype(np.float64), out2.numpy().T.astype(np.float64))
+        assert r64 <= 3 * r2.resid, (r64, r2.resid)
+    finally:
+        B.rb_srv_destroy(s)
