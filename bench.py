@@ -504,6 +504,28 @@ def run_exp1(B, wl, timed, st):
     return res
 
 
+def l2_probe_gbs():
+    """L2 bandwidth probe: device copies of a 32 MB FP32 buffer into another (64 MB in all, resident in
+    the 126 MB L2 after the first pass), 20 back to back between two CUDA events, read + write bytes
+    over their time, best of 5."""
+    import torch
+
+    x = torch.ones(8 << 20, device="cuda")
+    y = torch.empty_like(x)
+    for _ in range(3):
+        y.copy_(x)
+    best = float("inf")
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(20):
+            y.copy_(x)
+        e1.record()
+        torch.cuda.synchronize()
+        best = min(best, e0.elapsed_time(e1) / 1e3 / 20)
+    return 2 * x.numel() * 4 / best / 1e9
+
+
 def run_batched(B, wl, args):
     """512 uneven SPD problems, coordinate RBFGS, one persistent launch per round of 100 steps."""
     import numpy as np
@@ -513,20 +535,50 @@ def run_batched(B, wl, args):
     devs = [torch.from_numpy(np.ascontiguousarray(A.T)).float().cuda() for A, _, _ in probs]
     n = [A.shape[0] for A, _, _ in probs]
     q = [qq for _, qq, _ in probs]
+    t0 = time.perf_counter()
     b = B.rb_batch_create(n, [d.data_ptr() for d in devs], n, False, q, 4,
                           stream=torch.cuda.current_stream().cuda_stream)
+    create_s = time.perf_counter() - t0
+    tile = B.rb_batch_tile(b)
     B.rb_batch_step(b, 10)  # warm-up (also captures the round graph shape)
     torch.cuda.synchronize()
+    tol = 1e-5
     t0 = time.perf_counter()
-    rc, iters, resid, status, nconv = B.rb_batch_solve(b, len(n), 1e-5, args.batch_steps, 100, 16)
+    rc, iters, resid, status, nconv = B.rb_batch_solve(b, len(n), tol, args.batch_steps, 100, 16)
     wall = time.perf_counter() - t0
     B.rb_batch_destroy(b)
     steps = sum(iters)
+    # bytes a problem-step moves: X read by Y = X A[:, C] (n^2), A[:, C] read for Y and for T
+    # (2 n q), X's columns and rows C read and written (4 n q)
+    moved = sum(it * 4 * (ni * ni + 6 * ni * qi) for it, ni, qi in zip(iters, n, q))
+    achieved = moved / wall / 1e9
+    l2 = l2_probe_gbs()
+    # unconverged problems: steps predicted by the rate of coordinate sampling with trace
+    # probabilities, rho = 1 - lambda_min / Tr A (Sec. 7.2; lambda_max = 1, lambda_min = 1 / kappa), and
+    # whether tol lies below the FP32-storage floor of the exact inverse (~1.4e-9 kappa: 1.4e-5 at
+    # kappa = 1e4, the floor the survey measured at n = 512)
+    unconv = []
+    for i, ((A, qi, kappa), it, r) in enumerate(zip(probs, iters, resid)):
+        if r <= tol:
+            continue
+        rho = 1.0 - (1.0 / kappa) / float(np.trace(A))
+        more = math.log(max(r, tol) / tol) / -math.log(rho) if rho < 1 else float("inf")
+        unconv.append({"n": n[i], "q": qi, "kappa": kappa, "iters": it, "resid": r,
+                       "predicted_total_steps": it + more, "below_fp32_floor": 1.4e-9 * kappa > tol})
     return {"workload": f"{len(n)} problems, n log-uniform in [32, 1024], kappa log-uniform in [1e1, 1e4], "
-                        "coordinate blocks q in {4,8,16,32} with trace probabilities, tol 1e-5, "
+                        f"coordinate blocks q in {{4,8,16,32}} with trace probabilities, tol {tol:g}, "
                         f"at most {args.batch_steps} steps each",
+            "tile_threads_per_cta": tile, "create_with_autotune_s": create_s,
             "converged": nconv, "problem_steps_per_s": steps / wall, "wall_s": wall,
-            "median_resid": float(np.median(resid)), "max_resid": float(np.max(resid))}
+            "roofline": {"bound": "l2", "achieved": achieved, "peak": l2, "unit": "GB/s", "frac": achieved / l2,
+                         "peak_kind": "measured L2 copy probe (64 MB working set)",
+                         "bytes_per_problem_step": "4 (n^2 + 6 n q)"},
+            "median_resid": float(np.median(resid)), "max_resid": float(np.max(resid)),
+            "unconverged": {"count": len(unconv),
+                            "below_fp32_floor": sum(u["below_fp32_floor"] for u in unconv),
+                            "median_predicted_total_steps": (statistics.median(u["predicted_total_steps"]
+                                                                                for u in unconv) if unconv else 0),
+                            "max_predicted_total_steps": max((u["predicted_total_steps"] for u in unconv), default=0)}}
 
 
 def run_phases(args):

@@ -333,6 +333,15 @@ rb_status rb_batch_solve(rb_batch_t b, double tol, int max_iter, int check_every
                          double *resid, int *status, int *nconverged);
 /* X_i into out_dev (FP32, ld >= n_i); asynchronous. */
 rb_status rb_batch_export(rb_batch_t b, int i, void *out_dev, int64_t ld);
+/* Tile shape of the step kernel: threads per CTA, 256 or 512 (NMAX / threads rows of
+ * a problem per thread).  rb_batch_create picks it with an autotuner: the first batch
+ * for a key (largest n rounded up to a power of two, largest q, precision) times two
+ * steps of its problems with each shape, keeps the faster (the trial steps are undone)
+ * and caches the choice for later batches of the same key.  Every sum runs in an order
+ * that does not depend on the shape, so the iterates are the same for either;
+ * rb_batch_set_tile overrides the choice. */
+rb_status rb_batch_tile(rb_batch_t b, int *threads_per_cta);
+rb_status rb_batch_set_tile(rb_batch_t b, int threads_per_cta);
 rb_status rb_batch_destroy(rb_batch_t b);
 
 /*

@@ -76,6 +76,8 @@ _SIGS = {
                                  C.c_void_p, C.c_void_p]),
     "rb_batch_export": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64]),
     "rb_batch_destroy": (C.c_int, [C.c_void_p]),
+    "rb_batch_tile": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "rb_batch_set_tile": (C.c_int, [C.c_void_p, C.c_int]),
     "rbfgs_residual_start": (C.c_int, [C.c_void_p, C.c_int, C.c_uint64]),
     "rbfgs_residual_poll": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "rbfgs_footprint": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p]),
@@ -308,6 +310,16 @@ def rb_batch_solve(b, count, tol, max_iter, check_every, ncols):
 
 def rb_batch_export(b, i, out_dev, ld):
     return _check(_lib().rb_batch_export(b, i, _p(out_dev), ld), "rb_batch_export")
+
+
+def rb_batch_tile(b):
+    t = C.c_int()
+    _check(_lib().rb_batch_tile(b, C.byref(t)), "rb_batch_tile")
+    return t.value
+
+
+def rb_batch_set_tile(b, threads_per_cta):
+    return _check(_lib().rb_batch_set_tile(b, threads_per_cta), "rb_batch_set_tile")
 
 
 def rb_batch_destroy(b):

@@ -16,6 +16,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <numeric>
 #include <vector>
 
@@ -23,10 +25,9 @@
 
 namespace {
 
-constexpr int BT = 256;     // threads per CTA
+constexpr int BT = 256;     // threads per CTA of the residual kernel
 constexpr int QMAX = 32;    // largest block
 constexpr int NMAX = 1024;  // largest problem
-constexpr int RPT = NMAX / BT;  // rows per thread
 
 struct BatchDev {
     const float *A;
@@ -66,8 +67,15 @@ __device__ void draw_block(const BatchDev &d, int p, int n, int q, uint64_t k, i
     size = ((lo + 1) * q <= n) ? q : n - lo * q;
 }
 
-__global__ void __launch_bounds__(BT, 1) k_batch_rbfgs(BatchDev d, int steps)
+// TB threads per CTA (the tile shape the autotuner picks: 256 or 512), NMAX / TB rows of
+// every problem per thread.  The order of every sum (Y row by row over k, T element by
+// element over i, the q x q products element by element) does not depend on TB, so
+// the iterates are the same for every shape.
+template <int TB>
+__global__ void __launch_bounds__(TB, 1) k_batch_rbfgs(BatchDev d, int steps)
 {
+    constexpr int BT = TB;
+    constexpr int RPT = NMAX / TB;  // rows per thread
     extern __shared__ float bsm[];
     float *Ys = bsm;                                  // n x q, ld n + 1 (Y, then W)
     float *Gt = Ys + (NMAX + 1) * QMAX;               // 32 x QMAX tile of G rows
@@ -149,13 +157,36 @@ __global__ void __launch_bounds__(BT, 1) k_batch_rbfgs(BatchDev d, int steps)
                     if (c < q) Ys[i + c * ldy] = acc[r][c];
             }
             __syncthreads();
-            // T = G^T Y (FP32 over n rows)
-            for (int e = tid; e < q * q; e += BT) {
-                const int a = e % q, b = e / q;
-                float t = 0.f;
-                if (a < size)
-                    for (int i = 0; i < n; ++i) t = fmaf(A[i + (int64_t)(first + a) * n], Ys[i + b * ldy], t);
-                Tm[a + b * QMAX] = t;
+            // T = G^T Y (FP32 over n rows, i ascending): G's rows staged 32 at a time like the
+            // Y pass, each (a, b) summed by one thread
+            {
+                constexpr int NP = (QMAX * QMAX + BT - 1) / BT;
+                float t[NP];
+#pragma unroll
+                for (int u = 0; u < NP; ++u) t[u] = 0.f;
+                for (int i0 = 0; i0 < n; i0 += 32) {
+                    __syncthreads();
+                    for (int e = tid; e < 32 * QMAX; e += BT) {
+                        const int kk = e % 32, c = e / 32;
+                        Gt[kk * QMAX + c] = (i0 + kk < n && c < size) ? A[(i0 + kk) + (int64_t)(first + c) * n] : 0.f;
+                    }
+                    __syncthreads();
+                    const int kend = min(32, n - i0);
+#pragma unroll
+                    for (int u = 0; u < NP; ++u) {
+                        const int e = tid + u * BT;
+                        if (e < q * q) {
+                            const int a = e % q, b = e / q;
+                            const float *yb = Ys + i0 + b * ldy;
+                            for (int kk = 0; kk < kend; ++kk) t[u] = fmaf(Gt[kk * QMAX + a], yb[kk], t[u]);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < NP; ++u) {
+                    const int e = tid + u * BT;
+                    if (e < q * q) Tm[(e % q) + (e / q) * QMAX] = t[u];
+                }
             }
             // FP64 Cholesky of M (warp 0, row per lane)
             if (tid < 32) {
@@ -207,7 +238,7 @@ __global__ void __launch_bounds__(BT, 1) k_batch_rbfgs(BatchDev d, int steps)
             }
             __syncthreads();
             // B1 = (Lam + Lam T Lam) / 2: first Tm <- T Lam (in place via registers), then Lam (T Lam)
-            float tl[4];
+            float tl[(QMAX * QMAX + BT - 1) / BT];
             int ne = 0;
             for (int e = tid; e < q * q; e += BT, ++ne) {
                 const int a = e % q, b = e / q;
@@ -339,6 +370,7 @@ struct rb_batch {
     int *d_n = nullptr, *d_q = nullptr, *d_nb = nullptr, *d_order = nullptr, *d_active = nullptr,
         *d_status = nullptr, *d_queue = nullptr;
     double *d_resid = nullptr;
+    int tb = 256;                // threads per CTA of the step kernel (picked by the autotuner)
     int *h_active = nullptr;     // pinned
     double *h_resid = nullptr;   // pinned
     int *h_status = nullptr;     // pinned
@@ -383,6 +415,98 @@ static void batch_free(rb_batch *b)
     if (b->h_resid) cudaFreeHost(b->h_resid);
     if (b->h_status) cudaFreeHost(b->h_status);
     delete b;
+}
+
+static void launch_batch_step(rb_batch *b, cudaStream_t st, int steps)
+{
+    if (b->tb == 512)
+        k_batch_rbfgs<512><<<b->grid, 512, batch_smem(), st>>>(b->dev(), steps);
+    else
+        k_batch_rbfgs<256><<<b->grid, 256, batch_smem(), st>>>(b->dev(), steps);
+}
+
+// Tile-shape autotuner.  Candidates: 256 or 512 threads per CTA (4 or 2 rows of each
+// problem per thread).  Keyed by the batch's largest n (rounded up to a power of two),
+// its largest q and the precision (FP32): the first batch of a key times two steps of
+// every problem with each shape and keeps the faster; later batches of the key reuse it.
+// The iterates do not depend on the shape, so the choice changes only the speed.  The
+// trial steps are undone (X = I, k = 0, status cleared) before the batch is returned.
+std::mutex g_tune_mu;
+std::map<uint64_t, int> g_tune;
+
+static rb_status batch_autotune(rb_batch *b)
+{
+    int nmax = 1, qmax = 1;
+    for (int i = 0; i < b->count; ++i) {
+        nmax = std::max(nmax, b->n[i]);
+        qmax = std::max(qmax, b->q[i]);
+    }
+    int nb2 = 1;
+    while (nb2 < nmax) nb2 <<= 1;
+    const uint64_t key = ((uint64_t)nb2 << 32) | ((uint64_t)qmax << 8) | (uint64_t)RB_FP32;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune.find(key);
+        if (it != g_tune.end()) {
+            b->tb = it->second;
+            return RB_OK;
+        }
+    }
+    cudaStream_t st = b->st;
+    cudaEvent_t e0, e1;
+    RB_CUDA(cudaEventCreate(&e0));
+    RB_CUDA(cudaEventCreate(&e1));
+    float best = INFINITY;
+    int best_tb = 256;
+    for (int tb : {256, 512}) {
+        b->tb = tb;
+        cudaMemsetAsync(b->d_queue, 0, sizeof(int), st);
+        cudaEventRecord(e0, st);
+        rb_count_launch();
+        launch_batch_step(b, st, 2);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return RB_ECUDA;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            best_tb = tb;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    b->tb = best_tb;
+    // undo the trial steps
+    rb_count_launch();
+    k_batch_identity<<<dim3(64, b->count), 256, 0, st>>>(b->dev());
+    RB_CUDA(cudaMemsetAsync(b->k, 0, sizeof(uint64_t) * b->count, st));
+    RB_CUDA(cudaMemsetAsync(b->d_status, 0, sizeof(int) * b->count, st));
+    RB_CUDA(cudaStreamSynchronize(st));
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = best_tb;
+    return RB_OK;
+}
+
+extern "C" rb_status rb_batch_tile(rb_batch_t b, int *threads_per_cta)
+{
+    if (!b || !threads_per_cta) return RB_EINVAL;
+    *threads_per_cta = b->tb;
+    return RB_OK;
+}
+
+extern "C" rb_status rb_batch_set_tile(rb_batch_t b, int threads_per_cta)
+{
+    if (!b || (threads_per_cta != 256 && threads_per_cta != 512)) return RB_EINVAL;
+    if (threads_per_cta != b->tb && b->gexec) {  // the captured round launches the old shape
+        cudaGraphExecDestroy(b->gexec);
+        b->gexec = nullptr;
+    }
+    b->tb = threads_per_cta;
+    return RB_OK;
 }
 
 template <typename P>
@@ -511,13 +635,19 @@ extern "C" rb_status rb_batch_create(rb_batch_t *out, int count, const int *n, c
     }
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_batch_rbfgs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_smem());
+        cudaFuncSetAttribute(k_batch_rbfgs<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_smem());
+        cudaFuncSetAttribute(k_batch_rbfgs<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_smem());
         attr = true;
     }
     int sms = 0, dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     b->grid = std::max(1, std::min(count, sms > 0 ? sms : 148));
+    const rb_status ts = batch_autotune(b);
+    if (ts != RB_OK) {
+        batch_free(b);
+        return ts;
+    }
     *out = b;
     return RB_OK;
 }
@@ -541,7 +671,7 @@ static rb_status batch_round(rb_batch *b, int steps, int ncols, uint64_t col_see
         if (ok) {
             cudaMemcpyAsync(b->d_active, b->h_active, sizeof(int) * b->count, cudaMemcpyHostToDevice, cs);
             cudaMemsetAsync(b->d_queue, 0, sizeof(int), cs);
-            if (steps > 0) k_batch_rbfgs<<<b->grid, BT, batch_smem(), cs>>>(b->dev(), steps);
+            if (steps > 0) launch_batch_step(b, cs, steps);
             if (ncols > 0) {
                 k_batch_resid<<<b->count, BT, 0, cs>>>(b->dev(), ncols, col_seed, b->d_resid);
                 cudaMemcpyAsync(b->h_resid, b->d_resid, sizeof(double) * b->count, cudaMemcpyDeviceToHost, cs);

@@ -94,3 +94,24 @@ def test_batch_rejects_bad_sizes():
         B.rb_batch_create([8], [A.data_ptr()], [8], False, [6], 0, stream=stream_ptr())  # q not a multiple of 4
     with pytest.raises(B.RbfgsError):
         B.rb_batch_create([2000], [A.data_ptr()], [2000], False, [8], 0, stream=stream_ptr())  # n > 1024
+
+
+def test_tile_shapes_give_the_same_iterates():
+    # the autotuner's candidates (256 and 512 threads per CTA) sum in the same order, so a batch
+    # forced to either shape produces bit-identical iterates; the autotuner picked one of them
+    probs = _problems(6, 9)
+    b1, n = _create(probs, 13)
+    b2, _ = _create(probs, 13)
+    try:
+        assert B.rb_batch_tile(b1) in (256, 512)
+        B.rb_batch_set_tile(b1, 256)
+        B.rb_batch_set_tile(b2, 512)
+        B.rb_batch_step(b1, 40)
+        B.rb_batch_step(b2, 40)
+        for i in range(len(probs)):
+            assert np.array_equal(_export(b1, i, n[i]), _export(b2, i, n[i])), i
+        with pytest.raises(B.RbfgsError):
+            B.rb_batch_set_tile(b1, 384)
+    finally:
+        B.rb_batch_destroy(b1)
+        B.rb_batch_destroy(b2)
