@@ -84,6 +84,8 @@ def parse():
     ap.add_argument("--no-compare", action="store_true", help="skip the n = 4096 method comparison")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--batch-steps", type=int, default=2000)
+    ap.add_argument("--method", choices=["adarbfgs", "rbfgs", "aip"], default="adarbfgs",
+                    help="method of the phases / plain modes (rbfgs and aip run the n = 4096 ridge Hessian, q = 64)")
     ap.add_argument("--mode", choices=["bench", "phases", "plain"], default="bench",
                     help="phases: per-phase CUDA-event times of single AdaRBFGS steps (--prec may list forms, "
                          "comma-separated); plain: --warmup + --steps steps with no events, the form to put "
@@ -589,24 +591,31 @@ def run_phases(args):
     from paper_1602_01768_gb300 import workloads as wl
 
     torch.cuda.set_device(0)
-    A = wl.c3_matrix(n=args.n, device="cuda")
+    method = {"adarbfgs": B.RB_METHOD_ADARBFGS, "rbfgs": B.RB_METHOD_RBFGS, "aip": B.RB_METHOD_AIP}[args.method]
+    step = {"adarbfgs": B.adarbfgs_step, "rbfgs": B.rbfgs_step, "aip": B.aip_step}[args.method]
+    if method == B.RB_METHOD_ADARBFGS:
+        n, q = args.n, args.q
+        A = wl.c3_matrix(n=n, device="cuda")
+    else:
+        n, q = (args.n if args.n != N_DEFAULT else 4096), (args.q if args.q != Q_DEFAULT else 64)
+        A = wl.c2_matrix(n=n, device="cuda")
     st = torch.cuda.current_stream().cuda_stream
     for pn in args.prec.split(","):
-        o = B.make_opts(method=B.RB_METHOD_ADARBFGS, sketch=B.RB_SKETCH_GAUSS, q=args.q, prec=B.PREC[pn], seed=1,
+        o = B.make_opts(method=method, sketch=B.RB_SKETCH_GAUSS, q=q, prec=B.PREC[pn], seed=1,
                         core_fp64=CORE_OPT[args.core])
-        h = B.rbfgs_init(args.n, A.data_ptr(), args.n, False, o, st)
-        B.adarbfgs_step(h, args.warmup)
+        h = B.rbfgs_init(n, A.data_ptr(), n, False, o, st)
+        step(h, args.warmup)
         if args.mode == "plain":
-            B.adarbfgs_step(h, args.steps)
+            step(h, args.steps)
             B.rbfgs_sync(h)
-            print(json.dumps({"prec": pn, "n": args.n, "q": args.q, "steps": args.steps}), flush=True)
+            print(json.dumps({"method": args.method, "prec": pn, "n": n, "q": q, "steps": args.steps}), flush=True)
         else:
             prof = {}
             for _ in range(args.steps):
                 for name, ms in B.rbfgs_profile_step(h):
                     prof.setdefault(name, []).append(ms)
             ph = {k: round(statistics.median(v), 4) for k, v in prof.items()}
-            print(json.dumps({"prec": pn, "n": args.n, "q": args.q, "phases_ms": ph,
+            print(json.dumps({"method": args.method, "prec": pn, "n": n, "q": q, "phases_ms": ph,
                               "step_ms": round(sum(v for k, v in ph.items() if not k.startswith("@")), 4)}),
                   flush=True)
         B.rbfgs_destroy(h)
