@@ -86,8 +86,20 @@ struct Cfg {
     static constexpr int STAGES_A = STAGES_SMEM < STAGES_TMEM ? STAGES_SMEM : STAGES_TMEM;
     static constexpr int STAGES = STAGES_A > 8 ? 8 : STAGES_A;
     static constexpr int TMEM_COLS = CONVERT ? 512 : (2 * BN < 32 ? 32 : 2 * BN);
-    static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 /*align*/ + 512 /*barriers*/;
+    // BF16 products run three decoupled rings: NA FP32 A slots in shared memory, freed by the
+    // converter as soon as it has written the tile's BF16 parts into TMEM (so A streams NA
+    // k-blocks deep), NBS slots of B's BF16 parts, freed when their MMAs complete, and NT TMEM
+    // stages of A, freed when their MMAs complete.  Otherwise one ring of STAGES [A | B | B lo]
+    // stages, each freed when its MMAs complete.
+    static constexpr bool SPLIT = BF != 0;
+    static constexpr int NA = SPLIT ? 3 : 0;
+    static constexpr int NBS = SPLIT ? 3 : 0;
+    static constexpr int NT = SPLIT ? (STAGES_TMEM < 4 ? STAGES_TMEM : 4) : 0;
+    static constexpr int B2_BYTES = B_BYTES * (TERMS == 3 ? 2 : 1);  // B and its lo part
+    static constexpr int RING_BYTES = SPLIT ? NA * A_BYTES + NBS * B2_BYTES : STAGES * STAGE_BYTES;
+    static constexpr int SMEM = RING_BYTES + 1024 /*align*/ + 512 /*barriers*/;
     static_assert(STAGES >= 2, "pipeline needs two stages");
+    static_assert(!SPLIT || (NT >= 2 && RING_BYTES <= 200 * 1024), "BF16 rings");
     static_assert(!BF || (AMN == 0 && TERMS != 2), "BF16 products: K-contiguous A, 1 or 3 terms");
 };
 
@@ -195,11 +207,17 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     if (status_bad(status)) return;  // uniform: every thread reads the same word
 
     unsigned char *smem = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char *bar_area = smem + STAGES * CF::STAGE_BYTES;
+    unsigned char *bar_area = smem + CF::RING_BYTES;
+    // one ring: full / conv / empty per stage.  BF16 rings: full / empty per A slot (NA), conv /
+    // tempty per TMEM stage (NT), bfull / bempty per B slot (NBS)
+    constexpr int NFULL = CF::SPLIT ? CF::NA : STAGES, NCONV = CF::SPLIT ? CF::NT : STAGES;
     uint64_t *full = (uint64_t *)bar_area;
-    uint64_t *conv = full + STAGES;
-    uint64_t *empty = conv + STAGES;
-    uint64_t *chunk_full = empty + STAGES;  // [2] accumulator b holds a finished K chunk
+    uint64_t *conv = full + NFULL;
+    uint64_t *empty = conv + NCONV;
+    uint64_t *bfull = empty + NFULL;
+    uint64_t *bempty = bfull + CF::NBS;
+    uint64_t *tempty = bempty + CF::NBS;
+    uint64_t *chunk_full = tempty + CF::NT;  // [2] accumulator b holds a finished K chunk
     uint64_t *chunk_free = chunk_full + 2;  // [2] accumulator b drained
     uint32_t *tmem_slot = (uint32_t *)(chunk_free + 2);
     volatile int *abort_flag = (volatile int *)(tmem_slot + 1);
@@ -215,11 +233,16 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     const int t_b = u_b / nkb, kb_b = u_b - t_b * nkb;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < STAGES; ++s) {
+        for (int s = 0; s < NFULL; ++s) {
             mbar_init(smem_u32(&full[s]), 1);
-            mbar_init(smem_u32(&conv[s]), 128);
-            mbar_init(smem_u32(&empty[s]), 1);
+            mbar_init(smem_u32(&empty[s]), CF::SPLIT ? 128 : 1);  // BF16: freed by the 128 converter threads
         }
+        for (int s = 0; s < NCONV; ++s) mbar_init(smem_u32(&conv[s]), 128);
+        for (int s = 0; s < CF::NBS; ++s) {
+            mbar_init(smem_u32(&bfull[s]), 1);
+            mbar_init(smem_u32(&bempty[s]), 1);
+        }
+        for (int s = 0; s < CF::NT; ++s) mbar_init(smem_u32(&tempty[s]), 1);
         for (int b = 0; b < 2; ++b) {
             mbar_init(smem_u32(&chunk_full[b]), 1);
             mbar_init(smem_u32(&chunk_free[b]), 128);
@@ -238,9 +261,11 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;  // accumulators: columns [0, 2 BN); A stages after them
 
-    auto stage_a = [&](int s) { return smem + s * CF::STAGE_BYTES; };
-    auto stage_b = [&](int s) { return smem + s * CF::STAGE_BYTES + CF::A_BYTES; };
-    auto stage_blo = [&](int s) { return smem + s * CF::STAGE_BYTES + CF::A_BYTES + CF::B_BYTES; };
+    auto stage_a = [&](int s) { return CF::SPLIT ? smem + s * CF::A_BYTES : smem + s * CF::STAGE_BYTES; };
+    auto stage_b = [&](int s) {
+        return CF::SPLIT ? smem + CF::NA * CF::A_BYTES + s * CF::B2_BYTES : smem + s * CF::STAGE_BYTES + CF::A_BYTES;
+    };
+    auto stage_blo = [&](int s) { return stage_b(s) + CF::B_BYTES; };
     auto a_col = [&](int s) { return (uint32_t)(CF::NACC * CF::ACC_COLS + s * CF::A_TMEM_COLS); };
 
     // registers: the drain warps keep BN running sums per thread; the single-thread
@@ -249,7 +274,36 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
     constexpr int REG_LOW = GEMM_REG_LOW, REG_DRAIN = GEMM_REG_DRAIN;
     if (warp < 4) {
         asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(REG_LOW));
-        if (warp == 0) {
+        if (CF::SPLIT && (warp == 0 || warp == 2)) {
+            // ---------------- TMA producers: A ring (warp 0), B ring (warp 2) ----------------
+            if (lane == 0) {
+                const bool ring_a = warp == 0;
+                const int nslot = ring_a ? CF::NA : CF::NBS;
+                uint64_t *f = ring_a ? full : bfull, *e = ring_a ? empty : bempty;
+                int t = t_b, kb = kb_b, m0 = (t % mt) * BM, n0 = (t / mt) * BN;
+                for (int i = 0; i < nk; ++i) {
+                    const int s = i % nslot;
+                    if (i >= nslot && !mbar_wait(smem_u32(&e[s]), ((i / nslot) - 1) & 1, err, abort_flag)) break;
+                    const uint32_t fb = smem_u32(&f[s]);
+                    const int k = kb * CF::BKE;
+                    if (ring_a) {  // two 128 x 32 FP32 boxes per 64-wide k-block
+                        mbar_expect_tx(fb, CF::A_BYTES);
+                        tma_load_2d(smem_u32(stage_a(s)), &tmA, k, m0, fb);
+                        tma_load_2d(smem_u32(stage_a(s) + A_TILE_BYTES), &tmA, k + BK, m0, fb);
+                    } else {
+                        mbar_expect_tx(fb, CF::B2_BYTES);
+                        tma_load_2d(smem_u32(stage_b(s)), &tmB, k, n0, fb);
+                        if (TERMS == 3) tma_load_2d(smem_u32(stage_blo(s)), &tmBlo, k, n0, fb);
+                    }
+                    if (++kb == nkb) {
+                        kb = 0;
+                        ++t;
+                        m0 = (t % mt) * BM;
+                        n0 = (t / mt) * BN;
+                    }
+                }
+            }
+        } else if (warp == 0) {
             // ---------------- TMA producer (warp 0) ----------------
             if (lane == 0) {
                 int t = t_b, kb = kb_b, m0 = (t % mt) * BM, n0 = (t / mt) * BN;
@@ -298,12 +352,19 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                     } else {
                         if (cstart && c >= 1 && !mbar_wait(smem_u32(&chunk_free[0]), (c - 1) & 1, err, abort_flag)) break;
                     }
-                    const uint32_t wb = CF::CONVERT ? smem_u32(&conv[s]) : smem_u32(&full[s]);
-                    if (!mbar_wait(wb, (i / STAGES) & 1, err, abort_flag)) break;
+                    // BF16 rings: the TMEM stage of A (converted) and the B slot; else the stage
+                    const int st = CF::SPLIT ? i % CF::NT : s, sb = CF::SPLIT ? i % CF::NBS : s;
+                    if (CF::SPLIT) {
+                        if (!mbar_wait(smem_u32(&conv[st]), (i / CF::NT) & 1, err, abort_flag)) break;
+                        if (!mbar_wait(smem_u32(&bfull[sb]), (i / CF::NBS) & 1, err, abort_flag)) break;
+                    } else {
+                        const uint32_t wb = CF::CONVERT ? smem_u32(&conv[s]) : smem_u32(&full[s]);
+                        if (!mbar_wait(wb, (i / STAGES) & 1, err, abort_flag)) break;
+                    }
                     tc_fence_after();
                     const uint32_t dacc = tmem + (uint32_t)(b * CF::ACC_COLS);
-                    const uint32_t a_s = smem_u32(stage_a(s)), b_hi = smem_u32(stage_b(s)), b_lo = smem_u32(stage_blo(s));
-                    const uint32_t ta = tmem + a_col(s);
+                    const uint32_t a_s = smem_u32(stage_a(s)), b_hi = smem_u32(stage_b(sb)), b_lo = smem_u32(stage_blo(sb));
+                    const uint32_t ta = tmem + a_col(st);
                     if (BF) {
                         // K = 16 BF16 per MMA: 32 bytes along a 128-byte swizzle row of B, 8 TMEM columns of A
     #pragma unroll
@@ -349,7 +410,12 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                         }
                     }
                     }
-                    mma_commit(smem_u32(&empty[s]));
+                    if (CF::SPLIT) {  // B slot and TMEM stage free once these MMAs complete
+                        mma_commit(smem_u32(&bempty[sb]));
+                        mma_commit(smem_u32(&tempty[st]));
+                    } else {
+                        mma_commit(smem_u32(&empty[s]));
+                    }
                     if (cend) mma_commit(smem_u32(&chunk_full[b]));
                     ++p;
                     if (++kb == nkb) {
@@ -366,9 +432,14 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
             const int r = threadIdx.x - 128;  // tile row = TMEM lane
             const uint32_t lane_base = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
             for (int i = 0; i < nk; ++i) {
-                const int s = i % STAGES;
-                if (!mbar_wait(smem_u32(&full[s]), (i / STAGES) & 1, err, abort_flag)) break;
-                const uint32_t taddr = lane_base + a_col(s);
+                // BF16 rings: A slot s (NA deep) into TMEM stage st (NT deep, free once the MMAs of
+                // k-block i - NT complete); else one stage index for both
+                const int s = CF::SPLIT ? i % CF::NA : i % STAGES, st = CF::SPLIT ? i % CF::NT : s;
+                if (!mbar_wait(smem_u32(&full[s]), (i / (CF::SPLIT ? CF::NA : STAGES)) & 1, err, abort_flag)) break;
+                if (CF::SPLIT && i >= CF::NT &&
+                    !mbar_wait(smem_u32(&tempty[st]), ((i / CF::NT) - 1) & 1, err, abort_flag))
+                    break;
+                const uint32_t taddr = lane_base + a_col(st);
                 if (BF) {
                     // row r's 64 FP32 values -> 32 columns of BF16 hi pairs (and 32 of lo pairs)
 #pragma unroll
@@ -410,7 +481,8 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                 }
                 asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 tc_fence_before();
-                mbar_arrive(smem_u32(&conv[s]));
+                mbar_arrive(smem_u32(&conv[st]));
+                if (CF::SPLIT) mbar_arrive(smem_u32(&empty[s]));  // A slot read: the producer may refill it
             }
         }
     } else {
