@@ -94,11 +94,155 @@ k_gemm(int M, int N, int K, T alpha, const T *__restrict__ A, int64_t lda, const
     }
 }
 
+// FP32 SGEMM for aligned operands (ld a multiple of 4, 16-byte aligned bases): 128 x 128
+// tiles, 256 threads, 8 x 8 outputs per thread as 2 x 2 blocks of 4 x 4 (rows tm*4 and
+// 64 + tm*4, columns tn*4 and 64 + tn*4, tm = thread % 16: 128-bit shared loads without bank
+// conflicts, and consecutive threads own consecutive rows, so C moves as float4 columns),
+// BK = 8, tiles double-buffered in shared memory with the next tile's global loads
+// (float4 along each operand's contiguous dimension) issued before the current tile's
+// FMAs.  Every output is summed over k in ascending order with one fma per term, as in
+// k_gemm, so both kernels give the same bits.
+constexpr int SG_BM = 128, SG_BN = 128, SG_BK = 8, SG_NT = 256;
+
+template <bool TA, bool TB>
+__global__ void __launch_bounds__(SG_NT, 2)
+k_sgemm(int M, int N, int K, float alpha, const float *__restrict__ A, int64_t lda, const float *__restrict__ B,
+        int64_t ldb, float beta, float *__restrict__ C, int64_t ldc, const int *status)
+{
+    __shared__ __align__(16) float As[2][SG_BK][SG_BM];
+    __shared__ __align__(16) float Bs[2][SG_BK][SG_BN];
+    if (status_bad(status)) return;
+    const int tid = threadIdx.x, tm = tid % 16, tn = tid / 16;
+    const int m0 = blockIdx.x * SG_BM, n0 = blockIdx.y * SG_BN;
+    // one float4 of A and one of B per thread per tile (128 x 8 = 256 float4 each)
+    // !TA: A(m, k) = A[m + k lda], a float4 along m: (m = 4 (tid % 32), k = tid / 32)
+    //  TA: A(m, k) = A[k + m lda], a float4 along k: (m = tid / 2, k = 4 (tid % 2))
+    const int am = TA ? tid / 2 : 4 * (tid % 32), ak = TA ? 4 * (tid % 2) : tid / 32;
+    // !TB: B(k, n) = B[k + n ldb], a float4 along k: (n = tid / 2, k = 4 (tid % 2))
+    //  TB: B(k, n) = B[n + k ldb], a float4 along n: (n = 4 (tid % 32), k = tid / 32)
+    const int bn = TB ? 4 * (tid % 32) : tid / 2, bk = TB ? tid / 32 : 4 * (tid % 2);
+    auto load_a = [&](int k0, float4 &v) {
+        const int gm = m0 + am, gk = k0 + ak;
+        float e[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int mm = TA ? gm : gm + u, kk = TA ? gk + u : gk;
+            e[u] = (mm < M && kk < K) ? (TA ? A[kk + (int64_t)mm * lda] : A[mm + (int64_t)kk * lda]) : 0.f;
+        }
+        const bool full = TA ? (gm < M && gk + 3 < K) : (gm + 3 < M && gk < K);
+        v = full ? (TA ? *(const float4 *)(A + gk + (int64_t)gm * lda) : *(const float4 *)(A + gm + (int64_t)gk * lda))
+                 : make_float4(e[0], e[1], e[2], e[3]);
+    };
+    auto load_b = [&](int k0, float4 &v) {
+        const int gn = n0 + bn, gk = k0 + bk;
+        float e[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int nn = TB ? gn + u : gn, kk = TB ? gk : gk + u;
+            e[u] = (nn < N && kk < K) ? (TB ? B[nn + (int64_t)kk * ldb] : B[kk + (int64_t)nn * ldb]) : 0.f;
+        }
+        const bool full = TB ? (gn + 3 < N && gk < K) : (gn < N && gk + 3 < K);
+        v = full ? (TB ? *(const float4 *)(B + gn + (int64_t)gk * ldb) : *(const float4 *)(B + gk + (int64_t)gn * ldb))
+                 : make_float4(e[0], e[1], e[2], e[3]);
+    };
+    auto store_a = [&](int buf, const float4 &v) {
+        if (TA) {  // four k of one m
+            As[buf][ak][am] = v.x;
+            As[buf][ak + 1][am] = v.y;
+            As[buf][ak + 2][am] = v.z;
+            As[buf][ak + 3][am] = v.w;
+        } else {
+            *(float4 *)&As[buf][ak][am] = v;
+        }
+    };
+    auto store_b = [&](int buf, const float4 &v) {
+        if (TB) {
+            *(float4 *)&Bs[buf][bk][bn] = v;
+        } else {  // four k of one n
+            Bs[buf][bk][bn] = v.x;
+            Bs[buf][bk + 1][bn] = v.y;
+            Bs[buf][bk + 2][bn] = v.z;
+            Bs[buf][bk + 3][bn] = v.w;
+        }
+    };
+    float acc[8][8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) acc[i][j] = 0.f;
+    float4 ra, rb;
+    load_a(0, ra);
+    load_b(0, rb);
+    store_a(0, ra);
+    store_b(0, rb);
+    __syncthreads();
+    int buf = 0;
+    for (int k0 = 0; k0 < K; k0 += SG_BK) {
+        const bool more = k0 + SG_BK < K;
+        if (more) {  // the next tile's global loads, in flight during this tile's FMAs
+            load_a(k0 + SG_BK, ra);
+            load_b(k0 + SG_BK, rb);
+        }
+#pragma unroll
+        for (int kk = 0; kk < SG_BK; ++kk) {
+            const float4 a0 = *(const float4 *)&As[buf][kk][tm * 4], a1 = *(const float4 *)&As[buf][kk][64 + tm * 4];
+            const float4 b0 = *(const float4 *)&Bs[buf][kk][tn * 4], b1 = *(const float4 *)&Bs[buf][kk][64 + tn * 4];
+            const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+#pragma unroll
+                for (int j = 0; j < 8; ++j) acc[i][j] = fmaf(a[i], b[j], acc[i][j]);
+        }
+        if (more) {
+            store_a(buf ^ 1, ra);
+            store_b(buf ^ 1, rb);
+        }
+        __syncthreads();
+        buf ^= 1;
+    }
+    const bool cvec = ldc % 4 == 0 && (uintptr_t)C % 16 == 0;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int gn = n0 + (j < 4 ? tn * 4 + j : 64 + tn * 4 + j - 4);
+        if (gn >= N) continue;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {  // rows m0 + tm*4 .. + 3, then m0 + 64 + tm*4 .. + 3
+            const int gm = m0 + 64 * h + tm * 4;
+            float *c = C + gm + (int64_t)gn * ldc;
+            if (cvec && gm + 3 < M) {
+                float4 o = make_float4(alpha * acc[4 * h][j], alpha * acc[4 * h + 1][j], alpha * acc[4 * h + 2][j],
+                                       alpha * acc[4 * h + 3][j]);
+                if (beta != 0.f) {
+                    const float4 ci = *(const float4 *)c;
+                    o = make_float4(fmaf(alpha, acc[4 * h][j], beta * ci.x), fmaf(alpha, acc[4 * h + 1][j], beta * ci.y),
+                                    fmaf(alpha, acc[4 * h + 2][j], beta * ci.z),
+                                    fmaf(alpha, acc[4 * h + 3][j], beta * ci.w));
+                }
+                *(float4 *)c = o;
+            } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i)
+                    if (gm + i < M)
+                        c[i] = (beta == 0.f) ? alpha * acc[4 * h + i][j] : fmaf(alpha, acc[4 * h + i][j], beta * c[i]);
+            }
+        }
+    }
+}
+
 template <typename T, bool TA, bool TB>
 static void gemm_dispatch(cudaStream_t st, int M, int N, int K, T alpha, const T *A, int64_t lda, const T *B,
                           int64_t ldb, T beta, T *C, int64_t ldc, const int *status)
 {
     if constexpr (sizeof(T) == 4) {
+        const bool aligned = lda % 4 == 0 && ldb % 4 == 0 && (uintptr_t)A % 16 == 0 && (uintptr_t)B % 16 == 0;
+        // the register-blocked kernel where a 128 x 128 tile is filled enough to pay
+        if (aligned && (int64_t)M * N >= (int64_t)64 * SG_BM * SG_BN && M >= 64 && N >= 64) {
+            dim3 grid(ceil_div(M, SG_BM), ceil_div(N, SG_BN));
+            rb_count_launch();
+            k_sgemm<TA, TB><<<grid, SG_NT, 0, st>>>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, status);
+            return;
+        }
         if (N <= 32) {
             constexpr int BM = 128, BN = 32, BK = 16, TM = 8, TN = 2;
             dim3 grid(ceil_div(M, BM), ceil_div(N, BN));
