@@ -3,8 +3,9 @@
 One bench "step" is one complete AdaRBFGS solve (Algorithm 4) of the
 n = 16384 SPD matrix A = M^T M / m + 1e-4 I (M 65536 x 16384, 1 % dense
 N(0,1)) from L0 = I with a Gaussian sketch of q = 128 columns, run until the
-residual ||I - L L^T A||_F / sqrt(n) <= 1e-4 (sampled every 32 steps on 256
-columns, confirmed on 1024 columns).  Each step uses a fresh sketch seed.  The
+residual ||I - L L^T A||_F / sqrt(n) <= 1e-4 (sampled on 256 columns at checks
+spaced by the geometric rate the last two checks show, 32 to 256 steps apart,
+confirmed on 1024 columns).  Each step uses a fresh sketch seed.  The
 default form is the mixed-precision BF16x3 one: the two n x n-streaming GEMMs
 as 3-term BF16 splits, the other products 3xTF32, the rank-q correction 1xTF32.
 
@@ -36,7 +37,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "time to ‖I−XA‖_F/√n≤1e-4 at n=16384 (mixed vs FP32); solves/s, p99 latency"
 N_DEFAULT, Q_DEFAULT, TOL_DEFAULT = 16384, 128, 1e-4
-CHECK_EVERY, CHECK_COLS, CONFIRM_COLS = 32, 256, 1024
+# check_every < 0: predicted check spacing (rb_next_check_gap), at least |CHECK_EVERY| steps apart
+CHECK_EVERY, CHECK_COLS, CONFIRM_COLS = -32, 256, 1024
 MAX_ITER = 20000
 SERVE_MAX_ITER = 4000  # per request; requests that stall at their floor stop earlier (floor-limited)
 # DRAM bytes (read + write) of one k_tc_update launch at n = 8192, q = 128, from one ncu capture
@@ -326,13 +328,15 @@ def config(args):
                         f"M {4 * args.n}x{args.n} 1%-dense N(0,1)",
             "n": args.n, "q": args.q, "tol": args.tol, "parallelism": "replicas",
             "l2": "inputs larger than L2 (A and L are 1 GiB each)",
-            "residual_check": f"every {CHECK_EVERY} steps on {CHECK_COLS} columns, confirmed on {CONFIRM_COLS}"}
+            "residual_check": f"on {CHECK_COLS} columns, {-CHECK_EVERY} to {-8 * CHECK_EVERY} steps apart (predicted "
+                              f"from the geometric rate of the last two checks), confirmed on {CONFIRM_COLS}"}
 
 
 def run_serving(B, wl, args, requests=None, rate=None):
     """Poisson stream (the first `requests` requests of the seeded stream at `rate` req/s) through
-    the continuous-batching server: BF16x3 for tolerances >= 1e-4, mixed below; check every 32 steps
-    on 128 columns; requests that stall at their arithmetic's floor finish as floor-limited."""
+    the continuous-batching server: BF16x3 for tolerances >= 1e-4, mixed below; checks on 128 columns,
+    32 to 256 steps apart (predicted spacing); requests that stall at their arithmetic's floor finish
+    as floor-limited."""
     import numpy as np
     import torch
 
@@ -344,7 +348,7 @@ def run_serving(B, wl, args, requests=None, rate=None):
         mats[r["seed"]] = wl.c5_matrix(r["n"], r["seed"], device="cuda")
     torch.cuda.synchronize()
     budget = wl.WORKLOADS["c5_serving"]["budget_bytes"]
-    s = B.rb_srv_create(budget, 64, B.RB_BF16X3, 32, 128, SERVE_MAX_ITER)
+    s = B.rb_srv_create(budget, 64, B.RB_BF16X3, CHECK_EVERY, 128, SERVE_MAX_ITER)
     tickets = []
     t0 = time.perf_counter()
     for r in stream:

@@ -81,6 +81,7 @@ _SIGS = {
     "rbfgs_residual_start": (C.c_int, [C.c_void_p, C.c_int, C.c_uint64]),
     "rbfgs_residual_poll": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "rbfgs_footprint": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p]),
+    "rb_next_check_gap": (C.c_int, [C.c_int, C.c_int, C.c_double, C.c_int, C.c_double, C.c_double]),
     "rb_srv_create": (C.c_int, [C.c_void_p, C.c_size_t, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int]),
     "rb_srv_submit": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int64, C.c_int, C.c_double,
                                 C.c_uint64, C.c_int, C.c_void_p, C.c_int, C.c_int64, C.c_void_p]),
@@ -178,6 +179,10 @@ def rbfgs_solve(h, tol, max_iter, check_every, check_cols, confirm_cols):
     st = _check(_lib().rbfgs_solve(h, tol, max_iter, check_every, check_cols, confirm_cols, C.byref(it),
                                    C.byref(r)), "rbfgs_solve")
     return st, it.value, r.value
+
+
+def rb_next_check_gap(e, k0, r0, k1, r1, tol):
+    return int(_lib().rb_next_check_gap(e, k0, r0, k1, r1, tol))
 
 
 def rbfgs_export(h, what, out_dev, ld):

@@ -1177,15 +1177,37 @@ extern "C" rb_status rbfgs_footprint(int n, const rb_opts *opts, size_t *bytes)
     return RB_OK;
 }
 
+// Predicted spacing of residual checks: the residual falls about geometrically (the linear rate of
+// Sec. 6; Sec. 9's one-step bound for AdaRBFGS improves as the iterate does), so from two checks
+// (r0 after k0 steps, r1 after k1) the rate is log rho = log(r1 / r0) / (k1 - k0) and the steps
+// left to tol are d = log(tol / r1) / log rho; the next check comes after d / 2 steps, at least e
+// and at most 8 e (8 e while the residual is not falling).  Halving the predicted distance keeps
+// the overshoot past the crossing at most e steps while the rate holds or improves, as it does
+// for AdaRBFGS.
+extern "C" int rb_next_check_gap(int e, int k0, double r0, int k1, double r1, double tol)
+{
+    if (e < 1) return 1;
+    if (k0 < 0 || k1 <= k0 || !(r0 > 0) || !(r1 > tol) || !(tol > 0)) return e;
+    const double lr = log(r1 / r0) / (double)(k1 - k0);
+    if (!(lr < 0)) return 8 * e;
+    const double half = 0.5 * log(tol / r1) / lr;
+    return (int)std::max((double)e, std::min(8.0 * e, floor(half)));
+}
+
 extern "C" rb_status rbfgs_solve(rbfgs_t h, double tol, int max_iter, int check_every, int check_cols,
                                  int confirm_cols, int *iters, double *resid)
 {
-    if (!h || max_iter < 0 || check_every < 1 || check_cols < 0) return RB_EINVAL;
+    if (!h || max_iter < 0 || check_every == 0 || check_cols < 0) return RB_EINVAL;
+    const bool predicted = check_every < 0;
+    const int e = predicted ? -check_every : check_every;
     int done = 0;
     double r = INFINITY;
     uint64_t col_seed = 0x5eed0000ull;
+    int k0 = -1;  // the check before the last one: steps and residual
+    double r0 = 0.0;
+    int gap = e;
     while (done < max_iter) {
-        const int chunk = std::min(check_every, max_iter - done);
+        const int chunk = std::min(gap, max_iter - done);
         rb_status s = RB_OK;
         if (h->method == RB_METHOD_RBFGS)
             s = rbfgs_step(h, chunk);
@@ -1200,12 +1222,17 @@ extern "C" rb_status rbfgs_solve(rbfgs_t h, double tol, int max_iter, int check_
         if (s != RB_OK) return s;
         done += chunk;
         RB_TRY(rbfgs_residual(h, check_cols, col_seed++, &r));
+        double rk = r;
         if (r <= tol) {
             double rc = r;
             if (confirm_cols != check_cols) RB_TRY(rbfgs_residual(h, confirm_cols, col_seed++, &rc));
             r = rc;
             if (rc <= tol) break;
+            rk = rc;
         }
+        gap = predicted ? rb_next_check_gap(e, k0, r0, done, rk, tol) : e;
+        k0 = done;
+        r0 = rk;
     }
     if (iters) *iters = done;
     if (resid) *resid = r;

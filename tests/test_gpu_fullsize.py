@@ -62,7 +62,8 @@ def test_solve_to_tolerance_checked_in_fp64(c3, prec):
     A, A64 = c3
     h = _handle(A, prec)
     try:
-        st, iters, r = B.rbfgs_solve(h, TOL, 20000, 32, 256, 1024)
+        # the benchmark's check schedule: predicted spacing, 32 to 256 steps apart
+        st, iters, r = B.rbfgs_solve(h, TOL, 20000, -32, 256, 1024)
         assert st == B.RB_OK and r <= TOL
         L = _L(h)
     finally:
