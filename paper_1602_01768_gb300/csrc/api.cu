@@ -36,6 +36,7 @@ struct rb_ctx {
     bool slo_valid = false;                // Slo belongs to the S in place
     bool sbf_valid = false;                // Sbf holds the BF16 parts of the S in place
     float *Bv = nullptr, *Bs = nullptr;  // tensor-core V and S^: [D^-T; -C^-T] (2q x q) and C^-T (q x q)
+    float *Bvlo = nullptr;               // lo part of Bv, split by the streams that write each half
     float *Mf = nullptr, *Nf = nullptr;  // FP32 Gram products S^T A S and S~^T S~ (tensor-core path)
     void *Sbf = nullptr, *Gbf = nullptr;  // BF16 forms: [hi | lo] BF16 parts of S and G (n x q each, ld ldbf)
     int64_t ldbf = 0;
@@ -169,6 +170,7 @@ static void destroy_ctx(rb_ctx *h)
                      &h->V, &h->P3, &h->Cinv, &h->Dinv, &h->Lam, &h->B1, &h->R1, &h->R2, &h->R3};
     for (void **b : bufs) rb_free(*b);
     rb_freet(h->Bv);
+    rb_freet(h->Bvlo);
     rb_freet(h->Bs);
     rb_freet(h->Spart);
     rb_freet(h->Slo);
@@ -317,6 +319,7 @@ static rb_status alloc_sketch_workspace(rb_ctx *h)
     RB_TRY(rb_alloc(&h->Sh, nq));
     if (!h->f64) {
         RB_TRY(rb_alloc(&h->Bv, 2 * q * q * sizeof(float)));
+        RB_TRY(rb_alloc(&h->Bvlo, 2 * q * q * sizeof(float)));
         RB_TRY(rb_alloc(&h->Bs, q * q * sizeof(float)));
         RB_TRY(rb_alloc(&h->Mf, q * q * sizeof(float)));
         RB_TRY(rb_alloc(&h->Nf, q * q * sizeof(float)));
@@ -743,6 +746,10 @@ constexpr int SIDE_SMS_G = 4;
 constexpr int SIDE_SMS_UPD = 4;
 
 
+// V^T = [S~ | W^T] Bv is a 3-term product in the 3-term forms: each stream that writes a half of Bv
+// also writes that half's lo part into Bvlo, so that V's launch splits nothing.
+static bool bv_split(const rb_ctx *h) { return h->prec != RB_TF32 && h->prec != RB_BF16 && h->Bvlo != nullptr; }
+
 // D chain on the handle's D stream: S~^T S~ (one exact pass: S~ is TF32) on the SMs other
 // work leaves free, then its core, D^-T written as rows dofs .. dofs + q - 1 of Bv.
 static void ada_d_chain(rb_ctx *h, const float *St, int dofs, int reserve)
@@ -753,6 +760,7 @@ static void ada_d_chain(rb_ctx *h, const float *St, int dofs, int reserve)
         launch_core_tr64(h->st3, q, h->Nf, h->Bv + dofs, 2 * q, 1.f, nullptr, 0, 0.f, h->d_status);
     else
         launch_core_tr32(h->st3, q, h->Nf, nullptr, h->Bv + dofs, 2 * q, 1.f, nullptr, 0, 0.f, h->d_status);
+    if (bv_split(h)) tc_split_lo(h->st3, q, q, h->Bv + dofs, 2 * q, h->Bvlo + dofs, 2 * q);
     cudaEventRecord(h->ev_d, h->st3);
 }
 
@@ -843,6 +851,7 @@ static void ada_step_tc(rb_ctx *h)
                 cudaStreamWaitEvent(h->st3, h->ev_sk, 0);
                 if (cols) {  // D = I
                     launch_set_identity<float>(h->st3, q, h->Bv + dofs, 2 * q, 1.f);
+                    if (bv_split(h)) tc_split_lo(h->st3, q, q, h->Bv + dofs, 2 * q, h->Bvlo + dofs, 2 * q);
                     cudaEventRecord(h->ev_d, h->st3);
                 } else {
                     ada_d_chain(h, St, dofs, side_rsv_g);
@@ -888,6 +897,7 @@ static void ada_step_tc(rb_ctx *h)
                 launch_core_tr64(side, q, h->Mf, h->Bv + cofs, 2 * q, -1.f, h->Bs, q, 1.f, h->d_status);
             else
                 launch_core_tr32(side, q, h->Mf, nullptr, h->Bv + cofs, 2 * q, -1.f, h->Bs, q, 1.f, h->d_status);
+            if (bv_split(h)) tc_split_lo(side, q, q, h->Bv + cofs, 2 * q, h->Bvlo + cofs, 2 * q);
         } else {
             launch_gram<float>(side, n, q, q, S, n, G, n, h->part, h->M);    // S^T A S -> C^-1
             launch_core_ada32(side, q, h->M, nullptr, Ci, nullptr, h->d_status);
@@ -928,7 +938,8 @@ static void ada_step_tc(rb_ctx *h)
     mark(h, fork ? "W=G^TL | C core" : "W=G^TL");
     if (tcv) {
         // V^T = [S~ | W^T] [D^-T; -C^-T] (or both halves swapped), written transposed: V is q x n (ld q)
-        tc_gemm_nk_t(h->tc, st, acc, TC_A_MN, n, q, 2 * q, SW, n, h->Bv, 2 * q, V, q, stp);
+        tc_gemm_nk_t(h->tc, st, acc, TC_A_MN, n, q, 2 * q, SW, n, h->Bv, 2 * q, V, q, stp, 0,
+                     (acc == 3 && bv_split(h)) ? h->Bvlo : nullptr);
         // S^ = S C^-T, written transposed (row-major n x q) for the K-major update operand (side stream
         // when the update is fused)
         if (!fuse) tc_gemm_nk_t(h->tc, st, upd, TC_A_MN, n, q, q, S, n, h->Bs, q, Sh, q, stp);

@@ -569,6 +569,43 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                         write_c = true;
                     }
                 }
+                // Transposed output of a one-tile-per-CTA launch: the tile's MMAs are complete, so
+                // the ring is idle; each warp stages its 32 rows x BN block there and writes every
+                // output row (BN contiguous floats) with 16-byte stores across the warp, instead of
+                // one 4-byte store per row per column.
+                const bool staged = write_c && ctrans && part == nullptr && beta == 0.f && Clo == nullptr &&
+                                    Cbf == nullptr && (ldc & 3) == 0 && ((uintptr_t)C & 15) == 0 &&
+                                    (size_t)4 * 32 * (BN + 4) * 4 <= (size_t)CF::RING_BYTES;
+                if (staged) {
+                    float *stg = (float *)smem + wq * 32 * (BN + 4);  // [32 rows][BN + 4], 16-byte rows
+#pragma unroll
+                    for (int j = 0; j < BN; j += 4)
+                        *(float4 *)(stg + lane * (BN + 4) + j) =
+                            make_float4(alpha * run[j], alpha * run[j + 1], alpha * run[j + 2], alpha * run[j + 3]);
+                    __syncwarp();
+                    const int mrow0 = (t % mt) * BM + 32 * wq, n0 = (t / mt) * BN;
+                    for (int rr = 0; rr < 32; ++rr) {
+                        const int m = mrow0 + rr;
+                        if (m >= M) break;
+                        float *crow = C + (int64_t)m * ldc + n0;
+#pragma unroll
+                        for (int j0 = 0; j0 < BN; j0 += 128) {
+                            const int j = j0 + 4 * lane;
+                            if (j < BN) {
+                                const float4 v = *(const float4 *)(stg + rr * (BN + 4) + j);
+                                if (n0 + j + 3 < N) {
+                                    *(float4 *)(crow + j) = v;
+                                } else {
+                                    if (n0 + j < N) crow[j] = v.x;
+                                    if (n0 + j + 1 < N) crow[j + 1] = v.y;
+                                    if (n0 + j + 2 < N) crow[j + 2] = v.z;
+                                }
+                            }
+                        }
+                    }
+                    __syncwarp();
+                    write_c = false;
+                }
                 if (write_c) {
                     const int m = (t % mt) * BM + 32 * wq + lane, n0 = (t / mt) * BN;
                     if (m < M) {
@@ -906,10 +943,18 @@ int tc_gemm_nk(tc_plan *p, cudaStream_t st, int terms, int a_layout, int M, int 
 }
 
 int tc_gemm_nk_t(tc_plan *p, cudaStream_t st, int terms, int a_layout, int M, int N, int K, const float *A,
-                 int64_t lda, const float *B, int64_t ldb, float *C, int64_t ldc, const int *status, int reserve_sms)
+                 int64_t lda, const float *B, int64_t ldb, float *C, int64_t ldc, const int *status, int reserve_sms,
+                 const float *Blo)
 {
     return tc_run(p, st, terms, a_layout, M, N, K, 1.f, A, lda, B, ldb, 0.f, nullptr, 0, C, ldc, status, reserve_sms,
-                  1);
+                  1, Blo);
+}
+
+void tc_split_lo(cudaStream_t st, int rows, int cols, const float *X, int64_t ldx, float *Lo, int64_t ldl)
+{
+    if (rows <= 0 || cols <= 0) return;
+    rb_count_launch();
+    k_split_lo<<<dim3((rows + 255) / 256, cols), 256, 0, st>>>(rows, cols, X, ldx, Lo, ldl);
 }
 
 int tc_gemm_nk_axpby(tc_plan *p, cudaStream_t st, int terms, int a_layout, int M, int N, int K, float alpha,

@@ -31,9 +31,13 @@ int tc_gemm_nk(tc_plan *p, cudaStream_t st, int terms, int a_layout, int M, int 
                int reserve_sms = 0);
 // Same product with C written transposed: element (m, n) at C[n + m ldc]
 // (C^T column-major).  Tensor cores only: returns <0 where that is not possible.
+// Blo (may be null): B's lo part, as for tc_gemm_nk_lo.
 int tc_gemm_nk_t(tc_plan *p, cudaStream_t st, int terms, int a_layout, int M, int N, int K, const float *A,
                  int64_t lda, const float *B, int64_t ldb, float *C, int64_t ldc, const int *status,
-                 int reserve_sms = 0);
+                 int reserve_sms = 0, const float *Blo = nullptr);
+// Lo = X - hi(X) elementwise (hi = the top 11 significand bits that a TF32 MMA reads), rows x cols
+// column-major panels; the Blo operand of a 3-term product.
+void tc_split_lo(cudaStream_t st, int rows, int cols, const float *X, int64_t ldx, float *Lo, int64_t ldl);
 // As tc_gemm_nk, with two hand-offs between products.  Blo (may be null): the
 // lo part of B (element-wise x - hi(x), K x N, ld ldb, 16-byte aligned), already
 // formed by the kernel that wrote B, so this call does not split B itself.  Clo
