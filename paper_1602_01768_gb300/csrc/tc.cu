@@ -49,8 +49,9 @@ using namespace tcx;
 // converter writes its BF16 parts into TMEM, two K-consecutive values per
 // 32-bit column (the lower K index in the low half); B comes pre-split as BF16
 // hi and lo panels (64 BF16 = one 128-byte swizzle row).  x = hi + lo with
-// hi = bf16(x), lo = bf16(x - hi) (round to nearest): the 3-term product
-// hi hi + hi lo + lo hi carries ~16 bits, each MMA covers K = 16.
+// hi = bf16(x), lo = bf16(x - hi) (round to nearest; A's lo rounds ties away
+// from zero, B's to even): the 3-term product hi hi + hi lo + lo hi carries
+// ~16 bits, each MMA covers K = 16.
 template <int BN, int TERMS, int AMN, int BF = 0>
 struct Cfg {
     // The A tile lands in shared memory by TMA; the converter warps write the
@@ -75,7 +76,9 @@ struct Cfg {
     static constexpr bool CONVERT = HI_TMEM || LO_TMEM;
     static constexpr int LO_OFF = HI_TMEM ? 32 : 0;  // TMEM column of lo within a stage
     static constexpr int BKE = BF ? 64 : BK;          // K elements per k-block
-    static constexpr int CHUNK = CHUNK_KB * BK / BKE;  // k-blocks per accumulation chunk (512 of K)
+    // k-blocks per accumulation chunk: 64 MMA steps either way (512 of K at K = 8 per TF32 MMA,
+    // 1024 of K at K = 16 per BF16 MMA), so the drift each chunk bounds is the same
+    static constexpr int CHUNK = BF ? 2 * CHUNK_KB * BK / BKE : CHUNK_KB * BK / BKE;
     static constexpr int A_BYTES = BM * BKE * 4;
     static constexpr int B_BYTES = BN * BKE * (BF ? 2 : 4);
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES * (TERMS == 3 ? 2 : 1);  // [A | B | B lo]
@@ -93,13 +96,13 @@ struct Cfg {
     // stages, each freed when its MMAs complete.
     static constexpr bool SPLIT = BF != 0;
     static constexpr int NA = SPLIT ? 3 : 0;
-    static constexpr int NBS = SPLIT ? 3 : 0;
+    static constexpr int NBS = SPLIT ? 4 : 0;  // B waits on the MMAs: one slot more than A (measured)
     static constexpr int NT = SPLIT ? (STAGES_TMEM < 4 ? STAGES_TMEM : 4) : 0;
     static constexpr int B2_BYTES = B_BYTES * (TERMS == 3 ? 2 : 1);  // B and its lo part
     static constexpr int RING_BYTES = SPLIT ? NA * A_BYTES + NBS * B2_BYTES : STAGES * STAGE_BYTES;
     static constexpr int SMEM = RING_BYTES + 1024 /*align*/ + 512 /*barriers*/;
     static_assert(STAGES >= 2, "pipeline needs two stages");
-    static_assert(!SPLIT || (NT >= 2 && RING_BYTES <= 200 * 1024), "BF16 rings");
+    static_assert(!SPLIT || (NT >= 2 && RING_BYTES <= 224 * 1024), "BF16 rings");
     static_assert(!BF || (AMN == 0 && TERMS != 2), "BF16 products: K-contiguous A, 1 or 3 terms");
 };
 
@@ -436,32 +439,49 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                 // k-block i - NT complete); else one stage index for both
                 const int s = CF::SPLIT ? i % CF::NA : i % STAGES, st = CF::SPLIT ? i % CF::NT : s;
                 if (!mbar_wait(smem_u32(&full[s]), (i / (CF::SPLIT ? CF::NA : STAGES)) & 1, err, abort_flag)) break;
-                if (CF::SPLIT && i >= CF::NT &&
-                    !mbar_wait(smem_u32(&tempty[st]), ((i / CF::NT) - 1) & 1, err, abort_flag))
-                    break;
-                const uint32_t taddr = lane_base + a_col(st);
                 if (BF) {
-                    // row r's 64 FP32 values -> 32 columns of BF16 hi pairs (and 32 of lo pairs)
+                    // Row r's 64 FP32 values into registers first: the A slot is released before
+                    // the wait for a free TMEM stage, so the next load into it is not held up by
+                    // MMAs still reading TMEM.
+                    float v[4][16];
+#pragma unroll
+                    for (int g = 0; g < 2; ++g)
+#pragma unroll
+                        for (int h = 0; h < 2; ++h) load_a_half<0>(stage_a(s) + g * A_TILE_BYTES, r, h, v[2 * g + h]);
+                    if (CF::SPLIT) mbar_arrive(smem_u32(&empty[s]));  // A slot read: the producer may refill it
+                    if (CF::SPLIT && i >= CF::NT &&
+                        !mbar_wait(smem_u32(&tempty[st]), ((i / CF::NT) - 1) & 1, err, abort_flag))
+                        break;
+                    const uint32_t taddr = lane_base + a_col(st);
+                    // -> 32 columns of BF16 hi pairs (and 32 of lo pairs).  hi is rounded to nearest
+                    // even by the conversion unit; lo = x - hi (exact in FP32) is rounded to nearest,
+                    // ties away from zero, on the integer pipe (add half an ulp of BF16 to the bit
+                    // pattern, keep the top 16 bits): the conversion unit runs at a fraction of the
+                    // ALU rate, and one conversion per pair instead of two halves the converter's time.
 #pragma unroll
                     for (int g = 0; g < 2; ++g) {  // one 128 x 32 box each
                         uint32_t wh[16], wl[16];
 #pragma unroll
                         for (int h = 0; h < 2; ++h) {
-                            float v[16];
-                            load_a_half<0>(stage_a(s) + g * A_TILE_BYTES, r, h, v);
 #pragma unroll
                             for (int k = 0; k < 8; ++k) {
-                                const __nv_bfloat162 hi = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
-                                const float2 hf = __bfloat1622float2(hi);
-                                const __nv_bfloat162 lo = __floats2bfloat162_rn(v[2 * k] - hf.x, v[2 * k + 1] - hf.y);
-                                wh[8 * h + k] = *reinterpret_cast<const uint32_t *>(&hi);
-                                wl[8 * h + k] = *reinterpret_cast<const uint32_t *>(&lo);
+                                const float x0 = v[2 * g + h][2 * k], x1 = v[2 * g + h][2 * k + 1];
+                                const __nv_bfloat162 hi = __floats2bfloat162_rn(x0, x1);
+                                const uint32_t hb = *reinterpret_cast<const uint32_t *>(&hi);
+                                const uint32_t l0 = __float_as_uint(x0 - __uint_as_float(hb << 16)) + 0x8000u;
+                                const uint32_t l1 = __float_as_uint(x1 - __uint_as_float(hb & 0xFFFF0000u)) + 0x8000u;
+                                wh[8 * h + k] = hb;
+                                wl[8 * h + k] = __byte_perm(l0, l1, 0x7632);  // top halves: l0 low, l1 high
                             }
                         }
                         tmem_st16(taddr + 16 * g, wh);
                         if (CF::LO_TMEM) tmem_st16(taddr + CF::LO_OFF + 16 * g, wl);
                     }
                 } else {
+                if (CF::SPLIT && i >= CF::NT &&
+                    !mbar_wait(smem_u32(&tempty[st]), ((i / CF::NT) - 1) & 1, err, abort_flag))
+                    break;
+                const uint32_t taddr = lane_base + a_col(st);
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     float v[16];
@@ -482,7 +502,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                 asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 tc_fence_before();
                 mbar_arrive(smem_u32(&conv[st]));
-                if (CF::SPLIT) mbar_arrive(smem_u32(&empty[s]));  // A slot read: the producer may refill it
+                if (CF::SPLIT && !BF) mbar_arrive(smem_u32(&empty[s]));  // A slot read: the producer may refill it
             }
         }
     } else {

@@ -53,7 +53,7 @@ int tc_gemm_nk_axpby(tc_plan *p, cudaStream_t st, int terms, int a_layout, int M
 // (element (m, k) at A[k + m lda]) and B given as its BF16 parts Bh (hi) and Bl
 // (lo, needed for terms = 3), K x N, K contiguous, ld ldb (a multiple of 8),
 // 16-byte aligned.  terms = 1: hi(A) hi(B); terms = 3: hi hi + hi lo + lo hi
-// (~16 significant bits).  FP32 accumulation restarted every 512 of K.  Clo
+// (~16 significant bits).  FP32 accumulation restarted every 1024 of K (64 MMA steps).  Clo
 // (terms = 3, may be null): C's TF32 lo part beside C, as tc_gemm_nk_lo writes
 // it.  Returns 0 when launched, < 0 when the shape or alignment is outside the
 // kernel.  Cbf (may be null): C's own BF16 parts written beside C, hi at
