@@ -190,7 +190,7 @@ rb_status rbfgs_solve(rbfgs_t h, double tol, int max_iter, int check_every, int 
 
 /*
  * The predicted check spacing of rbfgs_solve, for callers that run their own
- * loop: steps to the next check after checks with residuals r0 (after k0
+ * loop on one handle: steps to the next check after checks with residuals r0 (after k0
  * steps) and r1 (after k1 > k0 steps), minimum spacing e >= 1.  Returns e when
  * k0 < 0 (no earlier check), r1 <= tol or an argument is not positive; 8 e when
  * r1 >= r0; else floor(log(tol / r1) / (2 log rho)) with
@@ -365,7 +365,7 @@ rb_status rb_batch_destroy(rb_batch_t b);
  * runs in the server's form `prec`, except that a BF16 form serves only
  * tolerances >= 1e-4 (smaller ones run in RB_MIXED): its products leave a
  * residual floor near 2e-5.  A request whose sampled residual has not fallen
- * by 10 % over 8 e steps (e = |check_every|) is finished as floor-limited (RB_NOTCONV with
+ * by 10 % over 8 check_every steps is finished as floor-limited (RB_NOTCONV with
  * floor_limited = 1): every FP32-storage form stops falling near a floor set by
  * its rounding (measured: ~3e-6 FP32, ~7e-6 3xTF32 at n / q = 64), so smaller
  * tolerances are not reachable in them.  Each
@@ -373,9 +373,7 @@ rb_status rb_batch_destroy(rb_batch_t b);
  * at least 32) waits in a FIFO queue until its device footprint
  * (rbfgs_footprint, plus a staging copy when A is in host memory) fits in
  * hbm_budget_bytes and fewer than max_live requests are running; it then
- * gets its own handle and stream, advances check_every steps at a time (or,
- * with check_every = -e < 0, the spacing rb_next_check_gap predicts from its
- * last two checks, e to 8 e steps) with
+ * gets its own handle and stream, advances check_every steps at a time with
  * non-blocking residual checks of check_cols sampled columns, and finishes
  * when the residual is <= tol, after max_iter steps (RB_NOTCONV) or on a
  * failure.  At the finish its factor L (FP32, ld ldo) is copied to `out`

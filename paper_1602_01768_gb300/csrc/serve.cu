@@ -4,9 +4,11 @@
 // scheduler thread admits them first-come-first-served while the HBM budget
 // (the handles' footprint, rbfgs_footprint) and the live-request cap allow,
 // gives each admitted request its own handle and CUDA stream, and keeps
-// every live request moving: AdaRBFGS steps (check_every of them, or with
-// check_every = -e the spacing rb_next_check_gap predicts, e to 8 e), then a
-// non-blocking residual check, polled without waiting.  Requests that reach
+// every live request moving: `check_every` AdaRBFGS steps, then a
+// non-blocking residual check, polled without waiting.  (A fixed, short chunk:
+// a request's chunk is enqueued on its stream in one go, and a chunk of a few
+// hundred steps would fill the stream's launch queue and block the scheduler
+// thread, starving the other requests.)  Requests that reach
 // their tolerance (or fail, or hit max_iter) write their factor L to the
 // caller's output, release their memory and wake waiters, so queued
 // requests are admitted as soon as room frees up.  Work of different
@@ -56,8 +58,6 @@ struct Req {
     int prec = RB_MIXED;     // the form this request runs in (chosen from its tolerance)
     double best = INFINITY;  // smallest residual seen (updated on a 10 % fall) and the steps then
     int best_steps = 0;
-    int k_prev = -1;         // steps and residual at the check before the last one
-    double r_prev = 0;
     int floor_limited = 0;
 };
 
@@ -70,7 +70,7 @@ int request_prec(int server_prec, double tol)
     return server_prec;
 }
 
-// Steps without a 10 % fall of the residual, in units of the minimum check spacing, after which a
+// Steps without a 10 % fall of the residual, in units of the check spacing, after which a
 // request is finished as floor-limited: the residual then sits at the floor of the request's
 // arithmetic, above its tolerance.
 constexpr int STALL_CHECKS = 8;
@@ -85,7 +85,6 @@ double now_s(const std::chrono::steady_clock::time_point &t0)
 struct rb_srv {
     size_t budget = 0, used = 0;
     int max_live = 0, prec = RB_MIXED, check_every = 32, check_cols = 256, max_iter = 20000;
-    bool predicted = false;  // check spacing from rb_next_check_gap (check_every = minimum)
     int device = 0;
     std::mutex mu;
     std::condition_variable cv;
@@ -228,12 +227,7 @@ static void worker_loop(rb_srv *s)
                         r->resid = r->best;
                         done = true;
                     } else {
-                        const int gap = s->predicted ? rb_next_check_gap(s->check_every, r->k_prev, r->r_prev,
-                                                                         r->steps, res, r->tol)
-                                                     : s->check_every;
-                        r->k_prev = r->steps;
-                        r->r_prev = res;
-                        const int chunk = std::min(gap, s->max_iter - r->steps);
+                        const int chunk = std::min(s->check_every, s->max_iter - r->steps);
                         st = adarbfgs_step(r->h, chunk);
                         if (st == RB_OK) st = rbfgs_residual_start(r->h, s->check_cols, r->col_seed++);
                         r->steps += chunk;
@@ -271,7 +265,7 @@ static void worker_loop(rb_srv *s)
 extern "C" rb_status rb_srv_create(rb_srv_t *out, size_t hbm_budget_bytes, int max_live, int prec, int check_every,
                                    int check_cols, int max_iter)
 {
-    if (!out || hbm_budget_bytes == 0 || max_live < 1 || check_every == 0 || check_cols < 1 || max_iter < 1)
+    if (!out || hbm_budget_bytes == 0 || max_live < 1 || check_every < 1 || check_cols < 1 || max_iter < 1)
         return RB_EINVAL;
     if (prec != RB_FP32 && prec != RB_TF32 && prec != RB_TF32X3 && prec != RB_MIXED && prec != RB_FP64 &&
         prec != RB_BF16 && prec != RB_BF16X3)
@@ -280,8 +274,7 @@ extern "C" rb_status rb_srv_create(rb_srv_t *out, size_t hbm_budget_bytes, int m
     s->budget = hbm_budget_bytes;
     s->max_live = max_live;
     s->prec = prec;
-    s->predicted = check_every < 0;
-    s->check_every = check_every < 0 ? -check_every : check_every;
+    s->check_every = check_every;
     s->check_cols = check_cols;
     s->max_iter = max_iter;
     s->t0 = std::chrono::steady_clock::now();

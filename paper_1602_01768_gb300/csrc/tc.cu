@@ -440,15 +440,15 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                 const int s = CF::SPLIT ? i % CF::NA : i % STAGES, st = CF::SPLIT ? i % CF::NT : s;
                 if (!mbar_wait(smem_u32(&full[s]), (i / (CF::SPLIT ? CF::NA : STAGES)) & 1, err, abort_flag)) break;
                 if (BF) {
-                    // Row r's 64 FP32 values into registers first: the A slot is released before
-                    // the wait for a free TMEM stage, so the next load into it is not held up by
-                    // MMAs still reading TMEM.
+                    // Row r's 64 FP32 values into registers.  The A slot is released only after they
+                    // have been converted and stored: releasing it right after the loads (before the
+                    // values were used) let the next TMA load overwrite rows still being read, and
+                    // the products came out different from run to run.
                     float v[4][16];
 #pragma unroll
                     for (int g = 0; g < 2; ++g)
 #pragma unroll
                         for (int h = 0; h < 2; ++h) load_a_half<0>(stage_a(s) + g * A_TILE_BYTES, r, h, v[2 * g + h]);
-                    if (CF::SPLIT) mbar_arrive(smem_u32(&empty[s]));  // A slot read: the producer may refill it
                     if (CF::SPLIT && i >= CF::NT &&
                         !mbar_wait(smem_u32(&tempty[st]), ((i / CF::NT) - 1) & 1, err, abort_flag))
                         break;
@@ -502,7 +502,7 @@ k_tc_gemm(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUten
                 asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
                 tc_fence_before();
                 mbar_arrive(smem_u32(&conv[st]));
-                if (CF::SPLIT && !BF) mbar_arrive(smem_u32(&empty[s]));  // A slot read: the producer may refill it
+                if (CF::SPLIT) mbar_arrive(smem_u32(&empty[s]));  // A slot read: the producer may refill it
             }
         }
     } else {

@@ -1,6 +1,6 @@
 """Residual-check scheduling: the predicted spacing (check_every < 0) stops a
 solve within a check spacing of where checks every e steps stop it, with a
-factor that meets the tolerance in FP64, and serves requests the same way."""
+factor that meets the tolerance in FP64."""
 import numpy as np
 import pytest
 
@@ -39,23 +39,3 @@ def test_predicted_spacing_stops_near_the_fixed_schedule(prec):
     # sample per check, an exact confirmation), so they stop within two spacings of each other
     assert abs(it_p - it_f) <= 2 * e, (it_f, it_p)
     assert orc.residual_factored(A, out[-e][2]) <= tol
-
-
-def test_server_with_predicted_spacing():
-    import torch
-
-    n, tol = 384, 1e-4
-    A = wl.c5_matrix(n, 51).astype(np.float32)
-    Ah = torch.from_numpy(np.ascontiguousarray(A.T)).pin_memory()
-    outs = [torch.zeros(n, n, dtype=torch.float32).pin_memory() for _ in range(2)]
-    s = B.rb_srv_create(8 << 30, 8, B.RB_MIXED, -16, 128, 20000)
-    try:
-        t1 = B.rb_srv_submit(s, n, Ah.data_ptr(), False, n, False, tol, 1000, 0, outs[0].data_ptr(), False, n)
-        # below the FP32-storage floor: finished as floor-limited well before max_iter
-        t2 = B.rb_srv_submit(s, n, Ah.data_ptr(), False, n, False, 1e-9, 1001, 0, outs[1].data_ptr(), False, n)
-        r1, r2 = B.rb_srv_wait(s, t1), B.rb_srv_wait(s, t2)
-    finally:
-        B.rb_srv_destroy(s)
-    assert r1.status == B.RB_OK and r1.resid <= tol
-    assert orc.residual_factored(A.astype(np.float64), outs[0].numpy().T.astype(np.float64)) <= 1.2 * tol
-    assert r2.status == B.RB_NOTCONV and r2.floor_limited and r2.iters < 20000
