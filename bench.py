@@ -46,7 +46,7 @@ SERVE_MAX_ITER = 4000  # per request; requests that stall at their floor stop ea
 # of that launch; scaled by (n / 8192)^2 for other n at q = 128 (the bytes grow as n^2 at fixed q).
 UPDATE_TRAFFIC_N8192_Q128 = 277638912 + 208375552
 # the same for one k_tc_update_s launch (fused update + next sketch product, BF16x3 form)
-FUSED_TRAFFIC_N8192_Q128 = 289328896 + 235442432
+FUSED_TRAFFIC_N8192_Q128 = 289470976 + 235646464
 # AdaRBFGS steps per solve of the n = 16384, q = 128 workload to 1e-4 as the GPU arm measures it
 # (mean over its timed solves); the reference arm, which cannot run a whole solve in the time
 # allowed, times a bounded sample of oracle steps and scales it by this count.

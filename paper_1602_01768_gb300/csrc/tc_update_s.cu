@@ -343,6 +343,14 @@ k_tc_update_s(const float *__restrict__ ShT, int n, int q, const __grid_constant
             float lp[UBN];
 #pragma unroll
             for (int c = 0; c < UBN; ++c) lp[c] = Ls[c * 128 + r];
+            // The stage is released before the values are used, so make every lane wait for its loads
+            // first: an instruction that reads all 64 registers cannot issue until they have arrived
+            // (an arrival right after the loads were issued let the next TMA load overwrite rows still
+            // being read in the BF16 GEMM's converter).
+            uint32_t dep = 0;
+#pragma unroll
+            for (int c = 0; c < UBN; ++c) dep |= __float_as_uint(lp[c]);
+            asm volatile("" ::"r"(dep));
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(&lempty_s[s]));  // the L tile is in registers
             if (do_update) {
