@@ -89,10 +89,10 @@ def parse():
     ap.add_argument("--batch-steps", type=int, default=2000)
     ap.add_argument("--method", choices=["adarbfgs", "rbfgs", "aip"], default="adarbfgs",
                     help="method of the phases / plain modes (rbfgs and aip run the n = 4096 ridge Hessian, q = 64)")
-    ap.add_argument("--mode", choices=["bench", "phases", "plain"], default="bench",
+    ap.add_argument("--mode", choices=["bench", "phases", "plain", "batched"], default="bench",
                     help="phases: per-phase CUDA-event times of single AdaRBFGS steps (--prec may list forms, "
                          "comma-separated); plain: --warmup + --steps steps with no events, the form to put "
-                         "under a profiler")
+                         "under a profiler; batched: the batched coordinate-RBFGS workload alone")
     return ap.parse_args()
 
 
@@ -510,6 +510,16 @@ def run_exp1(B, wl, timed, st):
     return res
 
 
+def max_sm_mhz():
+    """The GPU's largest SM clock (nvidia-smi clocks.max.sm), else GB300's 2070 MHz."""
+    try:
+        out = subprocess.run(["nvidia-smi", "--id=0", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits"],
+                             capture_output=True, text=True, timeout=20).stdout.strip().splitlines()
+        return float(out[0])
+    except Exception:
+        return 2070.0
+
+
 def l2_probe_gbs():
     """L2 bandwidth probe: device copies of a 32 MB FP32 buffer into another (64 MB in all, resident in
     the 126 MB L2 after the first pass), 20 back to back between two CUDA events, read + write bytes
@@ -559,6 +569,14 @@ def run_batched(B, wl, args):
     moved = sum(it * 4 * (ni * ni + 6 * ni * qi) for it, ni, qi in zip(iters, n, q))
     achieved = moved / wall / 1e9
     l2 = l2_probe_gbs()
+    # FP32 work of a problem-step on the CUDA cores: Y = X G (2 n^2 q), T = G^T Y and W = -Y Lam
+    # (2 n q^2 each), B1 = (Lam + Lam T Lam) / 2 (4 q^3); peak = SMs x 128 FP32 lanes x 2 flops x the
+    # SM clock (the largest clock nvidia-smi reports for the GPU, else 2070 MHz)
+    flops = sum(it * (2.0 * ni * ni * qi + 4.0 * ni * qi * qi + 4.0 * qi ** 3) for it, ni, qi in zip(iters, n, q))
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = max_sm_mhz()
+    alu_peak = sms * 128 * 2 * mhz * 1e6 / 1e12
+    alu = flops / wall / 1e12
     # unconverged problems: steps predicted by the rate of coordinate sampling with trace
     # probabilities, rho = 1 - lambda_min / Tr A (Sec. 7.2; lambda_max = 1, lambda_min = 1 / kappa), and
     # whether tol lies below the FP32-storage floor of the exact inverse (~1.4e-9 kappa: 1.4e-5 at
@@ -576,9 +594,12 @@ def run_batched(B, wl, args):
                         f"at most {args.batch_steps} steps each",
             "tile_threads_per_cta": tile, "create_with_autotune_s": create_s,
             "converged": nconv, "problem_steps_per_s": steps / wall, "wall_s": wall,
-            "roofline": {"bound": "l2", "achieved": achieved, "peak": l2, "unit": "GB/s", "frac": achieved / l2,
-                         "peak_kind": "measured L2 copy probe (64 MB working set)",
-                         "bytes_per_problem_step": "4 (n^2 + 6 n q)"},
+            "roofline": {"bound": "alu", "achieved": alu, "peak": alu_peak, "unit": "TFLOP/s", "frac": alu / alu_peak,
+                         "peak_kind": f"FP32 CUDA-core FMA: {sms} SMs x 128 lanes x 2 flops x {mhz:.0f} MHz",
+                         "flops_per_problem_step": "2 n^2 q + 4 n q^2 + 4 q^3"},
+            "l2_roofline": {"bound": "l2", "achieved": achieved, "peak": l2, "unit": "GB/s", "frac": achieved / l2,
+                            "peak_kind": "measured L2 copy probe (64 MB working set)",
+                            "bytes_per_problem_step": "4 (n^2 + 6 n q)"},
             "median_resid": float(np.median(resid)), "max_resid": float(np.max(resid)),
             "unconverged": {"count": len(unconv),
                             "below_fp32_floor": sum(u["below_fp32_floor"] for u in unconv),
@@ -629,6 +650,15 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.mode == "batched":
+        import torch
+
+        import paper_1602_01768_gb300._binding as B
+        from paper_1602_01768_gb300 import workloads as wl
+
+        torch.cuda.set_device(0)
+        print(json.dumps({"batched": run_batched(B, wl, args)}), flush=True)
         return
     if args.mode != "bench":
         run_phases(args)

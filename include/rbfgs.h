@@ -326,7 +326,11 @@ rb_status rbfgs_destroy(rbfgs_t h);
  * (q_i in {4, 8, ..., 32}, a multiple of 4), Philox key `seed` and counter
  * stream stream_ids[i] (NULL: i), exactly as an rbfgs_init handle with
  * RB_SKETCH_COORD_TRACE would draw them.  Storage FP32, the q x q Cholesky in
- * FP64.  All problems advance in one persistent launch: CTAs pull problems
+ * FP64.  The blocks are a fixed partition, so every block's Cholesky factor and
+ * Lambda = A[C, C]^-1 are formed once, at creation (FP64, Lambda kept in FP32);
+ * a step that draws a block whose factorisation broke down (pivot <= 0 or
+ * non-finite) fails its problem with RB_ENOTSPD and leaves its iterate
+ * untouched.  All problems advance in one persistent launch: CTAs pull problems
  * from a device work queue (largest n first) and run the requested steps
  * on each; every problem is processed by one CTA in a fixed order, so its
  * iterates do not depend on the rest of the batch.  The round (steps, then a

@@ -8,6 +8,11 @@
 //   G = A[:, C], M = A[C, C], Y = X G, T = G^T Y, C C^T = M (FP64 Cholesky),
 //   Lam = M^-1, W = S (Lam + Lam T Lam)/2 - Y Lam,
 //   X[:, C] += W + (W[C, :])^T restricted to rows C, X[C, j] += W[j, :]^T (j not in C).
+// The blocks are a fixed partition of [n], so M, its Cholesky factor and Lam
+// depend only on the block: they are formed once per block when the batch is
+// created (FP64 factorisation, Lam stored FP32) and a step reads the drawn
+// block's Lam; a block whose Cholesky broke down makes the step that draws it
+// fail with ST_NOTSPD, exactly as a factorisation inside the step would.
 // A persistent grid pulls problems from an atomic work queue (largest n
 // first); a CTA runs `steps` steps on its problem before taking the next.
 // Every step of a problem runs in one CTA in a fixed order, so a problem's
@@ -28,15 +33,23 @@ namespace {
 constexpr int BT = 256;     // threads per CTA of the residual kernel
 constexpr int QMAX = 32;    // largest block
 constexpr int NMAX = 1024;  // largest problem
+constexpr int YK = 128;           // columns of X (rows of G) per staged block of the Y pass
+constexpr int GLD = QMAX + 4;     // row pitch of a staged G block (16-byte rows, 4-way bank spread)
+constexpr int GT_FLOATS = YK * GLD;  // staged G: YK x GLD (Y), q x 32 or q x 32 cpw <= 4096 (T waves)
+constexpr int PRE_WARPS = 2;     // warps (blocks) per CTA of the per-block factorisation
 
 struct BatchDev {
     const float *A;
     float *X;
-    const int64_t *off;  // element offset of problem i in A and X
+    const int64_t *off;  // element offset of problem i in A and X (a multiple of 4)
     const int *n, *q;
+    const int *ld;       // leading dimension of A_i and X_i: n_i rounded up to a multiple of 4
     const uint64_t *P;  // trace-weight prefix sums, nb_i + 1 entries each
     const int64_t *offP;
     const int *nb;
+    float *Lam;          // per block b of problem i: Lam_b = A[C_b, C_b]^-1, q x q (ld q)
+    const int64_t *offL; // element offset of problem i's blocks in Lam
+    int *bad;            // per block (offset offP[i]): 1 = its Cholesky broke down
     const uint64_t *stream;
     uint64_t *k;       // steps done
     const int *active; // 0 = skip
@@ -47,7 +60,7 @@ struct BatchDev {
     uint64_t seed;
 };
 
-__device__ void draw_block(const BatchDev &d, int p, int n, int q, uint64_t k, int &first, int &size)
+__device__ void draw_block(const BatchDev &d, int p, int n, int q, uint64_t k, int &first, int &size, int &blk)
 {
     const uint64_t *P = d.P + d.offP[p];
     const int nb = d.nb[p];
@@ -63,28 +76,96 @@ __device__ void draw_block(const BatchDev &d, int p, int n, int q, uint64_t k, i
         else
             hi = mid - 1;
     }
+    blk = lo;
     first = lo * q;
     size = ((lo + 1) * q <= n) ? q : n - lo * q;
 }
 
-// TB threads per CTA (the tile shape the autotuner picks: 256 or 512), NMAX / TB rows of
-// every problem per thread.  The order of every sum (Y row by row over k, T element by
-// element over i, the q x q products element by element) does not depend on TB, so
-// the iterates are the same for every shape.
+// One warp per (problem, block): M = A[C, C] padded with I to q x q (FP64), lower
+// Cholesky M = C C^T (row per lane), C^-1 (column per lane), Lam = C^-T C^-1 (FP64 sums,
+// stored FP32, ld q).  A pivot <= 0 or non-finite marks the block bad.
+__global__ void __launch_bounds__(32 * PRE_WARPS) k_batch_blocks(BatchDev d, const int2 *items, int nitems)
+{
+    __shared__ double Ms[PRE_WARPS][QMAX * QMAX];
+    __shared__ double Cs[PRE_WARPS][QMAX * QMAX];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int it = blockIdx.x * PRE_WARPS + w;
+    if (it >= nitems) return;  // the whole warp: only warp-level syncs below
+    const int p = items[it].x, blk = items[it].y;
+    const int n = d.n[p], q = d.q[p], ld = d.ld[p];
+    const int first = blk * q, size = min(q, n - first);
+    const float *A = d.A + d.off[p];
+    double *M = Ms[w], *Ci = Cs[w];
+    for (int e = lane; e < q * q; e += 32) {
+        const int a = e % q, b = e / q;
+        M[a + b * QMAX] = (a < size && b < size) ? (double)A[(first + a) + (int64_t)(first + b) * ld]
+                                                 : (a == b ? 1.0 : 0.0);
+    }
+    __syncwarp();
+    bool fail = false;
+    for (int j = 0; j < q; ++j) {
+        const double dj = M[j + j * QMAX];  // the same value in every lane
+        if (!(dj > 0.0) || !isfinite(dj)) {
+            fail = true;
+            break;
+        }
+        const double sd = sqrt(dj);
+        __syncwarp();
+        if (lane == j) M[j + j * QMAX] = sd;
+        if (lane > j && lane < q) M[lane + j * QMAX] /= sd;
+        __syncwarp();
+        if (lane > j && lane < q) {
+            const double lij = M[lane + j * QMAX];
+            for (int c = j + 1; c <= lane; ++c) M[lane + c * QMAX] -= lij * M[c + j * QMAX];
+        }
+        __syncwarp();
+    }
+    if (fail) {
+        if (lane == 0) d.bad[d.offP[p] + blk] = 1;
+        return;
+    }
+    if (lane < q) {
+        const int c = lane;
+        Ci[c + c * QMAX] = 1.0 / M[c + c * QMAX];
+        for (int i = c + 1; i < q; ++i) {
+            double t = 0.0;
+            for (int k = c; k < i; ++k) t += M[i + k * QMAX] * Ci[k + c * QMAX];
+            Ci[i + c * QMAX] = -t / M[i + i * QMAX];
+        }
+    }
+    __syncwarp();
+    float *L = d.Lam + d.offL[p] + (int64_t)blk * q * q;
+    for (int e = lane; e < q * q; e += 32) {
+        const int a = e % q, b = e / q;
+        double t = 0.0;
+        for (int k = max(a, b); k < q; ++k) t += Ci[k + a * QMAX] * Ci[k + b * QMAX];
+        L[a + b * q] = (float)t;
+    }
+}
+
+// TB threads per CTA (the tile shape the autotuner picks: 256 or 512), RPT = NMAX / TB
+// consecutive rows of every problem per thread (rows RPT t .. RPT t + RPT - 1), read from X
+// as one 16- or 8-byte vector per column.  The order of every sum does not depend on TB, so the
+// iterates are the same for every shape:
+//   Y = X G     row by row, k ascending;
+//   T = G^T Y   per (a, b): 32-row chunks summed k ascending, chunks added in ascending
+//               order to a running total (a wave of chunks is computed in parallel when
+//               q^2 < TB, but always added in chunk order);
+//   q x q products and W = S B1 - Y Lam element by element, inner index ascending.
 template <int TB>
 __global__ void __launch_bounds__(TB, 1) k_batch_rbfgs(BatchDev d, int steps)
 {
-    constexpr int BT = TB;
-    constexpr int RPT = NMAX / TB;  // rows per thread
+    constexpr int RPT = NMAX / TB;  // consecutive rows per thread
+    constexpr int KU = 8;           // columns of X loaded ahead per thread
+    constexpr int NPM = (QMAX * QMAX + TB - 1) / TB;
     extern __shared__ float bsm[];
-    float *Ys = bsm;                                  // n x q, ld n + 1 (Y, then W)
-    float *Gt = Ys + (NMAX + 1) * QMAX;               // 32 x QMAX tile of G rows
-    double *Md = (double *)(Gt + 32 * QMAX);          // QMAX x QMAX (M, then C)
-    float *Lam = (float *)(Md + QMAX * QMAX);         // QMAX x QMAX
-    float *Tm = Lam + QMAX * QMAX;                    // T, then Lam T
-    float *B1 = Tm + QMAX * QMAX;                     // (Lam + Lam T Lam) / 2
-    float *Ci = B1 + QMAX * QMAX;                     // C^-1
-    __shared__ int s_item, s_first, s_size, s_fail;
+    float *Ys = bsm;                     // n x q, ld ldy = ld + 4 (Y, then W); rows n .. ld - 1 are zero
+    float *Gt = Ys + (NMAX + 4) * QMAX;  // staged rows of G = A[:, C]
+    float *Lam = Gt + GT_FLOATS;         // QMAX x QMAX
+    float *Tm = Lam + QMAX * QMAX;       // T, then sym(T) Lam
+    float *B1 = Tm + QMAX * QMAX;        // (Lam + Lam T Lam) / 2
+    float *part = B1 + QMAX * QMAX;      // TB chunk sums of T (one wave)
+    __shared__ int s_item, s_first, s_size, s_blk, s_bad;
 
     const int tid = threadIdx.x;
     for (;;) {
@@ -95,201 +176,270 @@ __global__ void __launch_bounds__(TB, 1) k_batch_rbfgs(BatchDev d, int steps)
         if (item >= d.count) break;
         const int p = d.order[item];
         if (!d.active[p] || d.status[p]) continue;
-        const int n = d.n[p], q = d.q[p];
+        const int n = d.n[p], q = d.q[p], ld = d.ld[p];
         const float *A = d.A + d.off[p];
         float *X = d.X + d.off[p];
-        const int ldy = n + 1;
+        const int ldy = ld + 4;  // 16-byte columns
         for (int s = 0; s < steps; ++s) {
             if (tid == 0) {
-                int f, z;
-                draw_block(d, p, n, q, d.k[p], f, z);
+                int f, z, b;
+                draw_block(d, p, n, q, d.k[p], f, z, b);
                 s_first = f;
                 s_size = z;
-                s_fail = 0;
+                s_blk = b;
+                s_bad = d.bad[d.offP[p] + b];
             }
             __syncthreads();
             const int first = s_first, size = s_size;
-            // M = A[C, C] padded with I (FP64)
-            for (int e = tid; e < q * q; e += BT) {
-                const int a = e % q, b = e / q;
-                Md[a + b * QMAX] = (a < size && b < size) ? (double)A[(first + a) + (int64_t)(first + b) * n]
-                                                          : (a == b ? 1.0 : 0.0);
+            if (s_bad) {  // the drawn block's Cholesky broke down at creation: A is not SPD
+                if (tid == 0) atomicOr(&d.status[p], ST_NOTSPD);
+                __syncthreads();
+                break;
             }
-            // Y = X G, G = A[:, C]: rows i = tid + BT r
+            {
+                const float *Lg = d.Lam + d.offL[p] + (int64_t)s_blk * q * q;
+                for (int e = tid; e < q * q; e += TB) Lam[(e % q) + (e / q) * QMAX] = Lg[e];
+            }
+            // Y = X G, G = A[:, C]: rows i0 .. i0 + RPT - 1; KU columns of X in flight per thread
+            const int i0 = RPT * tid;
             float acc[RPT][QMAX];
 #pragma unroll
             for (int r = 0; r < RPT; ++r)
 #pragma unroll
                 for (int c = 0; c < QMAX; ++c) acc[r][c] = 0.f;
-            for (int k0 = 0; k0 < n; k0 += 32) {
+            auto load_x = [&](float (&xv)[KU][RPT], int k0, int kb, int kend) {
+#pragma unroll
+                for (int u = 0; u < KU; ++u) {
+                    const float *xp = X + i0 + (int64_t)(k0 + kb + u) * ld;
+                    const bool ok = i0 < n && kb + u < kend;
+                    if constexpr (RPT == 4) {
+                        const float4 v = ok ? *(const float4 *)xp : make_float4(0.f, 0.f, 0.f, 0.f);
+                        xv[u][0] = v.x;
+                        xv[u][1] = v.y;
+                        xv[u][2] = v.z;
+                        xv[u][3] = v.w;
+                    } else {
+                        const float2 v = ok ? *(const float2 *)xp : make_float2(0.f, 0.f);
+                        xv[u][0] = v.x;
+                        xv[u][1] = v.y;
+                    }
+                }
+            };
+            for (int k0 = 0; k0 < n; k0 += YK) {
+                const int kend = min(YK, n - k0);
+                float xv[KU][RPT];
+                load_x(xv, k0, 0, kend);  // in flight across the staging below
                 __syncthreads();
-                for (int e = tid; e < 32 * QMAX; e += BT) {
-                    const int kk = e % 32, c = e / 32;
-                    Gt[kk * QMAX + c] = (k0 + kk < n && c < size) ? A[(k0 + kk) + (int64_t)(first + c) * n] : 0.f;
+                for (int e = tid; e < YK * QMAX; e += TB) {
+                    const int kk = e % YK, c = e / YK;
+                    Gt[kk * GLD + c] = (kk < kend && c < size) ? A[(k0 + kk) + (int64_t)(first + c) * ld] : 0.f;
                 }
                 __syncthreads();
-                const int kend = min(32, n - k0);
-                for (int kk = 0; kk < kend; ++kk) {
-                    const float4 *g4 = (const float4 *)(Gt + kk * QMAX);
+                for (int kb = 0; kb < kend; kb += KU) {
+                    float xn[KU][RPT];  // next columns, loaded while these are used
+                    load_x(xn, k0, kb + KU, kend);
 #pragma unroll
-                    for (int r = 0; r < RPT; ++r) {
-                        const int i = tid + BT * r;
-                        if (i >= n) break;
-                        const float x = X[i + (int64_t)(k0 + kk) * n];
+                    for (int u = 0; u < KU; ++u) {
+                        const float4 *g4 = (const float4 *)(Gt + (kb + u) * GLD);
 #pragma unroll
                         for (int c4 = 0; c4 < QMAX / 4; ++c4) {
                             if (4 * c4 >= q) break;
                             const float4 g = g4[c4];
-                            acc[r][4 * c4] = fmaf(x, g.x, acc[r][4 * c4]);
-                            acc[r][4 * c4 + 1] = fmaf(x, g.y, acc[r][4 * c4 + 1]);
-                            acc[r][4 * c4 + 2] = fmaf(x, g.z, acc[r][4 * c4 + 2]);
-                            acc[r][4 * c4 + 3] = fmaf(x, g.w, acc[r][4 * c4 + 3]);
+#pragma unroll
+                            for (int r = 0; r < RPT; ++r) {
+                                acc[r][4 * c4] = fmaf(xv[u][r], g.x, acc[r][4 * c4]);
+                                acc[r][4 * c4 + 1] = fmaf(xv[u][r], g.y, acc[r][4 * c4 + 1]);
+                                acc[r][4 * c4 + 2] = fmaf(xv[u][r], g.z, acc[r][4 * c4 + 2]);
+                                acc[r][4 * c4 + 3] = fmaf(xv[u][r], g.w, acc[r][4 * c4 + 3]);
+                            }
                         }
                     }
+#pragma unroll
+                    for (int u = 0; u < KU; ++u)
+#pragma unroll
+                        for (int r = 0; r < RPT; ++r) xv[u][r] = xn[u][r];
                 }
             }
+            // Y rows i0 .. i0 + RPT - 1 as one vector per column; rows n .. ld - 1 get 0 (X's zero
+            // rows, or no loads at all), which the T pass below reads
+            if (i0 < ld) {
 #pragma unroll
-            for (int r = 0; r < RPT; ++r) {
-                const int i = tid + BT * r;
-                if (i >= n) break;
-#pragma unroll
-                for (int c = 0; c < QMAX; ++c)
-                    if (c < q) Ys[i + c * ldy] = acc[r][c];
+                for (int c = 0; c < QMAX; ++c) {
+                    if (c >= q) break;
+                    float *yp = Ys + i0 + c * ldy;
+                    if constexpr (RPT == 4)
+                        *(float4 *)yp = make_float4(acc[0][c], acc[1][c], acc[2][c], acc[3][c]);
+                    else
+                        *(float2 *)yp = make_float2(acc[0][c], acc[1][c]);
+                }
             }
             __syncthreads();
-            // T = G^T Y (FP32 over n rows, i ascending): G's rows staged 32 at a time like the
-            // Y pass, each (a, b) summed by one thread
+            // T = G^T Y in 32-row chunks (see above); a staged chunk holds G's columns
+            // contiguously (rows within a column), so both operands are read 4 rows at a time
             {
-                constexpr int NP = (QMAX * QMAX + BT - 1) / BT;
-                float t[NP];
+                const int P = q * q, nch = (n + 31) >> 5;
+                if (P >= TB) {  // one chunk per wave, ceil(P / TB) pairs per thread
+                    float tr[NPM];
 #pragma unroll
-                for (int u = 0; u < NP; ++u) t[u] = 0.f;
-                for (int i0 = 0; i0 < n; i0 += 32) {
-                    __syncthreads();
-                    for (int e = tid; e < 32 * QMAX; e += BT) {
-                        const int kk = e % 32, c = e / 32;
-                        Gt[kk * QMAX + c] = (i0 + kk < n && c < size) ? A[(i0 + kk) + (int64_t)(first + c) * n] : 0.f;
-                    }
-                    __syncthreads();
-                    const int kend = min(32, n - i0);
+                    for (int u = 0; u < NPM; ++u) tr[u] = 0.f;
+                    for (int c = 0; c < nch; ++c) {
+                        const int r0 = c * 32;
+                        __syncthreads();
+                        for (int e = tid; e < 32 * q; e += TB) {
+                            const int kk = e % 32, a = e / 32;
+                            Gt[a * 32 + kk] = (r0 + kk < n && a < size) ? A[(r0 + kk) + (int64_t)(first + a) * ld] : 0.f;
+                        }
+                        __syncthreads();
+                        const int k4 = (min(32, n - r0) + 3) >> 2;  // rows up to ld - 1: Y and G are zero there
 #pragma unroll
-                    for (int u = 0; u < NP; ++u) {
-                        const int e = tid + u * BT;
-                        if (e < q * q) {
-                            const int a = e % q, b = e / q;
-                            const float *yb = Ys + i0 + b * ldy;
-                            for (int kk = 0; kk < kend; ++kk) t[u] = fmaf(Gt[kk * QMAX + a], yb[kk], t[u]);
+                        for (int u = 0; u < NPM; ++u) {
+                            const int e = tid + u * TB;
+                            if (e < P) {
+                                const int a = e % q, b = e / q;
+                                const float4 *y4 = (const float4 *)(Ys + r0 + b * ldy);
+                                const float4 *g4 = (const float4 *)(Gt + a * 32);
+                                float in = 0.f;
+                                for (int kk = 0; kk < k4; ++kk) {
+                                    const float4 g = g4[kk], y = y4[kk];
+                                    in = fmaf(g.x, y.x, in);
+                                    in = fmaf(g.y, y.y, in);
+                                    in = fmaf(g.z, y.z, in);
+                                    in = fmaf(g.w, y.w, in);
+                                }
+                                tr[u] += in;
+                            }
                         }
                     }
-                }
 #pragma unroll
-                for (int u = 0; u < NP; ++u) {
-                    const int e = tid + u * BT;
-                    if (e < q * q) Tm[(e % q) + (e / q) * QMAX] = t[u];
-                }
-            }
-            // FP64 Cholesky of M (warp 0, row per lane)
-            if (tid < 32) {
-                const int lane = tid;
-                for (int j = 0; j < q; ++j) {
-                    const double dj = Md[j + j * QMAX];
-                    if (!(dj > 0.0) || !isfinite(dj)) {
-                        if (lane == 0) s_fail = 1;
-                        break;
+                    for (int u = 0; u < NPM; ++u) {
+                        const int e = tid + u * TB;
+                        if (e < P) Tm[(e % q) + (e / q) * QMAX] = tr[u];
                     }
-                    const double sd = sqrt(dj);
-                    __syncwarp();
-                    if (lane == j) Md[j + j * QMAX] = sd;
-                    if (lane > j && lane < q) Md[lane + j * QMAX] /= sd;
-                    __syncwarp();
-                    if (lane > j && lane < q) {
-                        const double lij = Md[lane + j * QMAX];
-                        for (int c = j + 1; c <= lane; ++c) Md[lane + c * QMAX] -= lij * Md[c + j * QMAX];
+                } else {  // cpw chunks per wave, one pair per thread, added in chunk order by the pair's owner
+                    const int cpw = TB / P, cr = 32 * cpw;
+                    const int j = tid / P, e = tid % P, a = e % q, b = e / q;
+                    const bool act = j < cpw;
+                    float tr = 0.f;
+                    for (int c0 = 0; c0 < nch; c0 += cpw) {
+                        __syncthreads();
+                        for (int f = tid; f < cr * q; f += TB) {
+                            const int row = f % cr, aa = f / cr;
+                            const int i = c0 * 32 + row;
+                            Gt[aa * cr + row] = (i < n && aa < size) ? A[i + (int64_t)(first + aa) * ld] : 0.f;
+                        }
+                        __syncthreads();
+                        if (act) {
+                            float in = 0.f;
+                            if (c0 + j < nch) {
+                                const int r0 = (c0 + j) * 32, k4 = (min(32, n - r0) + 3) >> 2;
+                                const float4 *y4 = (const float4 *)(Ys + r0 + b * ldy);
+                                const float4 *g4 = (const float4 *)(Gt + a * cr + j * 32);
+                                for (int kk = 0; kk < k4; ++kk) {
+                                    const float4 g = g4[kk], y = y4[kk];
+                                    in = fmaf(g.x, y.x, in);
+                                    in = fmaf(g.y, y.y, in);
+                                    in = fmaf(g.z, y.z, in);
+                                    in = fmaf(g.w, y.w, in);
+                                }
+                            }
+                            part[tid] = in;
+                        }
+                        __syncthreads();
+                        if (tid < P)
+                            for (int jj = 0; jj < cpw && c0 + jj < nch; ++jj) tr += part[jj * P + tid];
                     }
-                    __syncwarp();
-                }
-            }
-            __syncthreads();
-            if (s_fail) {
-                if (tid == 0) atomicOr(&d.status[p], ST_NOTSPD);
-                __syncthreads();
-                break;
-            }
-            // C^-1 (FP32, column per lane of warp 0)
-            if (tid < 32) {
-                const int c = tid;
-                for (int i = 0; i < QMAX; ++i) Ci[i + c * QMAX] = 0.f;
-                if (c < q) {
-                    Ci[c + c * QMAX] = (float)(1.0 / Md[c + c * QMAX]);
-                    for (int i = c + 1; i < q; ++i) {
-                        double t = 0.0;
-                        for (int k = c; k < i; ++k) t += Md[i + k * QMAX] * (double)Ci[k + c * QMAX];
-                        Ci[i + c * QMAX] = (float)(-t / Md[i + i * QMAX]);
-                    }
+                    if (tid < P) Tm[a + b * QMAX] = tr;
                 }
             }
             __syncthreads();
-            // Lam = C^-T C^-1
-            for (int e = tid; e < q * q; e += BT) {
-                const int a = e % q, b = e / q;
+            // B1 = (Lam + Lam T Lam) / 2: first Tm <- sym(T) Lam (via registers), then Lam (Tm)
+            float tl[NPM];
+#pragma unroll
+            for (int u = 0; u < NPM; ++u) {
+                const int e = tid + u * TB;
                 float t = 0.f;
-                for (int k = max(a, b); k < q; ++k) t = fmaf(Ci[k + a * QMAX], Ci[k + b * QMAX], t);
-                Lam[a + b * QMAX] = t;
+                if (e < q * q) {
+                    const int a = e % q, b = e / q;
+                    for (int k = 0; k < q; ++k)
+                        t = fmaf(0.5f * (Tm[a + k * QMAX] + Tm[k + a * QMAX]), Lam[k + b * QMAX], t);
+                }
+                tl[u] = t;
             }
             __syncthreads();
-            // B1 = (Lam + Lam T Lam) / 2: first Tm <- T Lam (in place via registers), then Lam (T Lam)
-            float tl[(QMAX * QMAX + BT - 1) / BT];
-            int ne = 0;
-            for (int e = tid; e < q * q; e += BT, ++ne) {
-                const int a = e % q, b = e / q;
-                float t = 0.f;
-                for (int k = 0; k < q; ++k) t = fmaf(0.5f * (Tm[a + k * QMAX] + Tm[k + a * QMAX]), Lam[k + b * QMAX], t);
-                tl[ne] = t;
+#pragma unroll
+            for (int u = 0; u < NPM; ++u) {
+                const int e = tid + u * TB;
+                if (e < q * q) Tm[(e % q) + (e / q) * QMAX] = tl[u];
             }
             __syncthreads();
-            ne = 0;
-            for (int e = tid; e < q * q; e += BT, ++ne) Tm[(e % q) + (e / q) * QMAX] = tl[ne];
-            __syncthreads();
-            for (int e = tid; e < q * q; e += BT) {
+            for (int e = tid; e < q * q; e += TB) {
                 const int a = e % q, b = e / q;
                 float t = 0.f;
                 for (int k = 0; k < q; ++k) t = fmaf(Lam[a + k * QMAX], Tm[k + b * QMAX], t);
                 B1[a + b * QMAX] = 0.5f * (Lam[a + b * QMAX] + t);
             }
             __syncthreads();
-            // W = -Y Lam + S B1, in place of Y (row-wise)
+            // W = -Y Lam + S B1, in place of Y (each thread its own rows, one vector per column)
+            if (i0 < n) {
+                float y[RPT][QMAX];
 #pragma unroll
-            for (int r = 0; r < RPT; ++r) {
-                const int i = tid + BT * r;
-                if (i >= n) break;
-                float y[QMAX];
-#pragma unroll
-                for (int c = 0; c < QMAX; ++c) y[c] = (c < q) ? Ys[i + c * ldy] : 0.f;
-                const int ri = i - first;
-#pragma unroll 4
+                for (int c = 0; c < QMAX; ++c) {
+                    if constexpr (RPT == 4) {
+                        const float4 v = c < q ? *(const float4 *)(Ys + i0 + c * ldy) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        y[0][c] = v.x;
+                        y[1][c] = v.y;
+                        y[2][c] = v.z;
+                        y[3][c] = v.w;
+                    } else {
+                        const float2 v = c < q ? *(const float2 *)(Ys + i0 + c * ldy) : make_float2(0.f, 0.f);
+                        y[0][c] = v.x;
+                        y[1][c] = v.y;
+                    }
+                }
                 for (int c = 0; c < q; ++c) {
-                    float w = 0.f;
+                    float w[RPT];
 #pragma unroll
-                    for (int b = 0; b < QMAX; ++b) w = fmaf(y[b], (b < q) ? Lam[b + c * QMAX] : 0.f, w);
-                    w = -w;
-                    if (ri >= 0 && ri < size) w += B1[ri + c * QMAX];
-                    Ys[i + c * ldy] = w;
+                    for (int r = 0; r < RPT; ++r) w[r] = 0.f;
+                    const float4 *l4 = (const float4 *)(Lam + c * QMAX);
+#pragma unroll
+                    for (int b4 = 0; b4 < QMAX / 4; ++b4) {
+                        if (4 * b4 >= q) break;
+                        const float4 l = l4[b4];
+#pragma unroll
+                        for (int r = 0; r < RPT; ++r) {
+                            w[r] = fmaf(y[r][4 * b4], l.x, w[r]);
+                            w[r] = fmaf(y[r][4 * b4 + 1], l.y, w[r]);
+                            w[r] = fmaf(y[r][4 * b4 + 2], l.z, w[r]);
+                            w[r] = fmaf(y[r][4 * b4 + 3], l.w, w[r]);
+                        }
+                    }
+#pragma unroll
+                    for (int r = 0; r < RPT; ++r) {
+                        w[r] = -w[r];
+                        const int ri = i0 + r - first;
+                        if (ri >= 0 && ri < size) w[r] += B1[ri + c * QMAX];
+                    }
+                    float *wp = Ys + i0 + c * ldy;
+                    if constexpr (RPT == 4)
+                        *(float4 *)wp = make_float4(w[0], w[1], w[2], w[3]);
+                    else
+                        *(float2 *)wp = make_float2(w[0], w[1]);
                 }
             }
             __syncthreads();
-            // X update: columns C (all rows) and rows C (columns outside C)
-#pragma unroll
-            for (int r = 0; r < RPT; ++r) {
-                const int i = tid + BT * r;
-                if (i >= n) break;
+            // X[:, C] += W + (W[C, :])^T on rows C: all rows, consecutive rows across a warp
+            for (int e = tid; e < n * size; e += TB) {
+                const int i = e % n, c = e / n;
                 const int ri = i - first;
-                for (int c = 0; c < size; ++c) {
-                    float dlt = Ys[i + c * ldy];
-                    if (ri >= 0 && ri < size) dlt += Ys[(first + c) + ri * ldy];
-                    X[i + (int64_t)(first + c) * n] += dlt;
-                }
-                if (ri < 0 || ri >= size)
-                    for (int c = 0; c < size; ++c) X[(first + c) + (int64_t)i * n] += Ys[i + c * ldy];
+                float dlt = Ys[i + c * ldy];
+                if (ri >= 0 && ri < size) dlt += Ys[(first + c) + ri * ldy];
+                X[i + (int64_t)(first + c) * ld] += dlt;
+            }
+            // X[C, j] += W[j, :]^T for columns j outside C: the q rows of a column across
+            // consecutive threads
+            for (int e = tid; e < q * n; e += TB) {
+                const int c = e % q, j = e / q;
+                if (c < size && (j < first || j >= first + size)) X[(first + c) + (int64_t)j * ld] += Ys[j + c * ldy];
             }
             __syncthreads();
             if (tid == 0) d.k[p] += 1;
@@ -306,7 +456,7 @@ __global__ void __launch_bounds__(BT) k_batch_resid(BatchDev d, int mcols, uint6
     __shared__ int J[64];
     __shared__ double red[BT];
     const int p = blockIdx.x;
-    const int n = d.n[p];
+    const int n = d.n[p], ld = d.ld[p];
     const int m = min(mcols, n);
     const float *A = d.A + d.off[p];
     const float *X = d.X + d.off[p];
@@ -327,7 +477,7 @@ __global__ void __launch_bounds__(BT) k_batch_resid(BatchDev d, int mcols, uint6
         const int j = J[jj];
         for (int i = threadIdx.x; i < n; i += BT) {
             float z = 0.f;
-            for (int k = 0; k < n; ++k) z = fmaf(X[i + (int64_t)k * n], A[k + (int64_t)j * n], z);
+            for (int k = 0; k < n; ++k) z = fmaf(X[i + (int64_t)k * ld], A[k + (int64_t)j * ld], z);
             const double e = ((i == j) ? 1.0 : 0.0) - (double)z;
             s += e * e;
         }
@@ -344,17 +494,16 @@ __global__ void __launch_bounds__(BT) k_batch_resid(BatchDev d, int mcols, uint6
 __global__ void k_batch_identity(BatchDev d)
 {
     const int p = blockIdx.y;
-    const int n = d.n[p];
+    const int n = d.n[p], ld = d.ld[p];
     float *X = d.X + d.off[p];
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)n * n;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)ld * n;
          e += (int64_t)gridDim.x * blockDim.x)
-        X[e] = ((e % n) == (e / n)) ? 1.f : 0.f;
+        X[e] = ((e % ld) == (e / ld)) ? 1.f : 0.f;  // rows n .. ld - 1 stay zero
 }
 
-constexpr size_t batch_smem()
+constexpr size_t batch_smem(int tb)
 {
-    return sizeof(float) * ((NMAX + 1) * QMAX + 32 * QMAX) + sizeof(double) * QMAX * QMAX +
-           sizeof(float) * 4 * QMAX * QMAX;
+    return sizeof(float) * ((NMAX + 4) * QMAX + GT_FLOATS + 3 * QMAX * QMAX + tb);
 }
 
 }  // namespace
@@ -362,12 +511,13 @@ constexpr size_t batch_smem()
 struct rb_batch {
     int count = 0;
     cudaStream_t st = nullptr;
-    std::vector<int> n, q, nb, order;
-    std::vector<int64_t> off, offP;
-    float *A = nullptr, *X = nullptr;
+    std::vector<int> n, q, nb, order, ld;
+    std::vector<int64_t> off, offP, offL;
+    float *A = nullptr, *X = nullptr, *Lam = nullptr;
     uint64_t *P = nullptr, *k = nullptr, *stream = nullptr;
-    int64_t *d_off = nullptr, *d_offP = nullptr;
-    int *d_n = nullptr, *d_q = nullptr, *d_nb = nullptr, *d_order = nullptr, *d_active = nullptr,
+    int64_t *d_off = nullptr, *d_offP = nullptr, *d_offL = nullptr;
+    int *d_bad = nullptr;
+    int *d_n = nullptr, *d_q = nullptr, *d_ld = nullptr, *d_nb = nullptr, *d_order = nullptr, *d_active = nullptr,
         *d_status = nullptr, *d_queue = nullptr;
     double *d_resid = nullptr;
     int tb = 256;                // threads per CTA of the step kernel (picked by the autotuner)
@@ -388,9 +538,13 @@ struct rb_batch {
         d.off = d_off;
         d.n = d_n;
         d.q = d_q;
+        d.ld = d_ld;
         d.P = P;
         d.offP = d_offP;
         d.nb = d_nb;
+        d.Lam = Lam;
+        d.offL = d_offL;
+        d.bad = d_bad;
         d.stream = stream;
         d.k = k;
         d.active = d_active;
@@ -407,8 +561,8 @@ static void batch_free(rb_batch *b)
 {
     if (!b) return;
     if (b->gexec) cudaGraphExecDestroy(b->gexec);
-    void *ptrs[] = {b->A, b->X, b->P, b->k, b->stream, b->d_off, b->d_offP, b->d_n, b->d_q, b->d_nb,
-                    b->d_order, b->d_active, b->d_status, b->d_queue, b->d_resid};
+    void *ptrs[] = {b->A, b->X, b->Lam, b->P, b->k, b->stream, b->d_off, b->d_offP, b->d_offL, b->d_bad, b->d_n,
+                    b->d_q, b->d_ld, b->d_nb, b->d_order, b->d_active, b->d_status, b->d_queue, b->d_resid};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (b->h_active) cudaFreeHost(b->h_active);
@@ -420,9 +574,9 @@ static void batch_free(rb_batch *b)
 static void launch_batch_step(rb_batch *b, cudaStream_t st, int steps)
 {
     if (b->tb == 512)
-        k_batch_rbfgs<512><<<b->grid, 512, batch_smem(), st>>>(b->dev(), steps);
+        k_batch_rbfgs<512><<<b->grid, 512, batch_smem(512), st>>>(b->dev(), steps);
     else
-        k_batch_rbfgs<256><<<b->grid, 256, batch_smem(), st>>>(b->dev(), steps);
+        k_batch_rbfgs<256><<<b->grid, 256, batch_smem(256), st>>>(b->dev(), steps);
 }
 
 // Tile-shape autotuner.  Candidates: 256 or 512 threads per CTA (4 or 2 rows of each
@@ -534,29 +688,46 @@ extern "C" rb_status rb_batch_create(rb_batch_t *out, int count, const int *n, c
     b->q.assign(q, q + count);
     b->off.resize(count);
     b->offP.resize(count);
+    b->offL.resize(count);
     b->nb.resize(count);
-    int64_t tot = 0, totP = 0;
+    b->ld.resize(count);
+    int64_t tot = 0, totP = 0, totL = 0;
+    std::vector<int2> items;  // (problem, block) pairs of the per-block factorisation
     for (int i = 0; i < count; ++i) {
+        b->ld[i] = (n[i] + 3) & ~3;  // 16-byte columns: rows RPT t .. are read as one vector
         b->off[i] = tot;
-        tot += (int64_t)n[i] * n[i];
+        tot += (int64_t)b->ld[i] * n[i];
         b->nb[i] = (n[i] + q[i] - 1) / q[i];
         b->offP[i] = totP;
         totP += b->nb[i] + 1;
+        b->offL[i] = totL;
+        totL += (int64_t)b->nb[i] * q[i] * q[i];
+        for (int c = 0; c < b->nb[i]; ++c) items.push_back(make_int2(i, c));
     }
     b->order.resize(count);
     std::iota(b->order.begin(), b->order.end(), 0);
     std::stable_sort(b->order.begin(), b->order.end(), [&](int x, int y) { return n[x] > n[y]; });
+    int2 *d_items = nullptr;
     bool ok = dalloc(&b->A, sizeof(float) * tot) && dalloc(&b->X, sizeof(float) * tot) &&
+              dalloc(&b->Lam, sizeof(float) * totL) && dalloc(&b->d_offL, sizeof(int64_t) * count) &&
+              dalloc(&b->d_bad, sizeof(int) * totP) && dalloc(&d_items, sizeof(int2) * items.size()) &&
               dalloc(&b->P, sizeof(uint64_t) * totP) && dalloc(&b->k, sizeof(uint64_t) * count) &&
               dalloc(&b->stream, sizeof(uint64_t) * count) && dalloc(&b->d_off, sizeof(int64_t) * count) &&
               dalloc(&b->d_offP, sizeof(int64_t) * count) && dalloc(&b->d_n, sizeof(int) * count) &&
-              dalloc(&b->d_q, sizeof(int) * count) && dalloc(&b->d_nb, sizeof(int) * count) &&
+              dalloc(&b->d_q, sizeof(int) * count) && dalloc(&b->d_ld, sizeof(int) * count) && dalloc(&b->d_nb, sizeof(int) * count) &&
               dalloc(&b->d_order, sizeof(int) * count) && dalloc(&b->d_active, sizeof(int) * count) &&
               dalloc(&b->d_status, sizeof(int) * count) && dalloc(&b->d_queue, sizeof(int)) &&
               dalloc(&b->d_resid, sizeof(double) * count) &&
               cudaMallocHost(&b->h_active, sizeof(int) * count) == cudaSuccess &&
               cudaMallocHost(&b->h_resid, sizeof(double) * count) == cudaSuccess &&
               cudaMallocHost(&b->h_status, sizeof(int) * count) == cudaSuccess;
+    struct ItemsFree {
+        int2 *p;
+        ~ItemsFree()
+        {
+            if (p) cudaFree(p);
+        }
+    } items_guard{d_items};  // the block list is needed only while the batch is created
     if (!ok) {
         cudaGetLastError();
         batch_free(b);
@@ -566,17 +737,23 @@ extern "C" rb_status rb_batch_create(rb_batch_t *out, int count, const int *n, c
     // pack A (FP32) and compute the trace weights of every problem's blocks
     std::vector<uint64_t> hP(totP);
     std::vector<double> diag;
+    if (cudaMemsetAsync(b->A, 0, sizeof(float) * tot, st) != cudaSuccess) {  // rows n .. ld - 1 stay zero
+        batch_free(b);
+        return RB_ECUDA;
+    }
     for (int i = 0; i < count; ++i) {
         if (a_is_fp64)
-            launch_copy2d<double, float>(st, n[i], n[i], (const double *)A_dev[i], lda[i], b->A + b->off[i], n[i], 1.0);
+            launch_copy2d<double, float>(st, n[i], n[i], (const double *)A_dev[i], lda[i], b->A + b->off[i], b->ld[i],
+                                         1.0);
         else
-            launch_copy2d<float, float>(st, n[i], n[i], (const float *)A_dev[i], lda[i], b->A + b->off[i], n[i], 1.0);
+            launch_copy2d<float, float>(st, n[i], n[i], (const float *)A_dev[i], lda[i], b->A + b->off[i], b->ld[i],
+                                        1.0);
     }
     // diagonals of the packed FP32 A (the values the kernels use)
     std::vector<float> hd;
     for (int i = 0; i < count; ++i) {
         hd.resize(n[i]);
-        if (cudaMemcpy2DAsync(hd.data(), sizeof(float), b->A + b->off[i], sizeof(float) * (n[i] + 1), sizeof(float),
+        if (cudaMemcpy2DAsync(hd.data(), sizeof(float), b->A + b->off[i], sizeof(float) * (b->ld[i] + 1), sizeof(float),
                               n[i], cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaStreamSynchronize(st) != cudaSuccess) {
             batch_free(b);
@@ -613,8 +790,15 @@ extern "C" rb_status rb_batch_create(rb_batch_t *out, int count, const int *n, c
                   cudaSuccess &&
               cudaMemcpyAsync(b->d_offP, b->offP.data(), sizeof(int64_t) * count, cudaMemcpyHostToDevice, st) ==
                   cudaSuccess &&
+              cudaMemcpyAsync(b->d_offL, b->offL.data(), sizeof(int64_t) * count, cudaMemcpyHostToDevice, st) ==
+                  cudaSuccess &&
+              cudaMemcpyAsync(d_items, items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice, st) ==
+                  cudaSuccess &&
+              cudaMemsetAsync(b->d_bad, 0, sizeof(int) * totP, st) == cudaSuccess &&
               cudaMemcpyAsync(b->d_n, n, sizeof(int) * count, cudaMemcpyHostToDevice, st) == cudaSuccess &&
               cudaMemcpyAsync(b->d_q, q, sizeof(int) * count, cudaMemcpyHostToDevice, st) == cudaSuccess &&
+              cudaMemcpyAsync(b->d_ld, b->ld.data(), sizeof(int) * count, cudaMemcpyHostToDevice, st) ==
+                  cudaSuccess &&
               cudaMemcpyAsync(b->d_nb, b->nb.data(), sizeof(int) * count, cudaMemcpyHostToDevice, st) ==
                   cudaSuccess &&
               cudaMemcpyAsync(b->d_order, b->order.data(), sizeof(int) * count, cudaMemcpyHostToDevice, st) ==
@@ -627,6 +811,9 @@ extern "C" rb_status rb_batch_create(rb_batch_t *out, int count, const int *n, c
         dim3 g(64, count);
         rb_count_launch();
         k_batch_identity<<<g, 256, 0, st>>>(b->dev());
+        const int nit = (int)items.size();
+        rb_count_launch();
+        k_batch_blocks<<<(nit + PRE_WARPS - 1) / PRE_WARPS, 32 * PRE_WARPS, 0, st>>>(b->dev(), d_items, nit);
         cp = cudaStreamSynchronize(st) == cudaSuccess;
     }
     if (!cp) {
@@ -635,8 +822,8 @@ extern "C" rb_status rb_batch_create(rb_batch_t *out, int count, const int *n, c
     }
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(k_batch_rbfgs<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_smem());
-        cudaFuncSetAttribute(k_batch_rbfgs<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_smem());
+        cudaFuncSetAttribute(k_batch_rbfgs<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_smem(256));
+        cudaFuncSetAttribute(k_batch_rbfgs<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)batch_smem(512));
         attr = true;
     }
     int sms = 0, dev = 0;
@@ -751,7 +938,7 @@ extern "C" rb_status rb_batch_solve(rb_batch_t b, double tol, int max_iter, int 
 extern "C" rb_status rb_batch_export(rb_batch_t b, int i, void *out_dev, int64_t ld)
 {
     if (!b || i < 0 || i >= b->count || !out_dev || ld < b->n[i]) return RB_EINVAL;
-    launch_copy2d<float, float>(b->st, b->n[i], b->n[i], b->X + b->off[i], b->n[i], (float *)out_dev, ld, 1.0);
+    launch_copy2d<float, float>(b->st, b->n[i], b->n[i], b->X + b->off[i], b->ld[i], (float *)out_dev, ld, 1.0);
     RB_CUDA(cudaGetLastError());
     return RB_OK;
 }

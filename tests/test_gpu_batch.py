@@ -115,3 +115,26 @@ def test_tile_shapes_give_the_same_iterates():
     finally:
         B.rb_batch_destroy(b1)
         B.rb_batch_destroy(b2)
+
+
+def test_batch_indefinite_block_fails_only_its_problem():
+    # positive diagonal (the trace weights are valid) but the 2 x 2 leading block [[1, 2], [2, 1]] is
+    # indefinite: the Cholesky of every block that contains it breaks down, so the first step of that
+    # problem reports RB_ENOTSPD and leaves its iterate at X0 = I; the other problem steps normally
+    import torch
+
+    n0 = 16
+    Abad = np.eye(n0)
+    Abad[0, 1] = Abad[1, 0] = 2.0
+    Agood, _, _ = wl.spd_spectrum(24, 10.0, 7)
+    probs = [(Abad, 4, 0.0), (Agood.astype(np.float32).astype(np.float64), 8, 10.0)]
+    b, n = _create(probs, 3)
+    try:
+        B.rb_batch_step(b, 40)
+        rc, iters, resid, status, nconv = B.rb_batch_solve(b, len(probs), 1e-30, 1, 1, 8)
+        assert status[0] == B.RB_ENOTSPD and status[1] != B.RB_ENOTSPD, status
+        assert np.array_equal(_export(b, 0, n[0]), np.eye(n0, dtype=np.float32))
+        _, X = orc.rbfgs_run(probs[1][0], np.eye(n[1]), 8, orc.SKETCH_COORD_TRACE, 3, 1, 0, 41)
+        assert rel(_export(b, 1, n[1]), X) <= 1e-4
+    finally:
+        B.rb_batch_destroy(b)
