@@ -59,6 +59,15 @@ DTYPE = {"bf16x3": "f32 storage, bf16x3 + tf32x3 products", "bf16": "f32 storage
 CORE_OPT = {"default": 0, "fp64": 1, "fp32": -1}
 
 
+def core_desc(args, prec, B):
+    """Which precision factored the two q x q matrices of the timed solves."""
+    if args.core == "fp64" or prec == B.RB_FP64:
+        return {"C (S^T A S)": "fp64", "D (S~^T S~)": "fp64"}
+    if args.core == "fp32" or prec == B.RB_FP32:
+        return {"C (S^T A S)": "fp32", "D (S~^T S~)": "fp32"}
+    return {"C (S^T A S)": "fp64 (8-CTA cluster beside W = G^T L)", "D (S~^T S~)": "fp32"}
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -805,7 +814,9 @@ def main():
     if not args.no_forms:
         if prec != B.RB_MIXED:
             forms["mixed_3xtf32"] = one_solve(B.RB_MIXED)
-        forms[f"{args.prec}_fp64_core"] = one_solve(prec, core=1)
+        # both q x q cores in FP64 (the D core on one CTA beside the update), and both in FP32
+        forms[f"{args.prec}_fp64_cores"] = one_solve(prec, core=1)
+        forms[f"{args.prec}_fp32_cores"] = one_solve(prec, core=-1)
         # AdaRBFGS_cols (Sec. 10): S = L[:, C] gathered, D = I
         forms[f"{args.prec}_cols"] = one_solve(prec, sketch=B.RB_SKETCH_COORD_UNIFORM)
 
@@ -884,7 +895,7 @@ def main():
                "data": "synthetic", "config": config(args), "form": args.prec,
                "time_to_tol_s": t_solve, "iters_per_solve": iters, "resid_final": resids,
                "latency_s": {"p50": statistics.median(lat), "p99": p99},
-               "core": "fp64" if args.core == "fp64" or prec == B.RB_FP64 else "fp32",
+               "core": core_desc(args, prec, B),
                "fp32_form": fp32, "forms": forms, "fp64_check": fp64_check,
                "roofline": roofline, "gemm_rooflines": gemm_rooflines, "phases_ms": phases, "step_ms": step_ms,
                "cpu_baseline": cpu, "cpu_scaling": cpu_scaling, "e2e": e2e, "clocks": clocks, "gpu_launches": launches,

@@ -99,8 +99,11 @@ typedef struct {
     uint64_t stream_id; /* Philox counter word 3: independent streams for one seed */
     int32_t power_iters;/* Newton-Schulz: power iterations for ||A||_2 (0 = 100) */
     int32_t core_fp64;  /* AdaRBFGS with FP32 storage, precision of the q x q Cholesky factors and
-                           their inverses: 1 = FP64, -1 = FP32, 0 = the form's default (FP32 for
-                           every FP32-storage form; FP64 storage always factors in FP64) */
+                           their inverses: 1 = FP64 (both), -1 = FP32 (both), 0 = the form's
+                           default: the tensor-core forms factor C C^T = S^T A S in FP64 (with
+                           q <= 128 and n a multiple of 4) and D D^T = S~^T S~ (a Gaussian Gram,
+                           condition number near 1) in FP32; RB_FP32 factors both in FP32; FP64
+                           storage always factors in FP64 */
     int32_t reserved[6];
 } rb_opts;
 
@@ -148,6 +151,20 @@ rb_status aip_step(rbfgs_t h, int nsteps);
  * V = D^-1 S~^T - C^-1 W, L += S C^-T V.  Asynchronous.
  */
 rb_status adarbfgs_step(rbfgs_t h, int nsteps);
+
+/*
+ * The q x q core of Algorithm 4 on its own, in FP64: the lower Cholesky
+ * factor C of the symmetric part of M (C C^T = (M + M^T) / 2; M is q x q FP32,
+ * column-major, ld q, device memory, q <= 128) and its inverse, written as
+ * s C^-T (FP32, ld ldo >= q, device memory): R = C^-T of Eq. (Cholimprov),
+ * scaled.  *cluster in 1 .. 8 asks for the CTAs to spread the FP64 work over
+ * (a thread-block cluster when it is more than 1); on return it holds the CTAs
+ * that ran (1 when no such cluster fits).  Every cluster size gives the same
+ * bits.  A pivot <= 0 or non-finite returns RB_ENOTSPD and leaves out_dev
+ * untouched.  Allocates one status word; synchronises the stream.
+ */
+rb_status rbfgs_core64(int q, const float *M_dev, float s, float *out_dev, int64_t ldo, int *cluster,
+                       void *stream);
 
 /*
  * Residual ||I - X A||_F / sqrt(n) of the current iterate (X = L L^T for

@@ -60,6 +60,7 @@ _SIGS = {
     "mr_init": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_void_p]),
     "mr_step": (C.c_int, [C.c_void_p, C.c_int]),
     "rbfgs_sigma": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "rbfgs_core64": (C.c_int, [C.c_int, C.c_void_p, C.c_float, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]),
     "rbfgs_sigma_noalloc": (C.c_int, [C.c_int, C.c_void_p, C.c_int64, C.c_int, C.c_int, C.c_void_p, C.c_void_p]),
     "rbfgs_load_host": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int]),
     "rbfgs_export_host": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_int64]),
@@ -236,6 +237,13 @@ def rbfgs_sigma(h):
     s = C.c_double()
     _check(_lib().rbfgs_sigma(h, C.byref(s)), "rbfgs_sigma")
     return s.value
+
+
+def rbfgs_core64(q, M_dev, s, out_dev, ldo, cluster=1, stream=0):
+    """Returns the CTAs that ran."""
+    c = C.c_int(cluster)
+    _check(_lib().rbfgs_core64(q, _p(M_dev), s, _p(out_dev), ldo, C.byref(c), _p(stream)), "rbfgs_core64")
+    return c.value
 
 
 def rbfgs_sigma_noalloc(n, A_dev, lda, a_is_fp64, power_iters=0, stream=0):

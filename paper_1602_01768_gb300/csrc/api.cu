@@ -15,6 +15,7 @@
 
 struct rb_ctx {
     int method = 0, sketch = 0, prec = 0, core_fp64 = 0;
+    int c_core64 = 0;  // the C core (S^T A S) in FP64 even when core_fp64 is 0 (the tensor forms' default)
     int n = 0, q = 0;
     bool f64 = false;
     uint64_t seed = 0, stream_id = 0, k = 0;
@@ -393,6 +394,9 @@ extern "C" rb_status rbfgs_init(rbfgs_t *out, int n, const void *A_dev, int64_t 
     // q x q core precision with FP32 storage: FP64 when asked (> 0), FP32 when asked (< 0),
     // else the form's default
     h->core_fp64 = opts->core_fp64 > 0 ? 1 : opts->core_fp64 < 0 ? 0 : default_core_fp64(prec);
+    // by default the tensor-core forms factor S^T A S in FP64 (on a CTA cluster, beside W = G^T L)
+    // and S~^T S~, a Gaussian Gram with condition number near 1, in FP32
+    h->c_core64 = h->core_fp64 || (opts->core_fp64 == 0 && prec != RB_FP32 && prec != RB_FP64);
     h->st = (cudaStream_t)stream;
     rb_status s = RB_OK;
     do {
@@ -810,6 +814,7 @@ static void ada_step_tc(rb_ctx *h)
     const bool fuse = tcv && upd == 1 && h->Spart && !cols;
     // the next step's D chain runs during this step's fused update
     const bool dpipe = fuse;
+    bool core_first = false;  // FP64 C core on a cluster before W (W then runs on the side stream)
     const bool d_now = tcv && !(dpipe && h->d_ready);  // this step's D chain still to run (during G)
     const int rsv_g = (fork && ((d_now && !cols) || !tcv)) ? SIDE_SMS_G : 0;
     // the side stream's Gram products run stream-K on the SIDE_SMS SMs the main GEMMs leave free
@@ -887,14 +892,36 @@ static void ada_step_tc(rb_ctx *h)
         if (gram_main) mark(h, "S^T G");
         cudaEventRecord(h->ev_g, st);
         cudaStreamWaitEvent(side, h->ev_g, 0);
-        if (tcv) {  // S^T A S = S^T G (3 x TF32) -> -C^-T into Bv, C^-T into Bs
+        core_first = tcv && gram_main && fuse && h->c_core64;
+        if (core_first) {
+            // FP64 C core on a cluster of SIDE_SMS CTAs.  A cluster needs all its SMs in one GPC: it
+            // is launched in stream order right after S^T G, so it is placed while the GPU is idle,
+            // and W = G^T L, on the low-priority side stream behind an event, takes the other SMs.
+            launch_core_tr64(st, q, h->Mf, h->Bv + cofs, 2 * q, -1.f, h->Bs, q, 1.f, h->d_status, SIDE_SMS);
+            if (bv_split(h)) tc_split_lo(st, q, q, h->Bv + cofs, 2 * q, h->Bvlo + cofs, 2 * q);
+            mark_side(h, st, "@C core done");
+            bool wbf_s = false;
+            if (bfterms) {
+                __nv_bfloat16_raw *gb = (__nv_bfloat16_raw *)h->Gbf;
+                if (!gbf) tc_split_bf16(side, n, q, G, n, gb, gb + bfhalf, h->ldbf);
+                wbf_s = tc_gemm_bf(h->tc, side, bfterms, n, q, n, L, n, gb, gb + bfhalf, h->ldbf, W, nullptr, n, stp,
+                                   rsv) == 0;
+            }
+            if (!wbf_s)
+                tc_gemm_nk_lo(h->tc, side, acc, TC_A_K, n, q, n, L, n, G, glo ? h->Glo : nullptr, n, W, nullptr, n,
+                              stp, rsv);
+            cudaEventRecord(h->ev_core, side);  // W done
+            // on the SMs the core frees while W runs: S^ = S C^-T and the next step's sketch
+            tc_gemm_nk_t(h->tc2, st, upd, TC_A_MN, n, q, q, S, n, h->Bs, q, Sh, q, stp);
+            ada_draw<float>(h, St_next, h->k + 1, st);
+        } else if (tcv) {  // S^T A S = S^T G (3 x TF32) -> -C^-T into Bv, C^-T into Bs
             if (!gram_main) {
                 tc_gemm_nk_lo(h->tc2, side, 3, TC_A_K, q, q, n, S, n, G, glo ? h->Glo : nullptr, n, h->Mf, nullptr,
                               q, stp, side_rsv);
                 mark_side(h, side, "@S^T G done");
             }
-            if (h->core_fp64)
-                launch_core_tr64(side, q, h->Mf, h->Bv + cofs, 2 * q, -1.f, h->Bs, q, 1.f, h->d_status);
+            if (h->c_core64)  // C C^T = S^T A S in FP64, spread over a cluster of the SIDE_SMS SMs W leaves free
+                launch_core_tr64(side, q, h->Mf, h->Bv + cofs, 2 * q, -1.f, h->Bs, q, 1.f, h->d_status, SIDE_SMS);
             else
                 launch_core_tr32(side, q, h->Mf, nullptr, h->Bv + cofs, 2 * q, -1.f, h->Bs, q, 1.f, h->d_status);
             if (bv_split(h)) tc_split_lo(side, q, q, h->Bv + cofs, 2 * q, h->Bvlo + cofs, 2 * q);
@@ -902,12 +929,14 @@ static void ada_step_tc(rb_ctx *h)
             launch_gram<float>(side, n, q, q, S, n, G, n, h->part, h->M);    // S^T A S -> C^-1
             launch_core_ada32(side, q, h->M, nullptr, Ci, nullptr, h->d_status);
         }
-        cudaEventRecord(h->ev_core, side);
-        mark_side(h, side, "@C core done");
+        if (!core_first) {
+            cudaEventRecord(h->ev_core, side);
+            mark_side(h, side, "@C core done");
+        }
         // off the main stream while it runs W's tail and V: S^ = S C^-T (it needs only S and the C
         // core) and the next step's sketch (its buffer is free: nothing of this step reads it); only
         // the fused update waits for them
-        if (fuse) {
+        if (fuse && !core_first) {
             tc_gemm_nk_t(h->tc2, side, upd, TC_A_MN, n, q, q, S, n, h->Bs, q, Sh, q, stp);
             ada_draw<float>(h, St_next, h->k + 1, side);
             cudaEventRecord(h->ev_g, side);
@@ -922,8 +951,8 @@ static void ada_step_tc(rb_ctx *h)
             launch_core_ada<float>(st, q, h->M, h->N, Ci, Di, h->d_status);
         mark(h, "q x q core");
     }
-    bool wbf = false;
-    if (bfterms) {  // W^T = L^T G on G's BF16 parts (written by G's epilogue unless G fell back)
+    bool wbf = core_first;  // W already launched on the side stream
+    if (bfterms && !core_first) {  // W^T = L^T G on G's BF16 parts (written by G's epilogue unless G fell back)
         __nv_bfloat16_raw *gb = (__nv_bfloat16_raw *)h->Gbf;
         if (!gbf) tc_split_bf16(st, n, q, G, n, gb, gb + bfhalf, h->ldbf);
         wbf = tc_gemm_bf(h->tc, st, bfterms, n, q, n, L, n, gb, gb + bfhalf, h->ldbf, W, nullptr, n, stp, rsv) == 0;
@@ -931,7 +960,7 @@ static void ada_step_tc(rb_ctx *h)
     if (!wbf)
         tc_gemm_nk_lo(h->tc, st, acc, TC_A_K, n, q, n, L, n, G, glo ? h->Glo : nullptr, n, W, nullptr, n, stp,
                       rsv);  // W^T = L^T G (n x q)
-    if (fork) {  // join: C^-1 and D^-1 ready
+    if (fork) {  // join: C^-1 (or, with the core first, W) and D^-1 ready
         cudaStreamWaitEvent(st, h->ev_core, 0);
         if (tcv) cudaStreamWaitEvent(st, h->ev_d, 0);
     }
@@ -1481,6 +1510,31 @@ extern "C" rb_status rbfgs_sigma(rbfgs_t h, double *sigma)
     if (!h || !sigma || h->method != RB_METHOD_NS) return RB_EINVAL;
     *sigma = h->host_sigma;
     return RB_OK;
+}
+
+extern "C" rb_status rbfgs_core64(int q, const float *M_dev, float s, float *out_dev, int64_t ldo, int *cluster,
+                                void *stream)
+{
+    if (q < 1 || q > 128 || !M_dev || !out_dev || ldo < q || ldo > INT32_MAX || !cluster || *cluster < 1 ||
+        *cluster > 8)
+        return RB_EINVAL;
+    cudaStream_t st = (cudaStream_t)stream;
+    int *d_st = nullptr;
+    if (cudaMalloc(&d_st, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        return RB_ENOMEM;
+    }
+    int used = 0, hs = 0;
+    rb_status r = RB_OK;
+    if (cudaMemsetAsync(d_st, 0, sizeof(int), st) != cudaSuccess ||
+        (used = launch_core_tr64(st, q, M_dev, out_dev, (int)ldo, s, nullptr, 0, 0.f, d_st, *cluster)) == 0 ||
+        cudaMemcpyAsync(&hs, d_st, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        r = RB_ECUDA;
+    cudaFree(d_st);
+    if (r != RB_OK) return r;
+    *cluster = used;
+    return (hs & ST_NOTSPD) ? RB_ENOTSPD : (hs & ST_NONFINITE) ? RB_ENONFINITE : RB_OK;
 }
 
 extern "C" rb_status mr_init(rbfgs_t *out, int n, const void *A_dev, int64_t lda, int a_is_fp64, int prec,

@@ -6,10 +6,11 @@
 //
 // The algorithm is the blocked right-looking one of k_core_blk in core32.cu
 // (32 x 32 blocks, q padded to 32 nb with the identity): per block column p,
-// warp 0 factors and inverts the diagonal block, all threads form the panel
+// the CTA factors and inverts the diagonal block (diag_block), all threads form the panel
 // L_ip = A_ip X_pp^T and the trailing update A_ij -= L_ip L_jp^T; then the
 // off-diagonal blocks of X = L^-1 follow by block diagonals d,
 // T = sum_{k=j}^{i-1} L_ik X_kj, X_ij = -X_ii T (i = j + d).
+// k_core_cl64 below spreads the same work over a cluster of CTAs.
 // In FP64 the unpacked 128 x 129 layout of two matrices would not fit in
 // shared memory, so both A (overwritten by L) and X keep only their lower
 // block triangle, each block 32 x 33 (padded rows), and T has a scratch of
@@ -44,6 +45,73 @@ struct Core64Out {
     float s2;
 };
 
+// 1 / sqrt(d) in FP64 for a pivot d > 0: an FP32 estimate refined by two Newton-Raphson steps on
+// f(y) = y^-2 - d, y <- y (3 - d y^2) / 2, each of which about doubles the number of correct bits
+// (FP32's ~23 -> ~46 -> the FP64 rounding level).  GB300's FP64 units are few; this takes fewer
+// dependent FP64 operations than a square root followed by a division.  Outside [1e-30, 1e30] (or
+// not finite) it takes sqrt and a division instead.
+__device__ __forceinline__ double rsqrt_nr(double d)
+{
+    if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
+    double y = (double)rsqrtf((float)d);
+    const double h = 0.5 * d;
+    y = y * (1.5 - h * y * y);
+    y = y * (1.5 - h * y * y);
+    return y;
+}
+
+// Diagonal block p (rows and columns o .. o + 31, o = 32 p) of the block-packed matrices:
+// L_pp in place of A_pp (lower Cholesky) and X_pp = L_pp^-1, by all KT64 threads of the CTA.
+// One thread takes each pivot's reciprocal square root (rsqrt_nr; GB300 runs FP64 at a small
+// fraction of its FP32 rate, so the other warps do not repeat it: L_jj = d / sqrt(d), the column
+// below it scaled by 1 / sqrt(d) in the same warp), then the block's trailing elements are updated
+// one per thread.  X_pp is formed right-looking: row k is
+// finished by the stored reciprocal of L_kk, then every later row subtracts L_ik X_kc -- for each
+// element the same operations, in the same order, as a forward substitution down its column.
+// Sets *bad when a pivot is not positive and finite (the same in every thread).  invd: 32 doubles.
+__device__ void diag_block(double *a, double *x, int nb, int o, double *invd, int *bad)
+{
+    const int tid = threadIdx.x;
+    for (int j = 0; j < 32; ++j) {
+        if (tid < 32) {  // warp 0: pivot (lane 0) and column j scaled (lanes below the diagonal)
+            double inv = 0.0;
+            if (tid == 0) {
+                const double d = pk(a, nb, o + j, o + j);
+                if (!(d > 0.0) || !isfinite(d)) *bad = 1;
+                inv = rsqrt_nr(d);
+                invd[j] = inv;
+                pk(a, nb, o + j, o + j) = d * inv;
+            }
+            inv = __shfl_sync(0xffffffffu, inv, 0);
+            if (tid > j) pk(a, nb, o + tid, o + j) = pk(a, nb, o + tid, o + j) * inv;
+        }
+        __syncthreads();
+        for (int e = tid; e < 1024; e += KT64) {  // element (r, c), j < c <= r < 32
+            const int r = e >> 5, c = e & 31;
+            if (r > j && c > j && c <= r) {
+                const double lij = pk(a, nb, o + r, o + j);
+                pk(a, nb, o + r, o + c) -= lij * pk(a, nb, o + c, o + j);
+            }
+        }
+        __syncthreads();
+    }
+    if (*bad) return;  // read after the last barrier: the same in every thread
+    for (int e = tid; e < 1024; e += KT64) {
+        const int r = e & 31, c = e >> 5;
+        pk(x, nb, o + r, o + c) = (r == c) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    for (int k = 0; k < 32; ++k) {
+        if (tid <= k) pk(x, nb, o + k, o + tid) = pk(x, nb, o + k, o + tid) * invd[k];
+        __syncthreads();
+        for (int e = tid; e < 1024; e += KT64) {  // X_ic -= L_ik X_kc, i > k >= c
+            const int i = e >> 5, c = e & 31;
+            if (i > k && c <= k) pk(x, nb, o + i, o + c) -= pk(a, nb, o + i, o + k) * pk(x, nb, o + k, o + c);
+        }
+        __syncthreads();
+    }
+}
+
 __global__ void __launch_bounds__(KT64, 1) k_core_blk64(int q, Core64Out out, int *status)
 {
     extern __shared__ double smd[];
@@ -52,8 +120,9 @@ __global__ void __launch_bounds__(KT64, 1) k_core_blk64(int q, Core64Out out, in
     double *x = smd + NPACK * BLK;   // X = L^-1
     double *t = smd + 2 * NPACK * BLK;  // T blocks of the current block diagonal
     __shared__ int fail;
+    __shared__ double invd[32];
     if (status_bad(status)) return;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tid = threadIdx.x;
     if (tid == 0) fail = 0;
     // symmetric part of the padded matrix, lower block triangle only (identity padding)
     for (int e = tid; e < QP * QP; e += KT64) {
@@ -69,36 +138,7 @@ __global__ void __launch_bounds__(KT64, 1) k_core_blk64(int q, Core64Out out, in
     __syncthreads();
     for (int p = 0; p < nb; ++p) {
         const int o = 32 * p;
-        if (warp == 0) {
-            // diagonal block: L_pp in place (lane = row)
-            bool bad = false;
-            for (int j = 0; j < 32; ++j) {
-                const double d = pk(a, nb, o + j, o + j);
-                bad = bad || !(d > 0.0) || !isfinite(d);
-                const double sd = sqrt(d), inv = 1.0 / sd;
-                double lij = 0.0;
-                if (lane > j) {
-                    lij = pk(a, nb, o + lane, o + j) * inv;
-                    pk(a, nb, o + lane, o + j) = lij;
-                } else if (lane == j) {
-                    pk(a, nb, o + j, o + j) = sd;
-                }
-                __syncwarp();
-                for (int c = j + 1; c <= lane; ++c) pk(a, nb, o + lane, o + c) -= lij * pk(a, nb, o + c, o + j);
-                __syncwarp();
-            }
-            if (bad) {
-                if (lane == 0) fail = 1;
-            } else {
-                // X_pp = L_pp^-1 (lane = column), zeros above the diagonal of the block
-                for (int i = 0; i < 32; ++i) {
-                    double s = (i == lane) ? 1.0 : 0.0;
-                    for (int k = lane; k < i; ++k) s -= pk(a, nb, o + i, o + k) * pk(x, nb, o + k, o + lane);
-                    pk(x, nb, o + i, o + lane) = (i >= lane) ? s / pk(a, nb, o + i, o + i) : 0.0;
-                }
-            }
-        }
-        __syncthreads();
+        diag_block(a, x, nb, o, invd, &fail);
         if (fail) {
             if (tid == 0) atomicOr(status, ST_NOTSPD);
             return;
@@ -174,20 +214,210 @@ __global__ void __launch_bounds__(KT64, 1) k_core_blk64(int q, Core64Out out, in
     }
 }
 
+// The same factorisation and inverse on a cluster of CL CTAs (q <= 128).  Every CTA keeps a
+// full copy of A (-> L), X and T in its shared memory.  The diagonal blocks are factored and
+// inverted by every CTA alike (identical work on identical copies, so every CTA takes the same
+// branch on a failed pivot); the panel, the trailing update and the off-diagonal blocks of X are
+// split over the cluster's threads, and each element, computed by one thread exactly as in
+// k_core_blk64, is written to every CTA's copy through distributed shared memory before a
+// cluster barrier.  The results are bit-identical to k_core_blk64; the FP64 work of the panels,
+// updates and off-diagonal blocks is spread over CL SMs.
+__device__ __forceinline__ void cl_sync()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ uint32_t cl_rank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+__device__ __forceinline__ uint32_t cl_nrank()
+{
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+
+// Shared-memory address of `local` in the CTA of cluster rank r.
+__device__ __forceinline__ uint32_t cl_map(const void *local, uint32_t r)
+{
+    uint32_t out;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(out) : "r"((uint32_t)__cvta_generic_to_shared(local)), "r"(r));
+    return out;
+}
+
+__device__ __forceinline__ void cl_st(uint32_t addr, double v)
+{
+    asm volatile("st.shared::cluster.f64 [%0], %1;" ::"r"(addr), "d"(v) : "memory");
+}
+
+// *p = v in every CTA of the cluster (p points into this CTA's shared memory)
+__device__ __forceinline__ void put_all(double *p, double v, uint32_t ncl)
+{
+    for (uint32_t r = 0; r < ncl; ++r) cl_st(cl_map(p, r), v);
+}
+
+__global__ void __launch_bounds__(KT64, 1) k_core_cl64(int q, Core64Out out, int *status)
+{
+    extern __shared__ double smd[];
+    const int nb = (q + 31) / 32, QP = 32 * nb;
+    double *a = smd;
+    double *x = smd + NPACK * BLK;
+    double *t = smd + 2 * NPACK * BLK;
+    __shared__ int flag;
+    __shared__ double invd[32];
+    const int tid = threadIdx.x;
+    const uint32_t rank = cl_rank(), ncl = cl_nrank();
+    const int gt = (int)rank * KT64 + tid, gstride = (int)ncl * KT64;  // this thread's share of the cluster's work
+    // one reading of the status word for the whole cluster (rank 0's), so that every CTA takes
+    // the same path through the cluster barriers below
+    if (tid == 0) flag = (rank == 0 && status_bad(status)) ? 1 : 0;
+    cl_sync();
+    if (tid == 0 && rank != 0) {
+        int v;
+        asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(cl_map(&flag, 0)) : "memory");
+        flag = v;
+    }
+    cl_sync();  // rank 0's flag read everywhere before any CTA may leave
+    if (flag) return;
+    for (int e = tid; e < QP * QP; e += KT64) {  // every copy loads the same symmetric part
+        const int i = e % QP, j = e / QP;
+        if ((i >> 5) < (j >> 5)) continue;
+        double v;
+        if (i < q && j < q)
+            v = 0.5 * ((double)out.src[i + (size_t)j * q] + (double)out.src[j + (size_t)i * q]);
+        else
+            v = (i == j) ? 1.0 : 0.0;
+        pk(a, nb, i, j) = v;
+    }
+    if (tid == 0) flag = 0;
+    __syncthreads();
+    for (int p = 0; p < nb; ++p) {
+        const int o = 32 * p;
+        diag_block(a, x, nb, o, invd, &flag);  // in every CTA alike
+        if (flag) {  // the same in every CTA (same data, same operations)
+            if (tid == 0 && rank == 0) atomicOr(status, ST_NOTSPD);
+            return;
+        }
+        // panel: L_ip = A_ip X_pp^T, i > p (every value computed before any copy is written)
+        const int npanel = (nb - 1 - p) * 1024;
+        constexpr int PV = (3 * 1024 + KT64 * 2 - 1) / (KT64 * 2);  // values per thread (clusters of >= 2 CTAs)
+        double pv[PV];
+#pragma unroll
+        for (int u = 0; u < PV; ++u) {
+            const int e = gt + u * gstride;
+            pv[u] = 0.0;
+            if (e < npanel) {
+                const int blk = e >> 10, w = e & 1023, r = w & 31, c = w >> 5;
+                const int i = o + 32 * (blk + 1) + r;
+                double s = 0.0;
+                for (int k = 0; k <= c; ++k) s += pk(a, nb, i, o + k) * pk(x, nb, o + c, o + k);
+                pv[u] = s;
+            }
+        }
+        cl_sync();
+#pragma unroll
+        for (int u = 0; u < PV; ++u) {
+            const int e = gt + u * gstride;
+            if (e < npanel) {
+                const int blk = e >> 10, w = e & 1023, r = w & 31, c = w >> 5;
+                put_all(&pk(a, nb, o + 32 * (blk + 1) + r, o + c), pv[u], ncl);
+            }
+        }
+        cl_sync();
+        // trailing update: A_ij -= L_ip L_jp^T over the lower block triangle p < bj <= bi
+        const int m = nb - 1 - p;
+        const int ntr = m * (m + 1) / 2 * 1024;
+        for (int e = gt; e < ntr; e += gstride) {
+            int blk = e >> 10, bj = 0;
+            while (blk >= m - bj) {
+                blk -= m - bj;
+                ++bj;
+            }
+            const int bi = bj + blk, w = e & 1023, r = w & 31, c = w >> 5;
+            const int i = o + 32 * (bi + 1) + r, j = o + 32 * (bj + 1) + c;
+            double s = 0.0;
+            for (int k = 0; k < 32; ++k) s += pk(a, nb, i, o + k) * pk(a, nb, j, o + k);
+            double &dst = pk(a, nb, i, j);
+            put_all(&dst, dst - s, ncl);
+        }
+        cl_sync();
+    }
+    // off-diagonal blocks of X by block diagonals
+    for (int d = 1; d < nb; ++d) {
+        const int nt = (nb - d) * 1024;
+        for (int e = gt; e < nt; e += gstride) {  // T_j = sum_{k=j}^{j+d-1} L_(j+d, k) X_(k, j)
+            const int bj = e >> 10, w = e & 1023, r = w & 31, c = w >> 5, bi = bj + d;
+            double s = 0.0;
+            for (int bk = bj; bk < bi; ++bk)
+                for (int k = 0; k < 32; ++k) s += pk(a, nb, 32 * bi + r, 32 * bk + k) * pk(x, nb, 32 * bk + k, 32 * bj + c);
+            put_all(&t[bj * BLK + r + c * BLD], s, ncl);
+        }
+        cl_sync();
+        for (int e = gt; e < nt; e += gstride) {  // X_(j+d, j) = -X_(j+d, j+d) T_j
+            const int bj = e >> 10, w = e & 1023, r = w & 31, c = w >> 5, bi = bj + d;
+            double s = 0.0;
+            for (int k = 0; k <= r; ++k) s += pk(x, nb, 32 * bi + r, 32 * bi + k) * t[bj * BLK + k + c * BLD];
+            put_all(&pk(x, nb, 32 * bi + r, 32 * bj + c), -s, ncl);
+        }
+        cl_sync();
+    }
+    for (int e = gt; e < q * q; e += gstride) {
+        const int r = e % q, c = e / q;
+        const double w = (c >= r) ? pk(x, nb, c, r) : 0.0;
+        if (!isfinite(w)) atomicOr(status, ST_NONFINITE);
+        if (out.xt1) out.xt1[r + (size_t)c * out.ld1] = (float)(out.s1 * w);
+        if (out.xt2) out.xt2[r + (size_t)c * out.ld2] = (float)(out.s2 * w);
+    }
+}
+
 }  // namespace
 
-bool launch_core_tr64(cudaStream_t st, int q, const float *M, float *xt1, int ld1, float s1, float *xt2, int ld2,
-                      float s2, int *status)
+int launch_core_tr64(cudaStream_t st, int q, const float *M, float *xt1, int ld1, float s1, float *xt2, int ld2,
+                     float s2, int *status, int cluster)
 {
-    if (q > 32 * NBMAX) return false;
+    if (q > 32 * NBMAX) return 0;
     static bool attr = false;
     const size_t smem = sizeof(double) * (2 * NPACK + (NBMAX - 1)) * BLK;
+    const Core64Out o{M, xt1, ld1, s1, xt2, ld2, s2};
+    static int cl_ok = -1;  // 1 when a cluster of `cluster` CTAs of this kernel can be resident at all
+    if (cluster > 1 && cl_ok != 0) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(cluster, 1, 1);
+        cfg.blockDim = dim3(KT64, 1, 1);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = cluster;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        if (cl_ok < 0) {
+            int nclus = 0;
+            cl_ok = cudaFuncSetAttribute(k_core_cl64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) ==
+                            cudaSuccess &&
+                        cudaOccupancyMaxActiveClusters(&nclus, k_core_cl64, &cfg) == cudaSuccess && nclus > 0
+                    ? 1
+                    : 0;
+            cudaGetLastError();
+        }
+        if (cl_ok == 1) {
+            rb_count_launch();
+            if (cudaLaunchKernelEx(&cfg, k_core_cl64, q, o, status) == cudaSuccess) return cluster;
+            cudaGetLastError();  // not launched: one CTA below
+        }
+    }
     if (!attr) {
         if (cudaFuncSetAttribute(k_core_blk64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
-            return false;
+            return 0;
         attr = true;
     }
     rb_count_launch();
-    k_core_blk64<<<1, KT64, smem, st>>>(q, Core64Out{M, xt1, ld1, s1, xt2, ld2, s2}, status);
-    return true;
+    k_core_blk64<<<1, KT64, smem, st>>>(q, o, status);
+    return 1;
 }

@@ -36,9 +36,11 @@ void launch_core_ada32(cudaStream_t, int q, const double *M, const double *N, fl
 bool launch_core_tr32(cudaStream_t, int q, const float *M, float *Xinv, float *xt1, int ld1, float s1, float *xt2,
                       int ld2, float s2, int *status);
 // q <= 128: the same in FP64 (core64.cu): X = L^-1 of sym(M) factored and inverted in
-// FP64, written only as the scaled FP32 transposes s1 X^T / s2 X^T.
-bool launch_core_tr64(cudaStream_t, int q, const float *M, float *xt1, int ld1, float s1, float *xt2, int ld2,
-                      float s2, int *status);
+// FP64, written only as the scaled FP32 transposes s1 X^T / s2 X^T; cluster > 1 spreads the
+// work over a cluster of that many CTAs (one CTA when no such cluster fits), with the same result.
+// Returns the CTAs it launched (0: q > 128 or no launch).
+int launch_core_tr64(cudaStream_t, int q, const float *M, float *xt1, int ld1, float s1, float *xt2, int ld2,
+                     float s2, int *status, int cluster = 1);
 // q <= 64: the RBFGS / AIP core (FP64) from FP32 Gram matrices, packed as the 2q x q B operand
 // [B1; -Lam] (Tf given: RBFGS) or [Lam; -Lam] (Tf null: AIP), ld 2q; scratch: 3 q^2 doubles.
 void launch_core_pack(cudaStream_t, int q, const float *Mf, const float *Tf, float *Bw, double *scratch,

@@ -730,3 +730,37 @@ def test_checkpoint_resume_is_bit_exact(prec):
     finally:
         B.rbfgs_destroy(h1)
         B.rbfgs_destroy(h2)
+
+
+def test_fp64_core_on_a_cluster_matches_one_cta_and_the_oracle():
+    # The q x q core of Algorithm 4 in FP64 (C C^T = sym(M), written as C^-T): spread over a cluster
+    # of 8 CTAs it gives the same bits as on one CTA (each element is computed by one thread in the
+    # same order), and C^-T agrees with the oracle's FP64 Cholesky factor inverted by Gauss-Jordan
+    # to FP32 rounding.  An indefinite M returns RB_ENOTSPD and leaves the output untouched.
+    import torch
+
+    rng = np.random.default_rng(5)
+    for q in (128, 100, 64, 33, 7):
+        Z = rng.standard_normal((4 * q, q))
+        M = (Z.T @ Z / (4 * q) + 1e-3 * np.eye(q)).astype(np.float32)
+        Md = to_dev(M, torch.float32)
+        outs = {}
+        for cl in (1, 8):
+            out = empty_dev(q, q, torch.float32)
+            used = B.rbfgs_core64(q, Md.data_ptr(), -1.0, out.data_ptr(), q, cl, stream_ptr())
+            outs[cl] = (used, from_dev(out))
+        assert outs[1][0] == 1 and outs[8][0] == 8, (outs[1][0], outs[8][0])
+        assert np.array_equal(outs[1][1], outs[8][1]), q
+        rc, Cf = orc.cholesky(M.astype(np.float64))
+        assert rc == 0
+        ref = -orc.gauss_jordan(Cf).T
+        assert rel(outs[8][1], ref) <= 1e-6, (q, rel(outs[8][1], ref))
+    q = 48
+    M = np.eye(q, dtype=np.float32)
+    M[3, 5] = M[5, 3] = 2.0  # the 2 x 2 block [[1, 2], [2, 1]] is indefinite
+    Md = to_dev(M, torch.float32)
+    out = empty_dev(q, q, torch.float32)
+    out.fill_(7.0)
+    with pytest.raises(B.RbfgsError):
+        B.rbfgs_core64(q, Md.data_ptr(), 1.0, out.data_ptr(), q, 8, stream_ptr())
+    assert np.all(from_dev(out) == 7.0)
