@@ -911,6 +911,7 @@ static void ada_step_tc(rb_ctx *h)
                 tc_gemm_nk_lo(h->tc, side, acc, TC_A_K, n, q, n, L, n, G, glo ? h->Glo : nullptr, n, W, nullptr, n,
                               stp, rsv);
             cudaEventRecord(h->ev_core, side);  // W done
+            mark_side(h, side, "@W done");
             // on the SMs the core frees while W runs: S^ = S C^-T and the next step's sketch
             tc_gemm_nk_t(h->tc2, st, upd, TC_A_MN, n, q, q, S, n, h->Bs, q, Sh, q, stp);
             ada_draw<float>(h, St_next, h->k + 1, st);
