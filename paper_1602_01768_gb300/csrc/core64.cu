@@ -46,51 +46,72 @@ struct Core64Out {
 };
 
 // 1 / sqrt(d) in FP64 for a pivot d > 0: an FP32 estimate refined by two Newton-Raphson steps on
-// f(y) = y^-2 - d, y <- y (3 - d y^2) / 2, each of which about doubles the number of correct bits
-// (FP32's ~23 -> ~46 -> the FP64 rounding level).  GB300's FP64 units are few; this takes fewer
-// dependent FP64 operations than a square root followed by a division.  Outside [1e-30, 1e30] (or
-// not finite) it takes sqrt and a division instead.
+// f(y) = y^-2 - d, y <- y + (y / 2)(1 - d y^2), each of which about doubles the number of correct
+// bits (FP32's ~23 -> ~46 -> the FP64 rounding level); a step is three dependent FP64 operations
+// (t = d y; r = 1 - t y by one FMA; y + (y / 2) r by another), fewer than a square root followed by
+// a division on GB300, whose FP64 units are few.  Outside [1e-30, 1e30] (or not finite) it takes
+// sqrt and a division instead.
 __device__ __forceinline__ double rsqrt_nr(double d)
 {
     if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
     double y = (double)rsqrtf((float)d);
-    const double h = 0.5 * d;
-    y = y * (1.5 - h * y * y);
-    y = y * (1.5 - h * y * y);
+#pragma unroll
+    for (int it = 0; it < 2; ++it) {
+        const double t = d * y, hy = 0.5 * y;
+        const double r = fma(-t, y, 1.0);
+        y = fma(hy, r, y);
+    }
     return y;
+}
+
+// Pivot j of the diagonal block (warp 0): lane 0 takes the reciprocal square root of A_jj (stored
+// as invd[j], L_jj = d / sqrt(d)), and every lane below the diagonal scales its element of column j.
+__device__ __forceinline__ void pivot_col(double *a, int nb, int o, int j, double *invd, int *bad)
+{
+    const int lane = threadIdx.x & 31;
+    double inv = 0.0;
+    if (lane == 0) {
+        const double d = pk(a, nb, o + j, o + j);
+        if (!(d > 0.0) || !isfinite(d)) *bad = 1;
+        inv = rsqrt_nr(d);
+        invd[j] = inv;
+        pk(a, nb, o + j, o + j) = d * inv;
+    }
+    inv = __shfl_sync(0xffffffffu, inv, 0);
+    if (lane > j) pk(a, nb, o + lane, o + j) = pk(a, nb, o + lane, o + j) * inv;
 }
 
 // Diagonal block p (rows and columns o .. o + 31, o = 32 p) of the block-packed matrices:
 // L_pp in place of A_pp (lower Cholesky) and X_pp = L_pp^-1, by all KT64 threads of the CTA.
-// One thread takes each pivot's reciprocal square root (rsqrt_nr; GB300 runs FP64 at a small
-// fraction of its FP32 rate, so the other warps do not repeat it: L_jj = d / sqrt(d), the column
-// below it scaled by 1 / sqrt(d) in the same warp), then the block's trailing elements are updated
-// one per thread.  X_pp is formed right-looking: row k is
-// finished by the stored reciprocal of L_kk, then every later row subtracts L_ik X_kc -- for each
-// element the same operations, in the same order, as a forward substitution down its column.
+// Cholesky with one pivot of look-ahead: while warps 1 .. 15 update columns j + 2 .. 31 with
+// column j, warp 0 updates column j + 1, takes its pivot (one thread: GB300 runs FP64 at a small
+// fraction of its FP32 rate, so the other warps do not repeat it) and scales it, so one barrier
+// separates the steps.  X_pp right-looking: at step k every later row subtracts L_ik X_kc, X_kc
+// taken as the unscaled row times the stored 1 / L_kk, and the rows are scaled once at the end.
+// Each element sees the same operations in the same order as a textbook right-looking Cholesky and
+// a forward substitution down each column of the inverse, whatever the warp that runs them.
 // Sets *bad when a pivot is not positive and finite (the same in every thread).  invd: 32 doubles.
 __device__ void diag_block(double *a, double *x, int nb, int o, double *invd, int *bad)
 {
     const int tid = threadIdx.x;
+    if (tid < 32) pivot_col(a, nb, o, 0, invd, bad);
+    __syncthreads();
     for (int j = 0; j < 32; ++j) {
-        if (tid < 32) {  // warp 0: pivot (lane 0) and column j scaled (lanes below the diagonal)
-            double inv = 0.0;
-            if (tid == 0) {
-                const double d = pk(a, nb, o + j, o + j);
-                if (!(d > 0.0) || !isfinite(d)) *bad = 1;
-                inv = rsqrt_nr(d);
-                invd[j] = inv;
-                pk(a, nb, o + j, o + j) = d * inv;
+        // column j is final; update the block's trailing elements (r, c), j < c <= r, with it
+        if (tid < 32) {
+            if (j + 1 < 32) {
+                const int r = tid;  // column j + 1, by warp 0, then its pivot
+                if (r > j) pk(a, nb, o + r, o + j + 1) -= pk(a, nb, o + r, o + j) * pk(a, nb, o + j + 1, o + j);
+                __syncwarp();
+                pivot_col(a, nb, o, j + 1, invd, bad);
             }
-            inv = __shfl_sync(0xffffffffu, inv, 0);
-            if (tid > j) pk(a, nb, o + tid, o + j) = pk(a, nb, o + tid, o + j) * inv;
-        }
-        __syncthreads();
-        for (int e = tid; e < 1024; e += KT64) {  // element (r, c), j < c <= r < 32
-            const int r = e >> 5, c = e & 31;
-            if (r > j && c > j && c <= r) {
-                const double lij = pk(a, nb, o + r, o + j);
-                pk(a, nb, o + r, o + c) -= lij * pk(a, nb, o + c, o + j);
+        } else {
+            for (int e = tid - 32; e < 1024; e += KT64 - 32) {  // columns j + 2 .. 31
+                const int r = e >> 5, c = e & 31;
+                if (c > j + 1 && c <= r) {
+                    const double lij = pk(a, nb, o + r, o + j);
+                    pk(a, nb, o + r, o + c) -= lij * pk(a, nb, o + c, o + j);
+                }
             }
         }
         __syncthreads();
@@ -101,15 +122,21 @@ __device__ void diag_block(double *a, double *x, int nb, int o, double *invd, in
         pk(x, nb, o + r, o + c) = (r == c) ? 1.0 : 0.0;
     }
     __syncthreads();
-    for (int k = 0; k < 32; ++k) {
-        if (tid <= k) pk(x, nb, o + k, o + tid) = pk(x, nb, o + k, o + tid) * invd[k];
-        __syncthreads();
+    for (int k = 0; k < 31; ++k) {
         for (int e = tid; e < 1024; e += KT64) {  // X_ic -= L_ik X_kc, i > k >= c
             const int i = e >> 5, c = e & 31;
-            if (i > k && c <= k) pk(x, nb, o + i, o + c) -= pk(a, nb, o + i, o + k) * pk(x, nb, o + k, o + c);
+            if (i > k && c <= k) {
+                const double xkc = pk(x, nb, o + k, o + c) * invd[k];
+                pk(x, nb, o + i, o + c) -= pk(a, nb, o + i, o + k) * xkc;
+            }
         }
         __syncthreads();
     }
+    for (int e = tid; e < 1024; e += KT64) {
+        const int k = e >> 5, c = e & 31;
+        if (c <= k) pk(x, nb, o + k, o + c) = pk(x, nb, o + k, o + c) * invd[k];
+    }
+    __syncthreads();
 }
 
 __global__ void __launch_bounds__(KT64, 1) k_core_blk64(int q, Core64Out out, int *status)
