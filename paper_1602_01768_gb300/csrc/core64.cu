@@ -45,23 +45,114 @@ struct Core64Out {
     float s2;
 };
 
-// 1 / sqrt(d) in FP64 for a pivot d > 0: an FP32 estimate refined by two Newton-Raphson steps on
-// f(y) = y^-2 - d, y <- y + (y / 2)(1 - d y^2), each of which about doubles the number of correct
-// bits (FP32's ~23 -> ~46 -> the FP64 rounding level); a step is three dependent FP64 operations
-// (t = d y; r = 1 - t y by one FMA; y + (y / 2) r by another), fewer than a square root followed by
-// a division on GB300, whose FP64 units are few.  Outside [1e-30, 1e30] (or not finite) it takes
-// sqrt and a division instead.
+// 1 / sqrt(d) in FP64 for a pivot d > 0: an FP32 estimate y refined by one step of cubic
+// convergence from the series (1 - r)^(-1/2) = 1 + r/2 + 3 r^2/8 + ..., r = 1 - d y^2:
+// y <- y + y r (1/2 + 3 r/8).  The estimate is good to ~2^-22, so the omitted r^3 term is ~2^-66,
+// below FP64 rounding; the step is four dependent FP64 operations (GB300's FP64 units are few, and
+// every one on this chain is paid for each of the q pivots in turn).  Outside [1e-30, 1e30] (or not
+// finite) it takes sqrt and a division instead.
 __device__ __forceinline__ double rsqrt_nr(double d)
 {
     if (!(d > 1e-30 && d < 1e30)) return 1.0 / sqrt(d);
-    double y = (double)rsqrtf((float)d);
-#pragma unroll
-    for (int it = 0; it < 2; ++it) {
-        const double t = d * y, hy = 0.5 * y;
-        const double r = fma(-t, y, 1.0);
-        y = fma(hy, r, y);
+    const double y = (double)rsqrtf((float)d);
+    const double t = d * y;
+    const double r = fma(-t, y, 1.0);
+    const double c = fma(0.375, r, 0.5);
+    const double yr = y * r;
+    return fma(yr, c, y);
+}
+
+// Dot product of len terms ab(k) = (u_k, v_k) in four partial sums (term k into sum k mod 4, each
+// ascending, then (s0 + s1) + (s2 + s3)): four independent FMA chains instead of one.  Both FP64
+// kernels use it for every element, so they agree bit for bit.
+template <typename F>
+__device__ __forceinline__ double dot4(int len, F ab)
+{
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int k = 0;
+    for (; k + 4 <= len; k += 4) {
+        double u, v;
+        ab(k, u, v);
+        s0 = fma(u, v, s0);
+        ab(k + 1, u, v);
+        s1 = fma(u, v, s1);
+        ab(k + 2, u, v);
+        s2 = fma(u, v, s2);
+        ab(k + 3, u, v);
+        s3 = fma(u, v, s3);
     }
-    return y;
+    double u, v;
+    if (k < len) {
+        ab(k, u, v);
+        s0 = fma(u, v, s0);
+    }
+    if (k + 1 < len) {
+        ab(k + 1, u, v);
+        s1 = fma(u, v, s1);
+    }
+    if (k + 2 < len) {
+        ab(k + 2, u, v);
+        s2 = fma(u, v, s2);
+    }
+    return (s0 + s1) + (s2 + s3);
+}
+
+// The symmetric part of the q x q FP32 input, padded with the identity to 32 nb, into the lower
+// block triangle of a.  M is first copied into xs (at least q (q + 1) floats) with coalesced reads
+// and a padded pitch, so that both M_ij and M_ji are then read from shared memory without conflicts.
+__device__ void load_sym(double *a, float *xs, int q, int nb, const float *src)
+{
+    const int tid = threadIdx.x, QP = 32 * nb, ps = q + 1;
+    for (int e = tid; e < q * q; e += KT64) xs[(e % q) + (e / q) * ps] = src[e];
+    __syncthreads();
+    for (int e = tid; e < QP * QP; e += KT64) {
+        const int i = e % QP, j = e / QP;
+        if ((i >> 5) < (j >> 5)) continue;
+        double v;
+        if (i < q && j < q)
+            v = 0.5 * ((double)xs[i + j * ps] + (double)xs[j + i * ps]);
+        else
+            v = (i == j) ? 1.0 : 0.0;
+        pk(a, nb, i, j) = v;
+    }
+    __syncthreads();
+}
+
+// Panel element L_ip(r, c) = sum_{k <= c} A_ip(r, k) X_pp(c, k) (row i of the matrix, block column o).
+__device__ __forceinline__ double panel_val(double *a, double *x, int nb, int i, int o, int c)
+{
+    return dot4(c + 1, [&](int k, double &u, double &v) {
+        u = pk(a, nb, i, o + k);
+        v = pk(x, nb, o + c, o + k);
+    });
+}
+
+// Trailing-update term sum_{k < 32} L_ip(i, k) L_jp(j, k).
+__device__ __forceinline__ double trail_val(double *a, int nb, int i, int j, int o)
+{
+    return dot4(32, [&](int k, double &u, double &v) {
+        u = pk(a, nb, i, o + k);
+        v = pk(a, nb, j, o + k);
+    });
+}
+
+// T_j(r, c) = sum_{k = 32 bj}^{32 bi - 1} L(32 bi + r, k) X(k, 32 bj + c).
+__device__ __forceinline__ double t_val(double *a, double *x, int nb, int bi, int bj, int r, int c)
+{
+    return dot4(32 * (bi - bj), [&](int kk, double &u, double &v) {
+        const int k = 32 * bj + kk;
+        u = pk(a, nb, 32 * bi + r, k);
+        v = pk(x, nb, k, 32 * bj + c);
+    });
+}
+
+// X_(bi, bj)(r, c) = -sum_{k <= r} X_(bi, bi)(r, k) T_bj(k, c).
+__device__ __forceinline__ double x_val(double *x, const double *t, int nb, int bi, int bj, int r, int c)
+{
+    return -dot4(r + 1, [&](int k, double &u, double &v) {
+        u = pk(x, nb, 32 * bi + r, 32 * bi + k);
+        v = t[bj * BLK + k + c * BLD];
+    });
 }
 
 // Pivot j of the diagonal block (warp 0): lane 0 takes the reciprocal square root of A_jj (stored
@@ -142,7 +233,7 @@ __device__ void diag_block(double *a, double *x, int nb, int o, double *invd, in
 __global__ void __launch_bounds__(KT64, 1) k_core_blk64(int q, Core64Out out, int *status)
 {
     extern __shared__ double smd[];
-    const int nb = (q + 31) / 32, QP = 32 * nb;
+    const int nb = (q + 31) / 32;
     double *a = smd;                 // A, overwritten by L
     double *x = smd + NPACK * BLK;   // X = L^-1
     double *t = smd + 2 * NPACK * BLK;  // T blocks of the current block diagonal
@@ -151,18 +242,9 @@ __global__ void __launch_bounds__(KT64, 1) k_core_blk64(int q, Core64Out out, in
     if (status_bad(status)) return;
     const int tid = threadIdx.x;
     if (tid == 0) fail = 0;
-    // symmetric part of the padded matrix, lower block triangle only (identity padding)
-    for (int e = tid; e < QP * QP; e += KT64) {
-        const int i = e % QP, j = e / QP;
-        if ((i >> 5) < (j >> 5)) continue;
-        double v;
-        if (i < q && j < q)
-            v = 0.5 * ((double)out.src[i + (size_t)j * q] + (double)out.src[j + (size_t)i * q]);
-        else
-            v = (i == j) ? 1.0 : 0.0;
-        pk(a, nb, i, j) = v;
-    }
-    __syncthreads();
+    // symmetric part of the padded matrix, lower block triangle only (identity padding); X's space
+    // stages the FP32 input
+    load_sym(a, (float *)x, q, nb, out.src);
     for (int p = 0; p < nb; ++p) {
         const int o = 32 * p;
         diag_block(a, x, nb, o, invd, &fail);
@@ -179,10 +261,7 @@ __global__ void __launch_bounds__(KT64, 1) k_core_blk64(int q, Core64Out out, in
             pv[u] = 0.0;
             if (e < npanel) {
                 const int blk = e >> 10, w = e & 1023, r = w & 31, c = w >> 5;
-                const int i = o + 32 * (blk + 1) + r;
-                double s = 0.0;
-                for (int k = 0; k <= c; ++k) s += pk(a, nb, i, o + k) * pk(x, nb, o + c, o + k);
-                pv[u] = s;
+                pv[u] = panel_val(a, x, nb, o + 32 * (blk + 1) + r, o, c);
             }
         }
         __syncthreads();
@@ -206,9 +285,7 @@ __global__ void __launch_bounds__(KT64, 1) k_core_blk64(int q, Core64Out out, in
             }
             const int bi = bj + blk, w = e & 1023, r = w & 31, c = w >> 5;
             const int i = o + 32 * (bi + 1) + r, j = o + 32 * (bj + 1) + c;
-            double s = 0.0;
-            for (int k = 0; k < 32; ++k) s += pk(a, nb, i, o + k) * pk(a, nb, j, o + k);
-            pk(a, nb, i, j) -= s;
+            pk(a, nb, i, j) -= trail_val(a, nb, i, j, o);
         }
         __syncthreads();
     }
@@ -217,17 +294,12 @@ __global__ void __launch_bounds__(KT64, 1) k_core_blk64(int q, Core64Out out, in
         const int nt = (nb - d) * 1024;
         for (int e = tid; e < nt; e += KT64) {  // T_j = sum_{k=j}^{j+d-1} L_(j+d, k) X_(k, j)
             const int bj = e >> 10, w = e & 1023, r = w & 31, c = w >> 5, bi = bj + d;
-            double s = 0.0;
-            for (int bk = bj; bk < bi; ++bk)
-                for (int k = 0; k < 32; ++k) s += pk(a, nb, 32 * bi + r, 32 * bk + k) * pk(x, nb, 32 * bk + k, 32 * bj + c);
-            t[bj * BLK + r + c * BLD] = s;
+            t[bj * BLK + r + c * BLD] = t_val(a, x, nb, bi, bj, r, c);
         }
         __syncthreads();
         for (int e = tid; e < nt; e += KT64) {  // X_(j+d, j) = -X_(j+d, j+d) T_j
             const int bj = e >> 10, w = e & 1023, r = w & 31, c = w >> 5, bi = bj + d;
-            double s = 0.0;
-            for (int k = 0; k <= r; ++k) s += pk(x, nb, 32 * bi + r, 32 * bi + k) * t[bj * BLK + k + c * BLD];
-            pk(x, nb, 32 * bi + r, 32 * bj + c) = -s;
+            pk(x, nb, 32 * bi + r, 32 * bj + c) = x_val(x, t, nb, bi, bj, r, c);
         }
         __syncthreads();
     }
@@ -290,7 +362,7 @@ __device__ __forceinline__ void put_all(double *p, double v, uint32_t ncl)
 __global__ void __launch_bounds__(KT64, 1) k_core_cl64(int q, Core64Out out, int *status)
 {
     extern __shared__ double smd[];
-    const int nb = (q + 31) / 32, QP = 32 * nb;
+    const int nb = (q + 31) / 32;
     double *a = smd;
     double *x = smd + NPACK * BLK;
     double *t = smd + 2 * NPACK * BLK;
@@ -310,18 +382,8 @@ __global__ void __launch_bounds__(KT64, 1) k_core_cl64(int q, Core64Out out, int
     }
     cl_sync();  // rank 0's flag read everywhere before any CTA may leave
     if (flag) return;
-    for (int e = tid; e < QP * QP; e += KT64) {  // every copy loads the same symmetric part
-        const int i = e % QP, j = e / QP;
-        if ((i >> 5) < (j >> 5)) continue;
-        double v;
-        if (i < q && j < q)
-            v = 0.5 * ((double)out.src[i + (size_t)j * q] + (double)out.src[j + (size_t)i * q]);
-        else
-            v = (i == j) ? 1.0 : 0.0;
-        pk(a, nb, i, j) = v;
-    }
     if (tid == 0) flag = 0;
-    __syncthreads();
+    load_sym(a, (float *)x, q, nb, out.src);  // every copy loads the same symmetric part
     for (int p = 0; p < nb; ++p) {
         const int o = 32 * p;
         diag_block(a, x, nb, o, invd, &flag);  // in every CTA alike
@@ -339,10 +401,7 @@ __global__ void __launch_bounds__(KT64, 1) k_core_cl64(int q, Core64Out out, int
             pv[u] = 0.0;
             if (e < npanel) {
                 const int blk = e >> 10, w = e & 1023, r = w & 31, c = w >> 5;
-                const int i = o + 32 * (blk + 1) + r;
-                double s = 0.0;
-                for (int k = 0; k <= c; ++k) s += pk(a, nb, i, o + k) * pk(x, nb, o + c, o + k);
-                pv[u] = s;
+                pv[u] = panel_val(a, x, nb, o + 32 * (blk + 1) + r, o, c);
             }
         }
         cl_sync();
@@ -366,10 +425,8 @@ __global__ void __launch_bounds__(KT64, 1) k_core_cl64(int q, Core64Out out, int
             }
             const int bi = bj + blk, w = e & 1023, r = w & 31, c = w >> 5;
             const int i = o + 32 * (bi + 1) + r, j = o + 32 * (bj + 1) + c;
-            double s = 0.0;
-            for (int k = 0; k < 32; ++k) s += pk(a, nb, i, o + k) * pk(a, nb, j, o + k);
             double &dst = pk(a, nb, i, j);
-            put_all(&dst, dst - s, ncl);
+            put_all(&dst, dst - trail_val(a, nb, i, j, o), ncl);
         }
         cl_sync();
     }
@@ -378,17 +435,12 @@ __global__ void __launch_bounds__(KT64, 1) k_core_cl64(int q, Core64Out out, int
         const int nt = (nb - d) * 1024;
         for (int e = gt; e < nt; e += gstride) {  // T_j = sum_{k=j}^{j+d-1} L_(j+d, k) X_(k, j)
             const int bj = e >> 10, w = e & 1023, r = w & 31, c = w >> 5, bi = bj + d;
-            double s = 0.0;
-            for (int bk = bj; bk < bi; ++bk)
-                for (int k = 0; k < 32; ++k) s += pk(a, nb, 32 * bi + r, 32 * bk + k) * pk(x, nb, 32 * bk + k, 32 * bj + c);
-            put_all(&t[bj * BLK + r + c * BLD], s, ncl);
+            put_all(&t[bj * BLK + r + c * BLD], t_val(a, x, nb, bi, bj, r, c), ncl);
         }
         cl_sync();
         for (int e = gt; e < nt; e += gstride) {  // X_(j+d, j) = -X_(j+d, j+d) T_j
             const int bj = e >> 10, w = e & 1023, r = w & 31, c = w >> 5, bi = bj + d;
-            double s = 0.0;
-            for (int k = 0; k <= r; ++k) s += pk(x, nb, 32 * bi + r, 32 * bi + k) * t[bj * BLK + k + c * BLD];
-            put_all(&pk(x, nb, 32 * bi + r, 32 * bj + c), -s, ncl);
+            put_all(&pk(x, nb, 32 * bi + r, 32 * bj + c), x_val(x, t, nb, bi, bj, r, c), ncl);
         }
         cl_sync();
     }
