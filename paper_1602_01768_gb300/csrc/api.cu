@@ -892,7 +892,7 @@ static void ada_step_tc(rb_ctx *h)
         if (gram_main) mark(h, "S^T G");
         cudaEventRecord(h->ev_g, st);
         cudaStreamWaitEvent(side, h->ev_g, 0);
-        core_first = tcv && gram_main && fuse && h->c_core64;
+        core_first = tcv && gram_main && h->c_core64;
         if (core_first) {
             // FP64 C core on a cluster of SIDE_SMS CTAs.  A cluster needs all its SMs in one GPC: it
             // is launched in stream order right after S^T G, so it is placed while the GPU is idle,
@@ -912,9 +912,10 @@ static void ada_step_tc(rb_ctx *h)
                               stp, rsv);
             cudaEventRecord(h->ev_core, side);  // W done
             mark_side(h, side, "@W done");
-            // on the SMs the core frees while W runs: S^ = S C^-T and the next step's sketch
-            tc_gemm_nk_t(h->tc2, st, upd, TC_A_MN, n, q, q, S, n, h->Bs, q, Sh, q, stp);
-            ada_draw<float>(h, St_next, h->k + 1, st);
+            if (fuse) {  // on the SMs the core frees while W runs: S^ = S C^-T and the next step's sketch
+                tc_gemm_nk_t(h->tc2, st, upd, TC_A_MN, n, q, q, S, n, h->Bs, q, Sh, q, stp);
+                ada_draw<float>(h, St_next, h->k + 1, st);
+            }
         } else if (tcv) {  // S^T A S = S^T G (3 x TF32) -> -C^-T into Bv, C^-T into Bs
             if (!gram_main) {
                 tc_gemm_nk_lo(h->tc2, side, 3, TC_A_K, q, q, n, S, n, G, glo ? h->Glo : nullptr, n, h->Mf, nullptr,
